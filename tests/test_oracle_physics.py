@@ -1,0 +1,461 @@
+"""Pins of the oracle's simulation against closed forms and invariants.
+
+Deposit: charge equals the particle weight sum; a quiet uniform load gives
+n = 1 at every node including the wall nodes (half-volume correction).
+Ohm/Faraday: motional field of a uniform drift; discrete div B invariant in a
+periodic box; whistler / ion-cyclotron dispersion of a seeded circularly
+polarised mode; Bell non-resonant growth rate (Sec. 3.1 values). Faux shock
+(Sec. 2, Eq. 1): flux bookkeeping, downstream-frame speed conservation, return
+fraction, flux-weighted angle law, first-order limit; test-particle diffusive
+acceleration reproduces Eq. 2 and q_p = 3r/(r-1). Injection and open walls:
+exact counts, steady uniform density.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import oracle as O
+from tests.golden import paper
+
+GOLD = paper.load()
+
+
+def quiet_load(nx, ny, ppc_x, ppc_y=1, vel=None):
+    """Evenly spaced particles, ppc_x * ppc_y per cell (a quiet start)."""
+    ci, cj, fx, fy = [], [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            for a in range(ppc_x):
+                for b in range(ppc_y):
+                    ci.append(i); cj.append(j)
+                    fx.append((a + 0.5) / ppc_x); fy.append((b + 0.5) / ppc_y)
+    ci = np.array(ci, np.int32); cj = np.array(cj, np.int32)
+    fx = np.array(fx); fy = np.array(fy)
+    n = ci.size
+    v = np.zeros((3, n)) if vel is None else vel(ci + fx, cj + fy)
+    return ci, cj, fx, fy, v[0], v[1], v[2]
+
+
+# ----------------------------------------------------------------- deposit
+@pytest.mark.parametrize("dim", [1, 2])
+def test_deposit_total_charge_and_current(dim):
+    ny = 6 if dim == 2 else 1
+    sim = O.Oracle(dim=dim, nx=20, ny=ny, ppc=16, mach_a=3.0, beta_i=2.0, seed=11)
+    p = sim.particles()
+    w = 1.0 / 16
+    n = sim.grid(O.GRID_N); J = sim.grid(O.GRID_J)
+    vol = np.ones(sim.nxn); vol[0] = vol[-1] = 0.5  # wall nodes own half a cell
+    tot_n = (n * vol[None, :]).sum()
+    tot_j = (J * vol[None, :, None]).sum(axis=(0, 1))
+    npart = p["vx"].size
+    assert abs(tot_n - w * npart) <= npart * 2.0 ** -40 * 4
+    for c, k in enumerate(("vx", "vy", "vz")):
+        assert abs(tot_j[c] - w * p[k].sum()) <= npart * 2.0 ** -40 * 4 * (1 + abs(p[k]).max())
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_quiet_uniform_load_gives_unit_density_at_walls(dim):
+    nx, ny = 12, (5 if dim == 2 else 1)
+    sim = O.Oracle(dim=dim, nx=nx, ny=ny, ppc=4 if dim == 1 else 8, init_plasma=0)
+    sim.inject(*quiet_load(nx, ny, 4, 2 if dim == 2 else 1))
+    n = sim.grid(O.GRID_N)
+    assert np.all(n == 1.0)
+
+
+def test_density_floor_and_velocity_moment():
+    sim = O.Oracle(dim=1, nx=10, ppc=2, init_plasma=0, n_floor=0.05)
+    ci = np.array([3, 3], np.int32)
+    sim.inject(ci, ci * 0, np.array([0.0, 0.0]), np.zeros(2), np.array([2.0, 4.0]),
+               np.array([1.0, -1.0]), np.zeros(2))
+    n = sim.grid(O.GRID_N)[0]; u = sim.grid(O.GRID_U)[0]
+    assert n[3] == 1.0 and u[3, 0] == 3.0 and u[3, 1] == 0.0
+    others = np.delete(n, 3)
+    assert np.all(others == 0.05)
+
+
+# ----------------------------------------------------------------- fields
+def test_motional_electric_field_of_uniform_drift():
+    th = 30.0
+    M = 7.0
+    for bc in (O.BC_FAUXSHOCK, O.BC_PERIODIC):
+        sim = O.Oracle(dim=2, nx=8, ny=4, ppc=4, init_plasma=0, theta_bn_deg=th,
+                       beta_e=0.0, bc_x=bc)
+        sim.inject(*quiet_load(8, 4, 2, 2, vel=lambda x, y: np.stack(
+            [-M + 0 * x, 0 * x, 0 * x])))
+        E = sim.grid(O.GRID_E)
+        # E = -u x B0 with u = -M x, B0 = (cos, sin, 0): u x B0 = (0, 0, -M sin th),
+        # so E = (0, 0, +M sin th)
+        want_z = M * math.sin(math.radians(th))
+        assert np.allclose(E[..., 2], want_z, atol=1e-13)
+        assert np.allclose(E[..., :2], 0.0, atol=1e-13)
+    # in a periodic box the uniform cold drift is an equilibrium: B stays B0
+    B0 = sim.grid(O.GRID_B).copy()
+    sim.step(50)
+    assert np.abs(sim.grid(O.GRID_B) - B0).max() < 1e-12
+
+
+def _divB(B, dx, dy):
+    # node divergence from centres, periodic in both directions
+    Bpp = B; Bmp = np.roll(B, 1, axis=1); Bpm = np.roll(B, 1, axis=0)
+    Bmm = np.roll(Bpm, 1, axis=1)
+    dxbx = ((Bpp[..., 0] + Bpm[..., 0]) - (Bmp[..., 0] + Bmm[..., 0])) * (0.5 / dx)
+    dyby = ((Bpp[..., 1] + Bmp[..., 1]) - (Bpm[..., 1] + Bmm[..., 1])) * (0.5 / dy)
+    return dxbx + dyby
+
+
+def test_divergence_of_B_invariant_periodic_2d():
+    nx, ny, dx, dy = 16, 12, 0.5, 0.5
+    sim = O.Oracle(dim=2, nx=nx, ny=ny, dx=dx, dy=dy, ppc=8, bc_x=O.BC_PERIODIC,
+                   mach_a=2.0, beta_i=1.0, beta_e=1.0, seed=5, dt=0.01)
+    rng = np.random.default_rng(9)
+    B = sim.grid(O.GRID_B) + 0.05 * rng.standard_normal((ny, nx, 3))
+    sim.set_B(B)
+    d0 = _divB(sim.grid(O.GRID_B), dx, dy)
+    sim.step(20)
+    d1 = _divB(sim.grid(O.GRID_B), dx, dy)
+    assert np.abs(d1 - d0).max() < 1e-13
+    # and the field did evolve
+    assert np.abs(sim.grid(O.GRID_B) - B).max() > 1e-4
+
+
+def _mode_phase_amp(B, k, dx):
+    x = (np.arange(B.shape[1]) + 0.5) * dx
+    b = B[0, :, 1] + 1j * B[0, :, 2]
+    return (b * np.exp(-1j * k * x)).sum() / B.shape[1]
+
+
+@pytest.mark.parametrize("k,branch", [(1.0, +1), (1.0, -1), (0.5, +1), (0.5, -1)])
+def test_parallel_mode_dispersion_cold_plasma(k, branch):
+    # Cold Hall-MHD: for b = B_y + i B_z ~ exp(i(kx - wt)) about B0 = x,
+    # w^2 + k^2 w - k^2 = 0, i.e. |w| = (k^2/2)(sqrt(1 + 4/k^2) -+ 1)
+    # (ion-cyclotron / whistler branches, Alfven w -> k as k -> 0).
+    root = math.sqrt(k ** 4 + 4 * k ** 2)
+    w = (-k * k + root) / 2 if branch > 0 else (-k * k - root) / 2
+    m, cells_per_l = 2, 64
+    L = 2 * math.pi * m / k
+    nx = m * cells_per_l
+    dx = L / nx
+    dt = 0.002
+    amp = 1e-3
+    ppc = 8
+
+    def vel(x, y):
+        ph = k * x * dx
+        vb = -(k / w) * amp * np.exp(1j * ph)
+        return np.stack([0 * ph, vb.real, vb.imag])
+
+    sim = O.Oracle(dim=1, nx=nx, dx=dx, dt=dt, ppc=ppc, init_plasma=0,
+                   bc_x=O.BC_PERIODIC, mach_a=0.0, beta_i=0.0, beta_e=0.0)
+    xc = (np.arange(nx) + 0.5) * dx
+    B = sim.grid(O.GRID_B)
+    B[0, :, 1] = amp * np.cos(k * xc); B[0, :, 2] = amp * np.sin(k * xc)
+    sim.set_B(B)
+    sim.inject(*quiet_load(nx, 1, ppc, vel=vel))
+    period = 2 * math.pi / abs(w)
+    nsteps = int(1.5 * period / dt)
+    every = max(1, nsteps // 60)
+    ts, ph = [], []
+    for s in range(0, nsteps, every):
+        c = _mode_phase_amp(sim.grid(O.GRID_B), k, dx)
+        ts.append(s * dt); ph.append(np.angle(c))
+        sim.step(every)
+    ph = np.unwrap(ph)
+    slope = np.polyfit(ts, ph, 1)[0]
+    assert slope == pytest.approx(-w, rel=0.01)
+
+
+def test_bell_growth_rate_matches_sec31_kmax():
+    # Sec. 3.1: J_CR ~ 0.2 n_g v_A gives k_max ~ 0.1/d_i. With the current as
+    # a prescribed uniform x-current in Ohm's law, cold linear theory gives
+    # w^2 + A w - A = 0, A = k (k - J): growth gamma = sqrt(-A - A^2/4), the
+    # fastest mode at k = J/2 with gamma ~ k_max v_A.
+    J = GOLD["bell_j_early"]
+    kmax = GOLD["bell_kmax_early"]
+    assert J / 2 == pytest.approx(kmax)
+    A = kmax * (kmax - J)
+    gamma = math.sqrt(-A - A * A / 4)
+    nx, ppc = 128, 8
+    L = 2 * math.pi / kmax
+    dx = L / nx
+    dt = 0.01
+    sim = O.Oracle(dim=1, nx=nx, dx=dx, dt=dt, ppc=ppc, init_plasma=0,
+                   bc_x=O.BC_PERIODIC, mach_a=0.0, beta_i=0.0, beta_e=0.0, j_cr_ext=J)
+    xc = (np.arange(nx) + 0.5) * dx
+    B = sim.grid(O.GRID_B)
+    B[0, :, 1] = 1e-5 * np.cos(kmax * xc); B[0, :, 2] = 1e-5 * np.sin(kmax * xc)
+    sim.set_B(B)
+    sim.inject(*quiet_load(nx, 1, ppc))
+    ts, lam = [], []
+    t_end = 70.0
+    every = 100
+    for s in range(0, int(t_end / dt), every):
+        c = _mode_phase_amp(sim.grid(O.GRID_B), kmax, dx)
+        ts.append(s * dt); lam.append(math.log(abs(c)))
+        sim.step(every)
+    ts = np.array(ts); lam = np.array(lam)
+    sel = ts > 30.0
+    g = np.polyfit(ts[sel], lam[sel], 1)[0]
+    assert g == pytest.approx(gamma, rel=0.10)
+    assert math.exp(lam[-1]) < 0.1  # still linear
+
+
+# ----------------------------------------------------------------- faux shock
+def _u2(**kw):
+    d = dict(O.DEFAULTS); d.update(kw)
+    return d["u2"] if d["u2"] > 0 else d["mach_a"] / d["r_comp"]
+
+
+def test_fs_returned_keeps_downstream_speed_and_moves_upstream():
+    rng = np.random.default_rng(4)
+    u2 = _u2()
+    nret = 0
+    for pid in range(3000):
+        v = np.array([-abs(rng.normal(5, 4)) - 0.01, rng.normal(0, 3), rng.normal(0, 3)])
+        r, vn, mu = O.fs_rule(v, pid, 17)
+        if r:
+            nret += 1
+            w0 = np.linalg.norm(v + [u2, 0, 0]); w1 = np.linalg.norm(vn + [u2, 0, 0])
+            assert abs(w1 - w0) <= 1e-14 * w0
+            assert vn[0] >= 0.0
+            assert u2 / w0 <= mu <= 1.0
+        else:
+            assert np.array_equal(vn, v)
+    assert nret > 100
+
+
+@pytest.mark.parametrize("frame", [O.FRAME_SHOCK, O.FRAME_DOWNSTREAM])
+def test_fs_return_fraction_matches_eq1(frame):
+    # Eq. 1: P = ((1 - u2/v)/(1 + u2/v))^2 with v the speed in the chosen frame.
+    u2 = 2.5
+    rng = np.random.default_rng(5)
+    probs, hits = [], 0
+    N = 20000
+    for pid in range(N):
+        sp = rng.uniform(0.5, 40.0)
+        mu = -rng.uniform(0.05, 1.0)
+        phi = rng.uniform(0, 2 * math.pi)
+        v = sp * np.array([mu, math.sqrt(1 - mu * mu) * math.cos(phi),
+                           math.sqrt(1 - mu * mu) * math.sin(phi)])
+        vp = sp if frame == O.FRAME_SHOCK else np.linalg.norm(v + [u2, 0, 0])
+        w = np.linalg.norm(v + [u2, 0, 0])
+        P = ((1 - u2 / vp) / (1 + u2 / vp)) ** 2 if (vp > u2 and w > u2) else 0.0
+        probs.append(P)
+        r, _, _ = O.fs_rule(v, pid, 3, u2=u2, fs_speed_frame=frame)
+        hits += r
+    m = np.sum(probs)
+    sd = math.sqrt(np.sum(np.array(probs) * (1 - np.array(probs))))
+    assert abs(hits - m) < 4 * sd + 1, (hits, m, sd)
+
+
+def test_fs_first_order_limit_and_zero_kick():
+    # Sec. 2: for u2 << v, P_return ~ 1 - 4 u2 / v
+    c4 = GOLD["p_return_first_order_coeff"]
+    u2, v = 1.0, 200.0
+    N = 40000
+    hits = sum(O.fs_rule([-v, 0.0, 0.0], pid, 1, u2=u2)[0] for pid in range(N))
+    p_first = 1 - c4 * u2 / v
+    sd = math.sqrt(N * p_first * (1 - p_first))
+    assert abs(hits - N * p_first) < 4 * sd + N * 3 * (u2 / v) ** 2
+    # a vanishing kick returns every particle with its speed unchanged
+    for pid in range(200):
+        r, vn, _ = O.fs_rule([-3.0, 1.0, 0.5], pid, 2, u2=1e-12)
+        assert r and abs(np.linalg.norm(vn) - math.sqrt(10.25)) < 1e-9
+
+
+def test_fs_angle_law_is_flux_weighted():
+    # downstream isotropy + flux weighting: pdf(mu') ~ mu' - a on [a, 1],
+    # CDF ((mu - a)/(1 - a))^2
+    u2 = 2.0
+    v = np.array([-6.0, 0.0, 0.0])
+    w = np.linalg.norm(v + [u2, 0, 0])
+    a = u2 / w
+    mus, phis = [], []
+    for pid in range(40000):
+        r, vn, mu = O.fs_rule(v, pid, 9, u2=u2, fs_speed_frame=O.FRAME_DOWNSTREAM)
+        if r:
+            mus.append(mu)
+            phis.append(math.atan2(vn[2], vn[1]))
+    mus = np.array(mus)
+    ks = stats.kstest(mus, lambda m: np.clip(((m - a) / (1 - a)) ** 2, 0, 1))
+    assert ks.pvalue > 1e-3
+    assert stats.kstest((np.array(phis) + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-3
+
+
+def test_fs_counters_balance_in_a_run():
+    sim = O.Oracle(dim=1, nx=128, ppc=16, mach_a=10.0, seed=3)
+    sim.step(200)
+    d = sim.diag()
+    assert d["incident"] > 250  # ppc u_sh dt/dx = 1.6 crossings per step
+    assert d["incident"] == d["transmitted"] + d["reflected"]
+    assert d["reflected"] > 0
+    p = sim.particles()
+    returned = (p["id"] & O.ID_RETURNED) != 0
+    assert returned.sum() > 0
+    assert d["n_particles"] == 128 * 16 + d["injected"] - d["transmitted"] - d["escaped"]
+
+
+def test_paper_setup_thermal_open_all_transmitted():
+    # Sec. 2: the faux shock is an open boundary for the thermal plasma
+    sim = O.Oracle(dim=1, nx=64, ppc=8, mach_a=10.0, fs_mode_thermal=O.FS_OPEN)
+    sim.step(100)
+    d = sim.diag()
+    assert d["incident"] > 0 and d["reflected"] == 0
+    assert d["transmitted"] == d["incident"]
+
+
+def test_diffusive_acceleration_test_particles():
+    # Test-particle Monte Carlo: the faux-shock return (downstream side) plus
+    # an ideal isotropiser upstream (isotropic, flux-weighted return in the
+    # frame of the upstream flow, -u1 x in the shock frame). Eq. 2 with the
+    # particle speed v in place of c (non-relativistic particles, for which the
+    # momentum gain is the relevant one): <dp/p> ~ (4/3)(u1 - u2)/v per cycle;
+    # the integral spectrum N(>p) ~ p^-(q_p - 3), q_p = 3r/(r-1) (Sec. 2;
+    # q_p = 4 at r = 4).
+    r = GOLD["r_strong"]
+    u1 = 1.0
+    u2 = u1 / r
+    rng = np.random.default_rng(12)
+    n0 = 6000
+    v0 = 40.0
+    gains = []
+    vel = np.zeros((n0, 3))
+    vel[:, 0] = -v0
+    alive = np.ones(n0, bool)
+    for cycle in range(160):
+        idx = np.nonzero(alive)[0]
+        if idx.size == 0:
+            break
+        for k in idx:
+            p_before = math.sqrt(vel[k] @ vel[k])
+            ret, vn, _ = O.fs_rule(vel[k], int(k), cycle, u2=u2, mach_a=u1,
+                                   fs_speed_frame=O.FRAME_DOWNSTREAM)
+            if not ret:
+                alive[k] = False
+                continue
+            # upstream isotropiser: frame of the upstream flow
+            wv = vn + [u1, 0, 0]
+            wsp = np.linalg.norm(wv)
+            a = u1 / wsp
+            # pdf(mu) ~ (a - mu) on [-1, a]: crossing flux toward the shock
+            mu = a - (1 + a) * math.sqrt(rng.uniform())
+            ph = rng.uniform(0, 2 * math.pi)
+            st = math.sqrt(max(0.0, 1 - mu * mu))
+            vel[k] = wsp * np.array([mu, st * math.cos(ph), st * math.sin(ph)]) - [u1, 0, 0]
+            p_after = math.sqrt(vel[k] @ vel[k])
+            if 1 <= cycle < 12:  # the first crossing is a beam, not isotropic
+                gains.append((p_after - p_before) / (u1 - u2))
+    # Eq. 2 prefactor: <dp/p> v / (u1 - u2) = 4/3, to O(u/v)
+    assert np.mean(gains) == pytest.approx(GOLD["energy_gain_prefactor"], rel=0.05)
+    # integral spectrum slope from the speeds reached by all particles
+    ps = np.sort(np.linalg.norm(vel, axis=1))
+    grid = np.geomspace(1.5 * v0, 20 * v0, 12)
+    Ngt = np.array([(ps > g).sum() for g in grid])
+    ok = Ngt > 30
+    slope = np.polyfit(np.log(grid[ok]), np.log(Ngt[ok]), 1)[0]
+    q_p = 3 - slope
+    assert q_p == pytest.approx(GOLD["q_p_strong"], abs=0.15)
+    assert q_p == pytest.approx(3 * r / (r - 1), abs=0.15)
+
+
+# ----------------------------------------------------------------- injection
+def test_injection_counts_and_steady_density():
+    # Sec. 2: thermal plasma injected continuously at the far wall, drifting at
+    # u_sh toward the faux shock (open for it). Per transverse cell the count
+    # over S steps is the integer part of S * ppc u_sh dt / dx to within one.
+    nx, ny, ppc, M, dt, dx = 64, 4, 16, 8.0, 0.005, 0.5
+    sim = O.Oracle(dim=2, nx=nx, ny=ny, ppc=ppc, mach_a=M, dt=dt, dx=dx, dy=dx,
+                   fs_mode_thermal=O.FS_OPEN, beta_i=0.5, beta_e=0.5, seed=21)
+    S = 400
+    sim.step(S)
+    d = sim.diag()
+    rate = ppc * M * dt / dx
+    assert abs(d["injected"] - ny * rate * S) <= ny
+    assert d["n_particles"] == nx * ny * ppc + d["injected"] - d["transmitted"] - d["escaped"]
+    prof = sim.grid(O.GRID_PROFILE_N)
+    # plasma crossed the whole box (L / u_sh = 4 < S dt = 2? no: 32/8 = 4 > 2):
+    # interior density stays 1 within noise
+    inner = prof[4:-4]
+    assert abs(inner.mean() - 1.0) < 0.03
+    assert np.abs(inner - 1.0).max() < 6 / math.sqrt(ppc * ny)
+    db2 = sim.grid(O.GRID_PROFILE_DB2)
+    assert db2.max() < 25.0 / (ppc)
+
+
+def test_ion_acoustic_speed_from_electron_pressure():
+    # Cold ions, isothermal electrons (T_e = beta_e / 2): quasi-neutral
+    # longitudinal waves travel at c_s = sqrt(T_e) (m_i = 1), w = k c_s.
+    beta_e = 1.0
+    cs = math.sqrt(beta_e / 2)
+    k, m, cpl, ppc = 0.5, 2, 64, 16
+    L = 2 * math.pi * m / k
+    nx = m * cpl
+    dx = L / nx
+    dt = 0.01
+    delta = 1e-3
+    ci, cj, fx, fy, vx, vy, vz = quiet_load(nx, 1, ppc)
+    x0 = (ci + fx) * dx
+    # displacement xi = -(delta/k) sin(k x0) gives n = 1 + delta cos(k x)
+    x = x0 - (delta / k) * np.sin(k * x0)
+    ci = np.floor(x / dx).astype(np.int32) % nx
+    fx = x / dx - np.floor(x / dx)
+    vx = cs * delta * np.cos(k * x0)
+    sim = O.Oracle(dim=1, nx=nx, dx=dx, dt=dt, ppc=ppc, init_plasma=0,
+                   bc_x=O.BC_PERIODIC, mach_a=0.0, beta_i=0.0, beta_e=beta_e)
+    sim.inject(ci, cj, fx, fy, vx, vy, vz)
+    xn = np.arange(nx) * dx
+    period = 2 * math.pi / (k * cs)
+    nsteps = int(1.5 * period / dt)
+    every = nsteps // 60
+    ts, ph = [], []
+    for s in range(0, nsteps, every):
+        n = sim.grid(O.GRID_N)[0]
+        c = (n * np.exp(-1j * k * xn)).sum()
+        ts.append(s * dt); ph.append(np.angle(c))
+        sim.step(every)
+    slope = np.polyfit(ts, np.unwrap(ph), 1)[0]
+    assert slope == pytest.approx(-k * cs, rel=0.02)
+
+
+def test_whistler_along_y_in_2d():
+    # The same cold dispersion relation along y in a 2D box (B0 = y,
+    # theta_Bn = 90 deg): with the cyclic relabelling (x, y, z) -> (y, z, x),
+    # b = B_z + i B_x ~ exp(i(ky - wt)), w^2 + k^2 w - k^2 = 0.
+    k = 1.0
+    root = math.sqrt(k ** 4 + 4 * k ** 2)
+    w = (-k * k - root) / 2
+    m, cpl, ppc_y = 1, 64, 4
+    L = 2 * math.pi * m / k
+    ny, nx = m * cpl, 4
+    dy = L / ny
+    dt = 0.002
+    amp = 1e-3
+
+    def vel(x, y):
+        ph = k * y * dy
+        vb = -(k / w) * amp * np.exp(1j * ph)
+        return np.stack([vb.imag, 0 * ph, vb.real])
+
+    sim = O.Oracle(dim=2, nx=nx, ny=ny, dx=0.5, dy=dy, dt=dt, ppc=2 * ppc_y,
+                   init_plasma=0, bc_x=O.BC_PERIODIC, mach_a=0.0, beta_i=0.0,
+                   beta_e=0.0, theta_bn_deg=90.0)
+    yc = (np.arange(ny) + 0.5) * dy
+    B = sim.grid(O.GRID_B)
+    B[..., 0] = 0.0
+    B[:, :, 1] = 1.0
+    B[:, :, 2] = amp * np.cos(k * yc)[:, None]
+    B[:, :, 0] = amp * np.sin(k * yc)[:, None]
+    sim.set_B(B)
+    sim.inject(*quiet_load(nx, ny, 2, ppc_y, vel=vel))
+    period = 2 * math.pi / abs(w)
+    nsteps = int(1.5 * period / dt)
+    every = max(1, nsteps // 50)
+    ts, ph = [], []
+    for s in range(0, nsteps, every):
+        Bc = sim.grid(O.GRID_B)
+        b = (Bc[:, :, 2] + 1j * Bc[:, :, 0]).mean(axis=1)
+        ts.append(s * dt); ph.append(np.angle((b * np.exp(-1j * k * yc)).sum()))
+        sim.step(every)
+    slope = np.polyfit(ts, np.unwrap(ph), 1)[0]
+    assert slope == pytest.approx(-w, rel=0.01)
