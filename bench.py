@@ -1,0 +1,402 @@
+"""Benchmark: particle-steps/s of the full faux-shock hybrid step on GB300.
+
+Default workload (N=1): the 2D production-shaped faux-shock box computed in
+FP64 (4096 x 256 cells, dx = 0.5 d_i, 16 ppc = 16.8 M particles, M_A = 20,
+theta_Bn = 0, beta_i = beta_e = 1, dt = 0.0025, seed 2). The same run also
+times the FP32 precision form (8192 x 512 cells, 64 ppc = 268 M particles,
+M_A = 30, theta_Bn = 30 deg, dt = 0.002, seed 3) and reports it under "fp32"
+(the metric compares FP32 with FP64).
+
+A step is one full hybrid step: gather, Boris push, faux-shock pass/return,
+cell binning, moment deposition, moment finish, Ohm's law + Faraday RK4
+substeps and the node packing for the next gather. Inputs (particle state,
+1.6 GB FP64 / 15 GB FP32) are larger than L2 (129 MB), so no L2 flush is
+needed between steps.
+
+Multi-GPU: the path does not shard (one box per GPU); N > 1 runs N
+independent replicas (weak scaling), one per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s on 1 GB300 (full hybrid step), % HBM roofline; FP32 vs FP64"
+UNIT = "particle-steps/s"
+
+FP64_WORKLOAD = dict(dim=2, nx=4096, ny=256, dx=0.5, dy=0.5, dt=0.0025, mach_a=20.0,
+                     theta_bn_deg=0.0, beta_i=1.0, beta_e=1.0, ppc=16, seed=2)
+FP32_WORKLOAD = dict(dim=2, nx=8192, ny=512, dx=0.5, dy=0.5, dt=0.002, mach_a=30.0,
+                     theta_bn_deg=30.0, beta_i=1.0, beta_e=1.0, ppc=64, seed=3)
+WORKLOAD_NAME = ("2D faux-shock hybrid PIC, 4096x256 cells, dx=0.5 d_i, 16 ppc "
+                 "(16.8M protons), M_A=20, theta_Bn=0, beta_i=beta_e=1, dt=0.0025, "
+                 "FP64 plain method, seed 2")
+FP32_NAME = ("2D faux-shock hybrid PIC precision form, 8192x512 cells, 64 ppc "
+             "(268M protons), M_A=30, theta_Bn=30 deg, beta=1, dt=0.002, FP32, seed 3")
+
+# Algorithmic bytes of the particle push per particle-step: the particle state
+# (int32 cell, offsets, velocity, uint32 id) read once and written once.
+def particle_bytes(prec_bytes: int, dim: int) -> int:
+    return 2 * (4 + prec_bytes * dim + 3 * prec_bytes + 4)
+
+
+# Grid traffic per cell per step on a single pass (moments write + read 8
+# words, B read + write 6, E write 3, E + Bbar read by the gather 6).
+GRID_WORDS_PER_CELL = 23
+# FP64 operations of the written scheme per particle-step in 2D (gather 48,
+# Boris 46 + one division, move 8, deposit 38).
+FP64_OPS_PER_PARTICLE_STEP = 140
+# FP64 throughput of GB300: 1.25 TFLOP/s nominal counts an FMA as two; the
+# scheme issues unfused adds and multiplies, one operation per pipe slot.
+FP64_PEAK_OPS = 0.625e12
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    if n_gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    dist.init_process_group("nccl")
+    return (dist.get_rank(), dist.get_world_size(), int(os.environ.get("LOCAL_RANK", 0)),
+            dist)
+
+
+def timed_run(fs, torch, params: dict, prec, steps: int, warmup: int, dist, device,
+              sample_clocks: bool, local_rank: int):
+    """Device-resident timing of `steps` steps; returns measurements."""
+    sim = fs.FauxShock(device=device, precision=prec, **params)
+    stream = sim.stream
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    n0 = sim.num_particles()
+    l0 = sim.diag()["launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank) if sample_clocks else None
+    if clk:
+        clk.start()
+        time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    # per-phase events (the fused push kernel among them) are recorded by the
+    # library on the same stream inside the timed region
+    sim.profile(True)
+    sim.profile_read()
+    e0.record(stream)
+    for _ in range(steps):
+        sim.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop() if clk else None
+    ms = e0.elapsed_time(e1)
+    phases = sim.profile_read()
+    sim.profile(False)
+    d = sim.diag()
+    n1 = d["n_particles"]
+    launches = d["launches"] - l0
+    # per-launch duration of the dominant kernel (the fused particle step),
+    # measured with events around single launches on the same stream
+    sizes = sim.sizes
+    out = dict(ms_total=ms, n_mean=0.5 * (n0 + n1), launches=launches, clocks=clocks,
+               sim=sim, tiles=sizes.tiles, tile=(sizes.tile_x, sizes.tile_y),
+               phases={k: v[0] / max(v[1], 1) for k, v in phases.items()})
+    return out
+
+
+def ours(args):
+    import torch
+    from paper_2507_14282_gb300 import fs
+
+    rank, world, local_rank, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(local_rank)
+    device = f"cuda:{local_rank}"
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+
+    res64 = timed_run(fs, torch, FP64_WORKLOAD, fs.FS_FP64, args.steps, args.warmup, dist,
+                      device, True, local_rank)
+    t64 = res64["ms_total"]
+    if dist:
+        tt = torch.tensor([t64], device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t64 = float(tt.item())
+    value = res64["n_mean"] * args.steps * world / (t64 * 1e-3)
+    ms_step = t64 / args.steps
+    pb64 = particle_bytes(8, 2)
+    grid_b64 = GRID_WORDS_PER_CELL * 8 / FP64_WORKLOAD["ppc"]
+    step_bw64 = res64["n_mean"] * (pb64 + grid_b64) / (ms_step * 1e-3) / 1e9
+    kern64 = res64["phases"]["push"]
+    achieved_ops = res64["n_mean"] * FP64_OPS_PER_PARTICLE_STEP / (kern64 * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_push<double,2>",
+                "achieved": achieved_ops, "peak": FP64_PEAK_OPS / 1e12,
+                "unit": "TFLOP/s (FP64 ops)",
+                "frac": achieved_ops / (FP64_PEAK_OPS / 1e12),
+                "traffic": None,
+                "kernel_ms": kern64,
+                "hbm_achieved_gbs": res64["n_mean"] * pb64 / (kern64 * 1e-3) / 1e9,
+                "hbm_peak_gbs": hbm, "hbm_frac": res64["n_mean"] * pb64 / (kern64 * 1e-3) / 1e9 / hbm,
+                "peak_source": "derived from nominal FP64 1.25 TFLOP/s (FMA=2)",
+                "step_hbm_frac": step_bw64 / hbm,
+                "phases_ms": res64["phases"]}
+    gpu_launches = res64["launches"]
+    res64["sim"].close()
+    del res64["sim"]
+    torch.cuda.empty_cache()
+
+    fp32 = None
+    if not args.skip_fp32:
+        res32 = timed_run(fs, torch, FP32_WORKLOAD, fs.FS_FP32, args.steps32, args.warmup,
+                          dist, device, False, local_rank)
+        t32 = res32["ms_total"]
+        if dist:
+            tt = torch.tensor([t32], device=device)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t32 = float(tt.item())
+        ms32 = t32 / args.steps32
+        v32 = res32["n_mean"] * args.steps32 * world / (t32 * 1e-3)
+        pb32 = particle_bytes(4, 2)
+        gb32 = GRID_WORDS_PER_CELL * 4 / FP32_WORKLOAD["ppc"]
+        kern32 = res32["phases"]["push"]
+        ach = res32["n_mean"] * pb32 / (kern32 * 1e-3) / 1e9
+        fp32 = {"workload": FP32_NAME, "value": v32, "unit": UNIT, "ms_per_step": ms32,
+                "steps": args.steps32, "n_particles": res32["n_mean"],
+                "bytes_per_particle_step": pb32 + gb32,
+                "step_roofline_frac": res32["n_mean"] * (pb32 + gb32) / (ms32 * 1e-3) / 1e9 / hbm,
+                "roofline": {"bound": "hbm", "kernel": "k_push<float,2>", "achieved": ach,
+                             "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                             "kernel_ms": kern32, "peak_source": peak_src},
+                "phases_ms": res32["phases"],
+                "vs_fp64": v32 / value, "gpu_launches": res32["launches"]}
+        gpu_launches += res32["launches"]
+        res32["sim"].close()
+        del res32["sim"]
+        torch.cuda.empty_cache()
+
+    e2e = end_to_end(fs, torch, device, args, dist, world)
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "grid": [4096, 256], "ppc": 16,
+                       "n_particles": res64["n_mean"], "precision": "fp64",
+                       "tiles": res64["tiles"], "tile": list(res64["tile"]),
+                       "l2": "inputs larger than L2 (1.6 GB particle state per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "fp32": fp32,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": gpu_launches,
+            "clocks": res64["clocks"],
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def end_to_end(fs, torch, device, args, dist, world):
+    """The same metric through the public API with host buffers: the initial
+    particle state is uploaded from pinned host memory (fs_inject), the steps
+    run, and B, n and the diagnostics are read back to the host; all inside
+    the timed region. Bytes are reported per step."""
+    import numpy as np
+    p = dict(FP64_WORKLOAD)
+    nx, ny, ppc = p["nx"], p["ny"], p["ppc"]
+    rng = np.random.default_rng(p["seed"])
+    n = nx * ny * ppc
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    ci = pin(np.repeat(np.tile(np.arange(nx, dtype=np.int32), ny), ppc))
+    cj = pin(np.repeat(np.repeat(np.arange(ny, dtype=np.int32), nx), ppc))
+    fx = pin(rng.uniform(0, 1, n))
+    fy = pin(rng.uniform(0, 1, n))
+    vth = (p["beta_i"] / 2) ** 0.5
+    vx = pin(rng.normal(-p["mach_a"], vth, n))
+    vy = pin(rng.normal(0, vth, n))
+    vz = pin(rng.normal(0, vth, n))
+    steps = args.e2e_steps
+    sim = fs.FauxShock(device=device, precision=fs.FS_FP64, init_plasma=0, **p)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    sim.inject(ci, cj, fx, fy, vx, vy, vz)
+    sim.step(steps)
+    B = sim.grid(fs.FS_B)
+    nn = sim.grid(fs.FS_N)
+    d = sim.diag()
+    t1 = time.perf_counter()
+    dt = t1 - t0
+    if dist:
+        tt = torch.tensor([dt], device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+    h2d = sum(a.nbytes for a in (ci, cj, fx, fy, vx, vy, vz))
+    d2h = B.nbytes + nn.nbytes + 8 * 20
+    val = 0.5 * (n + d["n_particles"]) * steps * world / dt
+    sim.close()
+    torch.cuda.empty_cache()
+    return {"value": val, "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "wall_s": dt}
+
+
+def cpu_baseline(args):
+    """The FP64 CPU oracle, as it stands, on one host core, over a bounded
+    sample of the workload: a 1/16 x-slice (256 x 256 cells, same ppc and
+    physics) for a fixed number of steps."""
+    from oracle import oracle as O
+    p = dict(FP64_WORKLOAD)
+    p["nx"] = 256
+    sim = O.Oracle(**p)
+    n0 = sim.num_particles
+    steps = args.cpu_steps
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    n1 = sim.num_particles
+    sim.close()
+    return {"value": 0.5 * (n0 + n1) * steps / dt, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"256x256-cell x-slice of the FP64 workload (16 ppc, "
+                      f"{n0} particles), {steps} steps, {dt:.1f} s, 1 core of "
+                      f"{os.cpu_count()}"}
+
+
+def reference(args):
+    """The reference arm: the FP64 CPU oracle timed on the host on the same
+    workload and metric, each step a bounded sample (a 1/16 x-slice)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    p = dict(FP64_WORKLOAD)
+    p["nx"] = 256
+    sim = O.Oracle(**p)
+    sim.step(args.warmup)
+    n0 = sim.num_particles
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    n1 = sim.num_particles
+    sim.close()
+    v = 0.5 * (n0 + n1) * args.steps / dt
+    sample = (f"256x256-cell x-slice of the FP64 workload ({n0} particles) per step, "
+              f"1 core of {os.cpu_count()}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "sample": "1/16 x-slice (256x256 cells)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--steps32", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

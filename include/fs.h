@@ -1,0 +1,224 @@
+/*
+ * fs.h -- C ABI of the GB300 faux-shock hybrid particle-in-cell engine.
+ *
+ * The engine advances a hybrid plasma (kinetic ions, massless isothermal
+ * electron fluid) in a box whose x = 0 wall is the "faux shock" of Simon,
+ * Caprioli, Haggerty & Reville (arXiv 2507.14282, Sec. 2): a particle that
+ * crosses it leaves the box or is returned upstream with a momentum kick that
+ * mimics scattering in the downstream, with the return probability of Eq. 1.
+ * Plasma enters continuously through the far wall x = L drifting toward the
+ * faux shock at u_sh = M_A (Sec. 2); the far wall is open; y is periodic.
+ *
+ * Normalised units (Sec. 2): x in d_i, t in 1/Omega_ci, v in v_A, B in B0,
+ * n in n_g, E in v_A B0 / c, energy in m v_A^2, ion charge-to-mass 1.
+ *
+ * Conventions for every entry point:
+ *  - Every function returns an int status: FS_OK (0) or a negative FS_E*
+ *    code; fs_strerror() names it. No C++ exception crosses the ABI.
+ *  - Device memory is owned by the caller: fs_query() reports how many bytes
+ *    one simulation needs, the caller allocates one device buffer of that size
+ *    (any allocator, e.g. a torch uint8 tensor) and passes it to fs_init().
+ *    The library never allocates or frees device memory. The buffer must stay
+ *    valid until fs_destroy(). Host arrays passed in are copied before return.
+ *  - Work is enqueued on the CUDA stream given to fs_init() (NULL = legacy
+ *    default stream). Entry points documented "synchronises" wait for that
+ *    stream; the others only enqueue.
+ *  - Device-side error conditions (capacity exhausted, non-finite motion, id
+ *    overflow) are sticky: kernels record them in a device status word, and
+ *    the next synchronising call returns the corresponding code. A handle that
+ *    has reported an error keeps returning it.
+ *  - One handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef FS_H
+#define FS_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FS_OK 0
+#define FS_EINVAL (-1)        /* bad parameter, size, pointer or argument */
+#define FS_ECAPACITY (-2)     /* particle, tile or mover capacity exhausted */
+#define FS_ENAN (-3)          /* non-finite particle motion */
+#define FS_EIDOVERFLOW (-4)   /* more than 2^30 particle ids issued */
+#define FS_ECUDA (-5)         /* a CUDA call or kernel launch failed */
+#define FS_ETIMEOUT (-6)      /* reserved: a bounded device wait ran out */
+#define FS_EUNSTABLE (-7)     /* reserved: field solve beyond its stability bound */
+
+/* precision of particle and field arithmetic */
+#define FS_FP64 0
+#define FS_FP32 1
+
+/* x boundary: the faux-shock box (Sec. 2) or a periodic box (tests) */
+#define FS_BC_FAUXSHOCK 0
+#define FS_BC_PERIODIC 1
+
+/* what the faux shock does to a species crossing it (Sec. 2) */
+#define FS_OPEN 0   /* always leaves the box (the paper's thermal plasma) */
+#define FS_SHOCK 1  /* passes or returns with Eq. 1's probability */
+
+/* frame of the speed v in Eq. 1 */
+#define FS_FRAME_SHOCK 0       /* the paper's wording: shock-frame speed */
+#define FS_FRAME_DOWNSTREAM 1  /* downstream-frame speed (flux-ratio form) */
+
+/*
+ * Simulation parameters. fs_params_default() fills every field; callers then
+ * change what they need. Physical parameters follow the columns of the
+ * paper's Table 1 (M_A, Delta x, Delta t, theta_Bn, n_cr/n_g, p_iso) and the
+ * faux-shock description of Sec. 2 (r, u2 = u_sh / r, Eq. 1).
+ */
+typedef struct fs_params {
+  int dim;                 /* 1 or 2 */
+  int nx, ny;              /* cells; ny = 1 when dim = 1; nx < 65536, ny < 32768 */
+  double dx, dy, dt;       /* cell size in d_i, step in 1/Omega_ci */
+  int precision;           /* FS_FP64 or FS_FP32 */
+  double mach_a;           /* u_sh / v_A in the shock (simulation) frame */
+  double theta_bn_deg;     /* B0 = (cos, sin, 0) */
+  double beta_i, beta_e;   /* T_i = beta_i / 2, T_e = beta_e / 2 (isothermal) */
+  int ppc;                 /* thermal macroparticles per cell; weight 1/ppc */
+  int bc_x;                /* FS_BC_FAUXSHOCK or FS_BC_PERIODIC */
+  int fs_mode_thermal;     /* FS_OPEN (paper) or FS_SHOCK */
+  int fs_speed_frame;      /* FS_FRAME_SHOCK or FS_FRAME_DOWNSTREAM */
+  double r_comp;           /* compression ratio r (default 4) */
+  double u2;               /* downstream speed; <= 0 means mach_a / r_comp */
+  int inject_thermal;      /* thermal inflow at x = L (faux-shock box) */
+  int cr_enable;           /* cosmic-ray source at the faux shock (Sec. 2) */
+  double n_cr_ratio;       /* n_cr / n_g (0.01 in Table 1) */
+  double p_iso;            /* cosmic-ray speed in the downstream frame */
+  double u_cr;             /* cosmic-ray bulk drift; <= 0 means u2 */
+  int n_sub;               /* RK4 field substeps per particle step */
+  double n_floor;          /* density floor used in Ohm's law */
+  double eta;              /* resistivity (default 0) */
+  double j_cr_ext;         /* prescribed uniform x-current in Ohm's law */
+  int init_plasma;         /* load the uniform drifting plasma at t = 0 */
+  unsigned long long seed; /* Philox key */
+  double capacity_factor;  /* particle slots per tile / (ppc * cells per tile) */
+  double mover_fraction;   /* mover-list slots / particle slots */
+  int tile_x, tile_y;      /* cells per tile (0: chosen by the library) */
+  int hist_nx, hist_np;    /* x - p_x histogram bins */
+  double hist_pmin, hist_pmax;
+} fs_params;
+
+/* sizes reported by fs_query */
+typedef struct fs_sizes {
+  size_t device_bytes;          /* one device buffer of this many bytes */
+  size_t device_alignment;      /* its required alignment in bytes */
+  long long particle_capacity;  /* total particle slots */
+  long long tiles;              /* number of tiles */
+  int tile_x, tile_y;           /* tile shape in cells */
+  int nxn;                      /* node columns: nx + 1, or nx when periodic */
+} fs_sizes;
+
+/* diagnostics (fs_diag) */
+typedef struct fs_diag_t {
+  long long step, n_particles, next_id;
+  long long incident, transmitted, reflected, escaped, injected;
+  double kinetic, magnetic;       /* energies, m v_A^2 n_g d_i^dim units */
+  double px, py, pz;              /* total momentum */
+  double fs_energy;               /* cumulative w dE of returned particles */
+  double injected_energy, removed_energy;
+  int status;                     /* sticky device status bits */
+  long long launches;             /* kernels this handle has launched */
+} fs_diag_t;
+
+/* what codes for fs_moments */
+#define FS_B 0            /* B at cell centres: [ny][nx][3] doubles */
+#define FS_E 1            /* E at nodes: [ny][nxn][3] */
+#define FS_BBAR 2         /* B averaged to nodes: [ny][nxn][3] */
+#define FS_N 3            /* ion density at nodes (after floor): [ny][nxn] */
+#define FS_J 4            /* ion current at nodes: [ny][nxn][3] */
+#define FS_U 5            /* ion bulk velocity J/n at nodes: [ny][nxn][3] */
+#define FS_PROFILE_N 6    /* y-averaged n: [nxn] */
+#define FS_PROFILE_DB2 7  /* y-averaged |B - B0|^2 / B0^2: [nx] */
+#define FS_HIST_XPX 8     /* x - p_x histogram, all species: [hist_nx][hist_np] int64 */
+#define FS_HIST_XPX_CR 9  /* the same for the cosmic-ray species only */
+
+typedef struct fs_handle fs_handle;
+
+/* Fills *out with defaults for a dim-dimensional faux-shock box.
+   Returns FS_EINVAL if out is NULL or dim is not 1 or 2. */
+int fs_params_default(int dim, fs_params* out);
+
+/* Validates *p and reports the device buffer size it needs in *out.
+   Allocates nothing. Returns FS_EINVAL for an inconsistent parameter set. */
+int fs_query(const fs_params* p, fs_sizes* out);
+
+/* Creates a simulation in the caller's device buffer (device_mem, of
+   device_bytes >= fs_query's size, aligned to device_alignment) on the given
+   CUDA stream (a cudaStream_t, or NULL). Loads B0 and, when init_plasma is
+   set, ppc particles per cell (uniform positions, drifting Maxwellian,
+   Sec. 2), deposits the moments and computes E^0. Enqueues only. */
+int fs_init(const fs_params* p, void* device_mem, size_t device_bytes,
+            void* cuda_stream, fs_handle** out);
+
+/* Appends n particles given on the host: cell indices (ci, cj), in-cell
+   offsets (fx, fy) in [0, 1), velocities (vx, vy, vz); fy/cj ignored in 1D.
+   ids: NULL assigns fresh thermal ids; otherwise each id word (bits 0-29
+   particle number, bit 30 cosmic ray, bit 31 returned) is kept. Re-deposits
+   the moments and recomputes E from the current B. Synchronises.
+   FS_EINVAL on an out-of-range cell or offset; FS_ECAPACITY when a tile is
+   full. */
+int fs_inject(fs_handle* h, long long n, const int* ci, const int* cj,
+              const double* fx, const double* fy, const double* vx,
+              const double* vy, const double* vz, const unsigned* ids);
+
+/* Replaces B at the cell centres ([ny][nx][3] doubles on the host) and
+   recomputes E and B at the nodes from the current moments. Synchronises. */
+int fs_load_fields(fs_handle* h, const double* B_host);
+
+/* Advances nsteps particle steps (Sec. 2's boundary, the hybrid step).
+   Enqueues only; errors found on the device surface at the next
+   synchronising call. */
+int fs_step(fs_handle* h, int nsteps);
+
+/* Copies a grid quantity (what = FS_*) to dst (dst_bytes large enough:
+   doubles, or int64 for the histograms), on the host or (dst_on_device)
+   in device memory. Synchronises. */
+int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes,
+               int dst_on_device);
+
+/* Number of live particles. Synchronises. */
+int fs_num_particles(fs_handle* h, long long* n);
+
+/* Copies every live particle to host arrays of length cap (order
+   unspecified: sort by id to compare). *n receives the count.
+   FS_EINVAL if cap is too small. Synchronises. */
+int fs_get_particles(fs_handle* h, long long cap, int* ci, int* cj,
+                     double* fx, double* fy, double* vx, double* vy,
+                     double* vz, unsigned* id, long long* n);
+
+/* Diagnostics: FP64 energy/momentum sums, int64 faux-shock flux counters
+   (incident = transmitted + reflected), particle count. Synchronises. */
+int fs_diag(fs_handle* h, fs_diag_t* out);
+
+/* Per-phase timing of fs_step with CUDA events on the handle's stream
+   (tracing). Phases: FS_PHASE_PUSH (fused gather/push/faux shock/sort/
+   deposit kernel), FS_PHASE_MOVERS, FS_PHASE_INJECT, FS_PHASE_MOMENTS,
+   FS_PHASE_FIELDS (RK4 Ohm + Faraday and the node packing).
+   fs_profile(h, 1) starts recording (events are created on the host, no
+   device memory); fs_profile_read() synchronises and writes, per phase, the
+   summed milliseconds ms[k] and the number of steps timed counts[k] since the
+   last read (arrays of nphases <= FS_NPHASES entries), then restarts the
+   sums. fs_profile(h, 0) stops and releases the events. */
+#define FS_PHASE_PUSH 0
+#define FS_PHASE_MOVERS 1
+#define FS_PHASE_INJECT 2
+#define FS_PHASE_MOMENTS 3
+#define FS_PHASE_FIELDS 4
+#define FS_NPHASES 5
+int fs_profile(fs_handle* h, int enable);
+int fs_profile_read(fs_handle* h, double* ms, long long* counts, int nphases);
+
+/* Releases the handle (host memory only). The device buffer stays the
+   caller's. */
+int fs_destroy(fs_handle* h);
+
+/* Name of a status code. */
+const char* fs_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,784 @@
+// fs_api.cu -- the C ABI declared in include/fs.h: parameter validation,
+// tile decomposition, layout of the caller's device buffer, and the host
+// orchestration of the kernels (fs_ops.cuh) on the caller's stream.
+//
+// The library allocates no device memory: every device region below is a
+// slice of the single buffer the caller passes to fs_init().
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "fs.h"
+#include "fs_internal.h"
+
+using namespace fsx;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool divides(int a, int b) { return a > 0 && b % a == 0; }
+
+// Tile shape: cells per tile close to 1024 / ppc particles... chosen so that
+// the mean tile holds about half a shared-memory chunk of particles.
+void choose_tile(const fs_params* p, int* tx, int* ty) {
+  if (p->dim == 1) {
+    if (p->tile_x > 0) { *tx = p->tile_x; *ty = 1; return; }
+    int best = 0;
+    for (int c = 2; c <= 256 && c <= p->nx; ++c) {
+      if (!divides(c, p->nx)) continue;
+      if ((long long)c * p->ppc <= 512 || best == 0) best = c;
+    }
+    *tx = best ? best : p->nx;
+    *ty = 1;
+    return;
+  }
+  if (p->tile_x > 0 && p->tile_y > 0) { *tx = p->tile_x; *ty = p->tile_y; return; }
+  int bx = 0, by = 0;
+  long long bestc = -1;
+  for (int cy = 1; cy <= 32 && cy <= p->ny; ++cy) {
+    if (!divides(cy, p->ny)) continue;
+    for (int cx = 2; cx <= 64 && cx <= p->nx; ++cx) {
+      if (!divides(cx, p->nx)) continue;
+      const long long cells = (long long)cx * cy;
+      if (cells * p->ppc > 512) continue;
+      // prefer more cells, then squarer tiles
+      const long long score = cells * 1000 - (long long)abs(cx - 2 * cy);
+      if (score > bestc) { bestc = score; bx = cx; by = cy; }
+    }
+  }
+  if (bestc < 0) {  // ppc very large: smallest legal tile
+    bx = 0;
+    for (int cx = 2; cx <= p->nx; ++cx) if (divides(cx, p->nx)) { bx = cx; break; }
+    by = 1;
+  }
+  *tx = bx;
+  *ty = by;
+}
+
+int validate(const fs_params* p) {
+  if (!p) return FS_EINVAL;
+  if (p->dim != 1 && p->dim != 2) return FS_EINVAL;
+  if (p->nx < 2 || p->nx > 65535) return FS_EINVAL;
+  if (p->ny < 1 || p->ny > 32767) return FS_EINVAL;
+  if (p->dim == 1 && p->ny != 1) return FS_EINVAL;
+  if (!(p->dx > 0) || !(p->dt > 0) || (p->dim == 2 && !(p->dy > 0))) return FS_EINVAL;
+  if (p->precision != FS_FP64 && p->precision != FS_FP32) return FS_EINVAL;
+  if (p->ppc < 1 || p->n_sub < 1) return FS_EINVAL;
+  if (p->bc_x != FS_BC_FAUXSHOCK && p->bc_x != FS_BC_PERIODIC) return FS_EINVAL;
+  if (p->fs_mode_thermal != FS_OPEN && p->fs_mode_thermal != FS_SHOCK) return FS_EINVAL;
+  if (p->fs_speed_frame != FS_FRAME_SHOCK && p->fs_speed_frame != FS_FRAME_DOWNSTREAM)
+    return FS_EINVAL;
+  if (!(p->r_comp > 1.0) && !(p->u2 > 0)) return FS_EINVAL;
+  if (!(p->beta_i >= 0) || !(p->beta_e >= 0)) return FS_EINVAL;
+  if (!(p->n_floor > 0)) return FS_EINVAL;
+  if (!(p->capacity_factor >= 1.0) || !(p->mover_fraction > 0)) return FS_EINVAL;
+  if (p->cr_enable) {
+    const double u2 = p->u2 > 0 ? p->u2 : p->mach_a / p->r_comp;
+    const double ucr = p->u_cr > 0 ? p->u_cr : u2;
+    if (!(p->p_iso > ucr)) return FS_EINVAL;
+  }
+  if (p->hist_nx < 1 || p->hist_np < 1 || !(p->hist_pmax > p->hist_pmin)) return FS_EINVAL;
+  if (p->mach_a < 0) return FS_EINVAL;
+  return FS_OK;
+}
+
+int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
+  int r = validate(p);
+  if (r) return r;
+  memset(g, 0, sizeof(*g));
+  memset(ph, 0, sizeof(*ph));
+  memset(L, 0, sizeof(*L));
+  int tx, ty;
+  choose_tile(p, &tx, &ty);
+  if (tx < 2 || !divides(tx, p->nx)) return FS_EINVAL;
+  if (p->dim == 2) {
+    if (ty < 1 || !divides(ty, p->ny)) return FS_EINVAL;
+  } else {
+    ty = 1;
+  }
+  g->dim = p->dim;
+  g->nx = p->nx;
+  g->ny = p->ny;
+  g->bc_x = p->bc_x;
+  g->nxn = (p->bc_x == FS_BC_PERIODIC) ? p->nx : p->nx + 1;
+  g->TX = tx;
+  g->TY = ty;
+  g->ntx = p->nx / tx;
+  g->nty = p->ny / ty;
+  g->ntiles = g->ntx * g->nty;
+  const long long cells_per_tile = (long long)tx * ty;
+  long long cap = (long long)ceil(p->capacity_factor * (double)(cells_per_tile * p->ppc)) + 64;
+  cap = (cap + 31) / 32 * 32;
+  if (cap > (1LL << 30)) return FS_EINVAL;
+  g->tile_cap = (int)cap;
+  g->cap_total = cap * g->ntiles;
+  if (g->cap_total >= (1LL << 31) - 1) return FS_EINVAL;
+  long long mc = (long long)ceil(p->mover_fraction * (double)g->cap_total) + 1024;
+  if (mc > (1LL << 31) - 1) mc = (1LL << 31) - 1;
+  g->mover_cap = (int)mc;
+  g->staging_cap = 1 << 16;
+  // shared-memory chunk: 1024 particles, or 2048 when the mean tile is larger
+  g->chunk = (cells_per_tile * p->ppc > 700) ? 2048 : 1024;
+  g->na = (tx + 3) * (p->dim == 2 ? ty + 3 : 1);
+  g->nk = (tx + 2) * (p->dim == 2 ? ty + 2 : 1) + 2;
+  const size_t smem = (p->precision == FS_FP64)
+                          ? push_smem_bytes_f64(p->dim, tx, ty, g->chunk)
+                          : push_smem_bytes_f32(p->dim, tx, ty, g->chunk);
+  if (smem > 227 * 1024 - 1024) return FS_EINVAL;
+  if (g->nk > 32 * 1024) return FS_EINVAL;
+
+  // physics constants (the same FP64 expressions the scheme is written in)
+  ph->dtdx = p->dt / p->dx;
+  ph->dtdy = (p->dim == 2) ? p->dt / p->dy : 0.0;
+  ph->hdt = 0.5 * p->dt;
+  ph->hdx = 0.5 / p->dx;
+  ph->hdy = (p->dim == 2) ? 0.5 / p->dy : 0.0;
+  ph->idx = 1.0 / p->dx;
+  ph->h = p->dt / (double)p->n_sub;
+  ph->hh = 0.5 * ph->h;
+  ph->h6 = ph->h / 6.0;
+  ph->te = 0.5 * p->beta_e;
+  ph->vth = sqrt(0.5 * p->beta_i);
+  ph->w_th = 1.0 / (double)p->ppc;
+  ph->w_cr = p->n_cr_ratio / (double)p->ppc;
+  ph->u2 = p->u2 > 0.0 ? p->u2 : p->mach_a / p->r_comp;
+  ph->u_cr = p->u_cr > 0.0 ? p->u_cr : ph->u2;
+  ph->p_iso = p->p_iso;
+  ph->mach_a = p->mach_a;
+  ph->n_floor = p->n_floor;
+  ph->eta = p->eta;
+  ph->jcr = p->j_cr_ext;
+  ph->rate = (((double)p->ppc * p->mach_a) * p->dt) / p->dx;
+  ph->cellvol = (p->dim == 2) ? p->dx * p->dy : p->dx;
+  const double th = p->theta_bn_deg * (3.14159265358979323846264338327950288 / 180.0);
+  ph->b0x = cos(th);
+  ph->b0y = sin(th);
+  ph->b0z = 0.0;
+  ph->fs_mode_thermal = p->fs_mode_thermal;
+  ph->fs_frame = p->fs_speed_frame;
+  ph->inject_thermal = p->inject_thermal ? 1 : 0;
+  ph->cr_enable = p->cr_enable ? 1 : 0;
+  ph->seed = p->seed;
+  ph->hist_nx = p->hist_nx;
+  ph->hist_np = p->hist_np;
+  ph->hist_pmin = p->hist_pmin;
+  ph->hist_pmax = p->hist_pmax;
+
+  // device buffer layout
+  const size_t T = (p->precision == FS_FP64) ? 8 : 4;
+  const size_t A = (p->precision == FS_FP64) ? 8 : 4;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    o = up(o, kAlign);
+    const size_t r = o;
+    o += bytes;
+    return r;
+  };
+  auto parts = [&](size_t* dst, size_t n) {
+    dst[0] = take(4 * n);
+    dst[1] = take(T * n);
+    dst[2] = take(p->dim == 2 ? T * n : 0);
+    dst[3] = take(T * n);
+    dst[4] = take(T * n);
+    dst[5] = take(T * n);
+    dst[6] = take(4 * n);
+  };
+  parts(L->part[0], g->cap_total);
+  parts(L->part[1], g->cap_total);
+  parts(L->mov, g->mover_cap);
+  parts(L->stg, g->staging_cap);
+  L->tile_base = take(4 * (size_t)g->ntiles);
+  L->cnt[0] = take(4 * (size_t)g->ntiles);
+  L->cnt[1] = take(4 * (size_t)g->ntiles);
+  const size_t nc = (size_t)p->nx * p->ny, nn = (size_t)g->nxn * p->ny;
+  L->B = take(3 * T * nc);
+  L->Bs = take(3 * T * nc);
+  L->Bsum = take(3 * T * nc);
+  L->E = take(3 * T * nn);
+  L->Es = take(3 * T * nn);
+  L->Bb = take(3 * T * nn);
+  L->G = take(8 * T * (size_t)(p->nx + 1) * (p->ny + 1));
+  L->n = take(T * nn);
+  L->u = take(3 * T * nn);
+  L->J = take(3 * T * nn);
+  L->partial = take(A * 4 * (size_t)g->na * g->ntiles);
+  L->far = take(A * 4 * nn);
+  L->acc = take(8 * (size_t)p->ny);
+  L->inj = take(4 * (2 * (size_t)p->ny + 2));
+  L->ctr = take(sizeof(Counters));
+  L->hist = take(8 * (size_t)p->hist_nx * p->hist_np);
+  L->prof = take(8 * ((size_t)g->nxn + p->nx));
+  L->total = up(o, kAlign);
+  return FS_OK;
+}
+
+int status_to_code(int st) {
+  if (st & kStatusTimeout) return FS_ETIMEOUT;
+  if (st & kStatusNaN) return FS_ENAN;
+  if (st & kStatusIdOverflow) return FS_EIDOVERFLOW;
+  if (st & (kStatusCapacity | kStatusBadCell)) return FS_ECAPACITY;
+  return FS_OK;
+}
+
+__global__ void k_fill_tiles(int* base, int* cnt, int ntiles, int cap, int init) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles;
+       t += gridDim.x * blockDim.x) {
+    base[t] = t * cap;
+    cnt[t] = init;
+  }
+}
+
+template <typename T>
+__global__ void k_fill_B(T* B, int nc, double bx, double by, double bz) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += gridDim.x * blockDim.x) {
+    B[c] = (T)bx;
+    B[(size_t)nc + c] = (T)by;
+    B[(size_t)2 * nc + c] = (T)bz;
+  }
+}
+
+// Synchronise the stream, then fold the device status word into the handle.
+int sync_and_check(Sim* s) {
+  if (s->sticky) return s->sticky;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->sticky = FS_ECUDA;
+  int st = 0;
+  e = cudaMemcpy(&st, s->base + s->L.ctr + offsetof(Counters, status), sizeof(int),
+                 cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return s->sticky = FS_ECUDA;
+  const int code = status_to_code(st);
+  if (code) s->sticky = code;
+  return code;
+}
+
+int grid_blocks(long long n) {
+  long long g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 4096) g = 4096;
+  return (int)g;
+}
+
+int redeposit(Sim* s) {
+  cudaError_t e = cudaMemsetAsync(s->base + s->L.far, 0,
+                                  (s->p.precision == FS_FP64 ? 8 : 4) * 4 *
+                                      (size_t)s->g.nxn * s->g.ny,
+                                  s->stream);
+  if (e != cudaSuccess) return FS_ECUDA;
+  if ((e = s->ops->deposit_all(s, s->cur)) != cudaSuccess) return FS_ECUDA;
+  if ((e = s->ops->moments(s)) != cudaSuccess) return FS_ECUDA;
+  if ((e = s->ops->ohm_final(s)) != cudaSuccess) return FS_ECUDA;
+  return FS_OK;
+}
+
+}  // namespace
+
+struct fs_handle {
+  Sim sim;
+  // phase timing (fs_profile): one set of FS_NPHASES + 1 events per step
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t used = 0;  // event sets recorded since the last read
+  double ms[FS_NPHASES] = {0};
+  long long counts[FS_NPHASES] = {0};
+};
+
+namespace {
+void release_events(fs_handle* h) {
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  h->events.clear();
+  h->used = 0;
+}
+}  // namespace
+
+extern "C" {
+
+int fs_params_default(int dim, fs_params* out) {
+  if (!out || (dim != 1 && dim != 2)) return FS_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->dim = dim;
+  out->nx = 512;
+  out->ny = (dim == 2) ? 64 : 1;
+  out->dx = 0.5;
+  out->dy = 0.5;
+  out->dt = 0.005;
+  out->precision = FS_FP64;
+  out->mach_a = 10.0;
+  out->theta_bn_deg = 0.0;
+  out->beta_i = 1.0;
+  out->beta_e = 1.0;
+  out->ppc = 32;
+  out->bc_x = FS_BC_FAUXSHOCK;
+  out->fs_mode_thermal = FS_SHOCK;
+  out->fs_speed_frame = FS_FRAME_SHOCK;
+  out->r_comp = 4.0;
+  out->u2 = 0.0;
+  out->inject_thermal = 1;
+  out->cr_enable = 0;
+  out->n_cr_ratio = 0.01;
+  out->p_iso = 100.0;
+  out->u_cr = 0.0;
+  out->n_sub = 2;
+  out->n_floor = 0.05;
+  out->eta = 0.0;
+  out->j_cr_ext = 0.0;
+  out->init_plasma = 1;
+  out->seed = 1;
+  out->capacity_factor = 3.0;
+  out->mover_fraction = 0.25;
+  out->tile_x = 0;
+  out->tile_y = 0;
+  out->hist_nx = 64;
+  out->hist_np = 64;
+  out->hist_pmin = -40.0;
+  out->hist_pmax = 40.0;
+  return FS_OK;
+}
+
+int fs_query(const fs_params* p, fs_sizes* out) {
+  if (!out) return FS_EINVAL;
+  Geo g;
+  Phys ph;
+  Layout L;
+  const int r = derive(p, &g, &ph, &L);
+  if (r) return r;
+  out->device_bytes = L.total;
+  out->device_alignment = kAlign;
+  out->particle_capacity = g.cap_total;
+  out->tiles = g.ntiles;
+  out->tile_x = g.TX;
+  out->tile_y = g.TY;
+  out->nxn = g.nxn;
+  return FS_OK;
+}
+
+int fs_init(const fs_params* p, void* device_mem, size_t device_bytes,
+            void* cuda_stream, fs_handle** out) {
+  if (!out) return FS_EINVAL;
+  *out = nullptr;
+  fs_handle* h = new (std::nothrow) fs_handle();
+  if (!h) return FS_EINVAL;
+  Sim* s = &h->sim;
+  int r = derive(p, &s->g, &s->ph, &s->L);
+  if (r) { delete h; return r; }
+  if (!device_mem || device_bytes < s->L.total || ((uintptr_t)device_mem % kAlign) != 0) {
+    delete h;
+    return FS_EINVAL;
+  }
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, device_mem) != cudaSuccess ||
+      attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    delete h;
+    return FS_EINVAL;
+  }
+  s->p = *p;
+  s->base = (char*)device_mem;
+  s->stream = (cudaStream_t)cuda_stream;
+  s->cur = 0;
+  s->step = 0;
+  s->sticky = 0;
+  s->ops = (p->precision == FS_FP64) ? &ops_f64() : &ops_f32();
+  const long long nc = (long long)p->nx * p->ny;
+  const size_t Tsz = (p->precision == FS_FP64) ? 8 : 4;
+  cudaError_t e = cudaSuccess;
+  auto zero = [&](size_t off, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->base + off, 0, bytes, s->stream);
+  };
+  zero(s->L.ctr, sizeof(Counters));
+  zero(s->L.acc, 8 * (size_t)p->ny);
+  zero(s->L.far, (s->L.acc > s->L.far) ? s->L.acc - s->L.far : 0);
+  zero(s->L.G, 8 * Tsz * (size_t)(p->nx + 1) * (p->ny + 1));
+  zero(s->L.cnt[1], 4 * (size_t)s->g.ntiles);
+  if (e != cudaSuccess) { delete h; return FS_ECUDA; }
+  const int init_cnt = p->init_plasma ? s->g.TX * s->g.TY * p->ppc : 0;
+  if (init_cnt > s->g.tile_cap) { delete h; return FS_EINVAL; }
+  if (p->init_plasma && nc * (long long)p->ppc > (long long)kIdMask) { delete h; return FS_EIDOVERFLOW; }
+  k_fill_tiles<<<grid_blocks(s->g.ntiles), 256, 0, s->stream>>>(
+      (int*)(s->base + s->L.tile_base), (int*)(s->base + s->L.cnt[0]), s->g.ntiles,
+      s->g.tile_cap, init_cnt);
+  if (p->precision == FS_FP64)
+    k_fill_B<double><<<grid_blocks(nc), 256, 0, s->stream>>>(
+        (double*)(s->base + s->L.B), (int)nc, s->ph.b0x, s->ph.b0y, s->ph.b0z);
+  else
+    k_fill_B<float><<<grid_blocks(nc), 256, 0, s->stream>>>(
+        (float*)(s->base + s->L.B), (int)nc, s->ph.b0x, s->ph.b0y, s->ph.b0z);
+  if (cudaGetLastError() != cudaSuccess) { delete h; return FS_ECUDA; }
+  if (p->init_plasma) {
+    if (s->ops->init_particles(s) != cudaSuccess) { delete h; return FS_ECUDA; }
+    const unsigned long long next = (unsigned long long)nc * p->ppc;
+    if (cudaMemcpyAsync(s->base + s->L.ctr + offsetof(Counters, next_id), &next, 8,
+                        cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+      delete h;
+      return FS_ECUDA;
+    }
+    // the copy reads a host stack value: wait for it before returning
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) { delete h; return FS_ECUDA; }
+  }
+  r = redeposit(s);
+  if (r) { delete h; return r; }
+  *out = h;
+  return FS_OK;
+}
+
+int fs_step(fs_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return FS_EINVAL;
+  Sim* s = &h->sim;
+  if (s->sticky) return s->sticky;
+  const bool inj = s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable);
+  const long long per_step = 1 + 1 + (inj ? 3 : 0) + 1 + 8LL * s->p.n_sub + 1;
+  constexpr int kSet = FS_NPHASES + 1;
+  for (int k = 0; k < nsteps; ++k) {
+    cudaEvent_t* ev = nullptr;
+    if (h->profiling) {
+      while (h->events.size() < (h->used + 1) * kSet) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return s->sticky = FS_ECUDA;
+        h->events.push_back(e);
+      }
+      ev = &h->events[h->used * kSet];
+      h->used++;
+    }
+    if (s->ops->step(s, s->cur, s->step, ev) != cudaSuccess) return s->sticky = FS_ECUDA;
+    s->cur = 1 - s->cur;
+    s->step++;
+    s->launches += per_step;
+  }
+  return FS_OK;
+}
+
+int fs_inject(fs_handle* h, long long n, const int* ci, const int* cj,
+              const double* fx, const double* fy, const double* vx,
+              const double* vy, const double* vz, const unsigned* ids) {
+  if (!h || n < 0) return FS_EINVAL;
+  Sim* s = &h->sim;
+  if (n == 0) return FS_OK;
+  if (!ci || !fx || !vx || !vy || !vz) return FS_EINVAL;
+  if (s->g.dim == 2 && (!cj || !fy)) return FS_EINVAL;
+  for (long long k = 0; k < n; ++k) {
+    const int j = (s->g.dim == 2) ? cj[k] : 0;
+    if (ci[k] < 0 || ci[k] >= s->g.nx || j < 0 || j >= s->g.ny) return FS_EINVAL;
+    if (!(fx[k] >= 0.0 && fx[k] < 1.0)) return FS_EINVAL;
+    if (s->g.dim == 2 && !(fy[k] >= 0.0 && fy[k] < 1.0)) return FS_EINVAL;
+    if (!isfinite(vx[k]) || !isfinite(vy[k]) || !isfinite(vz[k])) return FS_EINVAL;
+  }
+  int r = sync_and_check(s);
+  if (r) return r;
+  unsigned long long next = 0;
+  if (cudaMemcpy(&next, s->base + s->L.ctr + offsetof(Counters, next_id), 8,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return s->sticky = FS_ECUDA;
+  const bool dbl = (s->p.precision == FS_FP64);
+  const size_t Tsz = dbl ? 8 : 4;
+  // stage through the mover list (unused between steps) in large chunks
+  const int chunk = s->g.mover_cap > s->g.staging_cap ? s->g.mover_cap : s->g.staging_cap;
+  const size_t* stg = s->g.mover_cap > s->g.staging_cap ? s->L.mov : s->L.stg;
+  std::vector<int> cell(chunk);
+  std::vector<uint32_t> id(chunk);
+  std::vector<char> buf(5 * Tsz * (size_t)chunk);
+  for (long long k0 = 0; k0 < n; k0 += chunk) {
+    const int m = (int)((n - k0) < chunk ? (n - k0) : chunk);
+    char* cols[5];
+    for (int c = 0; c < 5; ++c) cols[c] = buf.data() + (size_t)c * Tsz * chunk;
+    for (int k = 0; k < m; ++k) {
+      const long long q = k0 + k;
+      const int j = (s->g.dim == 2) ? cj[q] : 0;
+      cell[k] = (j << 16) | ci[q];
+      uint32_t w;
+      if (ids) {
+        w = ids[q];
+        const unsigned long long num = w & kIdMask;
+        if (num >= next) next = num + 1;
+      } else {
+        if (next > kIdMask) return s->sticky = FS_EIDOVERFLOW;
+        w = (uint32_t)next++;
+      }
+      id[k] = w;
+      const double vals[5] = {fx[q], s->g.dim == 2 ? fy[q] : 0.0, vx[q], vy[q], vz[q]};
+      for (int c = 0; c < 5; ++c) {
+        if (dbl) {
+          ((double*)cols[c])[k] = vals[c];
+        } else {
+          float f = (float)vals[c];
+          if (c < 2 && f >= 1.0f) f = 0x1.fffffep-1f;
+          ((float*)cols[c])[k] = f;
+        }
+      }
+    }
+    cudaError_t e = cudaMemcpyAsync(s->base + stg[0], cell.data(), 4 * (size_t)m,
+                                    cudaMemcpyHostToDevice, s->stream);
+    const int map[5] = {1, 2, 3, 4, 5};
+    for (int c = 0; c < 5 && e == cudaSuccess; ++c) {
+      if (c == 1 && s->g.dim == 1) continue;
+      e = cudaMemcpyAsync(s->base + stg[map[c]], cols[c], Tsz * (size_t)m,
+                          cudaMemcpyHostToDevice, s->stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->base + stg[6], id.data(), 4 * (size_t)m,
+                          cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = s->ops->insert_staged(s, s->cur, m, stg == s->L.mov);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->sticky = FS_ECUDA;
+  }
+  if (cudaMemcpy(s->base + s->L.ctr + offsetof(Counters, next_id), &next, 8,
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return s->sticky = FS_ECUDA;
+  r = redeposit(s);
+  if (r) return s->sticky = r;
+  return sync_and_check(s);
+}
+
+int fs_load_fields(fs_handle* h, const double* B_host) {
+  if (!h || !B_host) return FS_EINVAL;
+  Sim* s = &h->sim;
+  int r = sync_and_check(s);
+  if (r) return r;
+  const size_t nc = (size_t)s->g.nx * s->g.ny;
+  const bool dbl = (s->p.precision == FS_FP64);
+  std::vector<char> tmp(3 * nc * (dbl ? 8 : 4));
+  for (size_t q = 0; q < nc; ++q)
+    for (int c = 0; c < 3; ++c) {
+      if (dbl) ((double*)tmp.data())[c * nc + q] = B_host[q * 3 + c];
+      else ((float*)tmp.data())[c * nc + q] = (float)B_host[q * 3 + c];
+    }
+  if (cudaMemcpyAsync(s->base + s->L.B, tmp.data(), tmp.size(), cudaMemcpyHostToDevice,
+                      s->stream) != cudaSuccess)
+    return s->sticky = FS_ECUDA;
+  if (s->ops->ohm_final(s) != cudaSuccess) return s->sticky = FS_ECUDA;
+  return sync_and_check(s);
+}
+
+int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes, int dst_on_device) {
+  if (!h || !dst) return FS_EINVAL;
+  Sim* s = &h->sim;
+  int r = sync_and_check(s);
+  if (r) return r;
+  const Geo& g = s->g;
+  const bool dbl = (s->p.precision == FS_FP64);
+  const size_t Tsz = dbl ? 8 : 4;
+  if (what == FS_HIST_XPX || what == FS_HIST_XPX_CR) {
+    const size_t need = 8 * (size_t)s->ph.hist_nx * s->ph.hist_np;
+    if (dst_bytes < need) return FS_EINVAL;
+    if (s->ops->hist(s, s->cur, what == FS_HIST_XPX ? -1 : 1) != cudaSuccess)
+      return s->sticky = FS_ECUDA;
+    if (cudaMemcpyAsync(dst, s->base + s->L.hist, need,
+                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess)
+      return s->sticky = FS_ECUDA;
+    return sync_and_check(s);
+  }
+  if (what == FS_PROFILE_N || what == FS_PROFILE_DB2) {
+    const size_t cnt = (what == FS_PROFILE_N) ? g.nxn : g.nx;
+    if (dst_bytes < 8 * cnt) return FS_EINVAL;
+    if (s->ops->profiles(s) != cudaSuccess) return s->sticky = FS_ECUDA;
+    const size_t off = s->L.prof + (what == FS_PROFILE_N ? 0 : 8 * (size_t)g.nxn);
+    if (cudaMemcpyAsync(dst, s->base + off, 8 * cnt,
+                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess)
+      return s->sticky = FS_ECUDA;
+    return sync_and_check(s);
+  }
+  size_t planes = 3, cols = g.nxn, src = 0;
+  switch (what) {
+    case FS_B: src = s->L.B; cols = g.nx; break;
+    case FS_E: src = s->L.E; break;
+    case FS_BBAR: src = s->L.Bb; break;
+    case FS_N: src = s->L.n; planes = 1; break;
+    case FS_J: src = s->L.J; break;
+    case FS_U: src = s->L.u; break;
+    default: return FS_EINVAL;
+  }
+  const size_t npts = cols * g.ny;
+  if (dst_bytes < 8 * planes * npts) return FS_EINVAL;
+  if (dst_on_device) {
+    if (s->ops->export_grid(s, what, (double*)dst) != cudaSuccess) return s->sticky = FS_ECUDA;
+    return sync_and_check(s);
+  }
+  std::vector<char> tmp(planes * npts * Tsz);
+  if (cudaMemcpyAsync(tmp.data(), s->base + src, tmp.size(), cudaMemcpyDeviceToHost,
+                      s->stream) != cudaSuccess)
+    return s->sticky = FS_ECUDA;
+  r = sync_and_check(s);
+  if (r) return r;
+  double* o = (double*)dst;
+  for (size_t q = 0; q < npts; ++q)
+    for (size_t c = 0; c < planes; ++c)
+      o[q * planes + c] = dbl ? ((double*)tmp.data())[c * npts + q]
+                              : (double)((float*)tmp.data())[c * npts + q];
+  return FS_OK;
+}
+
+int fs_num_particles(fs_handle* h, long long* n) {
+  if (!h || !n) return FS_EINVAL;
+  Sim* s = &h->sim;
+  int r = sync_and_check(s);
+  if (r) return r;
+  std::vector<int> cnt(s->g.ntiles);
+  if (cudaMemcpy(cnt.data(), s->base + s->L.cnt[s->cur], 4 * (size_t)s->g.ntiles,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return s->sticky = FS_ECUDA;
+  long long tot = 0;
+  for (int c : cnt) tot += (c < s->g.tile_cap ? c : s->g.tile_cap);
+  *n = tot;
+  return FS_OK;
+}
+
+int fs_get_particles(fs_handle* h, long long cap, int* ci, int* cj, double* fx,
+                     double* fy, double* vx, double* vy, double* vz, unsigned* id,
+                     long long* n) {
+  if (!h || !n) return FS_EINVAL;
+  Sim* s = &h->sim;
+  long long tot = 0;
+  int r = fs_num_particles(h, &tot);
+  if (r) return r;
+  *n = tot;
+  if (cap < tot) return FS_EINVAL;
+  if (tot > 0 && (!ci || !cj || !fx || !fy || !vx || !vy || !vz || !id)) return FS_EINVAL;
+  const Geo& g = s->g;
+  const bool dbl = (s->p.precision == FS_FP64);
+  const size_t Tsz = dbl ? 8 : 4;
+  std::vector<int> cnt(g.ntiles), base(g.ntiles);
+  cudaMemcpy(cnt.data(), s->base + s->L.cnt[s->cur], 4 * (size_t)g.ntiles, cudaMemcpyDeviceToHost);
+  cudaMemcpy(base.data(), s->base + s->L.tile_base, 4 * (size_t)g.ntiles, cudaMemcpyDeviceToHost);
+  const size_t* off = s->L.part[s->cur];
+  long long o = 0;
+  std::vector<char> tb(7 * 8 * (size_t)g.tile_cap);
+  for (int t = 0; t < g.ntiles; ++t) {
+    const int c = cnt[t] < g.tile_cap ? cnt[t] : g.tile_cap;
+    if (c <= 0) continue;
+    const size_t b = (size_t)base[t];
+    cudaError_t e = cudaSuccess;
+    char* p[7];
+    for (int k = 0; k < 7; ++k) p[k] = tb.data() + (size_t)k * 8 * g.tile_cap;
+    e = cudaMemcpy(p[0], s->base + off[0] + 4 * b, 4 * (size_t)c, cudaMemcpyDeviceToHost);
+    for (int k = 1; k <= 5 && e == cudaSuccess; ++k) {
+      if (k == 2 && g.dim == 1) continue;
+      e = cudaMemcpy(p[k], s->base + off[k] + Tsz * b, Tsz * (size_t)c, cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p[6], s->base + off[6] + 4 * b, 4 * (size_t)c, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return s->sticky = FS_ECUDA;
+    for (int k = 0; k < c; ++k, ++o) {
+      const int cell = ((int*)p[0])[k];
+      ci[o] = cell & 0xFFFF;
+      cj[o] = cell >> 16;
+      auto getT = [&](int col) {
+        return dbl ? ((double*)p[col])[k] : (double)((float*)p[col])[k];
+      };
+      fx[o] = getT(1);
+      fy[o] = (g.dim == 2) ? getT(2) : 0.0;
+      vx[o] = getT(3);
+      vy[o] = getT(4);
+      vz[o] = getT(5);
+      id[o] = ((uint32_t*)p[6])[k];
+    }
+  }
+  return FS_OK;
+}
+
+int fs_diag(fs_handle* h, fs_diag_t* out) {
+  if (!h || !out) return FS_EINVAL;
+  Sim* s = &h->sim;
+  int r = sync_and_check(s);
+  if (r) return r;
+  if (s->ops->diag(s, s->cur) != cudaSuccess) return s->sticky = FS_ECUDA;
+  Counters c;
+  if (cudaMemcpyAsync(&c, s->base + s->L.ctr, sizeof(c), cudaMemcpyDeviceToHost,
+                      s->stream) != cudaSuccess)
+    return s->sticky = FS_ECUDA;
+  r = sync_and_check(s);
+  if (r) return r;
+  long long np = 0;
+  r = fs_num_particles(h, &np);
+  if (r) return r;
+  memset(out, 0, sizeof(*out));
+  out->step = s->step;
+  out->n_particles = np;
+  out->next_id = (long long)c.next_id;
+  out->incident = (long long)c.incident;
+  out->transmitted = (long long)c.transmitted;
+  out->reflected = (long long)c.reflected;
+  out->escaped = (long long)c.escaped;
+  out->injected = (long long)c.injected;
+  out->kinetic = c.sums[0];
+  out->px = c.sums[1];
+  out->py = c.sums[2];
+  out->pz = c.sums[3];
+  out->magnetic = c.sums[4];
+  out->fs_energy = c.fs_energy;
+  out->injected_energy = c.injected_energy;
+  out->removed_energy = c.removed_energy;
+  out->status = c.status;
+  out->launches = s->launches;
+  return FS_OK;
+}
+
+int fs_profile(fs_handle* h, int enable) {
+  if (!h) return FS_EINVAL;
+  if (enable) {
+    h->profiling = true;
+    return FS_OK;
+  }
+  cudaStreamSynchronize(h->sim.stream);
+  h->profiling = false;
+  release_events(h);
+  return FS_OK;
+}
+
+int fs_profile_read(fs_handle* h, double* ms, long long* counts, int nphases) {
+  if (!h || !ms || !counts || nphases < 1 || nphases > FS_NPHASES) return FS_EINVAL;
+  Sim* s = &h->sim;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return s->sticky = FS_ECUDA;
+  constexpr int kSet = FS_NPHASES + 1;
+  for (size_t u = 0; u < h->used; ++u) {
+    for (int k = 0; k < FS_NPHASES; ++k) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, h->events[u * kSet + k], h->events[u * kSet + k + 1]) !=
+          cudaSuccess)
+        return s->sticky = FS_ECUDA;
+      h->ms[k] += t;
+      h->counts[k] += 1;
+    }
+  }
+  h->used = 0;
+  for (int k = 0; k < nphases; ++k) {
+    ms[k] = h->ms[k];
+    counts[k] = h->counts[k];
+  }
+  for (int k = 0; k < FS_NPHASES; ++k) {
+    h->ms[k] = 0;
+    h->counts[k] = 0;
+  }
+  return FS_OK;
+}
+
+int fs_destroy(fs_handle* h) {
+  if (!h) return FS_EINVAL;
+  cudaStreamSynchronize(h->sim.stream);
+  release_events(h);
+  delete h;
+  return FS_OK;
+}
+
+const char* fs_strerror(int status) {
+  switch (status) {
+    case FS_OK: return "ok";
+    case FS_EINVAL: return "invalid argument";
+    case FS_ECAPACITY: return "particle capacity exhausted";
+    case FS_ENAN: return "non-finite particle motion";
+    case FS_EIDOVERFLOW: return "particle id overflow";
+    case FS_ECUDA: return "CUDA error";
+    case FS_ETIMEOUT: return "device wait timed out";
+    case FS_EUNSTABLE: return "field solve unstable";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,897 @@
+// fs_engine.cuh -- the hot-path kernels of one hybrid step, templated on the
+// arithmetic type T (float or double) and the dimension DIM (1 or 2).
+//
+// Step n -> n+1 (Sec. 2 boundary inside a textbook hybrid PIC step):
+//   k_push     one CTA per tile of cells: CIC gather of E^n and Bbar^n from a
+//              shared-memory field tile, Boris push, move, open far wall,
+//              faux-shock pass/return (Eq. 1), in-tile counting sort by new
+//              cell, CIC deposit of n and J by runs of sorted particles with a
+//              warp segmented reduction into a shared-memory node tile, then
+//              stayers written back to the tile's bucket and leavers to the
+//              mover list. Deposit partials per tile, no global atomics
+//              (except rare far movers).
+//   k_movers   leavers appended to their destination tile's bucket.
+//   k_inject_* thermal inflow at x = L and the cosmic-ray source at x = 0.
+//   k_moments  sum of the per-tile partials in a fixed order, wall
+//              half-volume correction, density floor, u = J / n.
+//   k_ohm / k_faraday  RK4 substeps of dB/dt = -curl E(B), E from Ohm's law.
+//   k_ohm (final) also packs E and Bbar per node for the next gather.
+//
+// The FP64 instantiation is compiled without FMA contraction and evaluates
+// every expression in the same order as the written scheme, so that it agrees
+// bit for bit with an implementation of the same scheme on the CPU. Node sums
+// of the FP64 deposit are int64 fixed point (2^-40), independent of order.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fs_device.cuh"
+#include "fs_internal.h"
+
+namespace fsx {
+
+constexpr int kBlock = 256;
+
+template <typename T>
+struct Num;
+template <>
+struct Num<float> {
+  using acc = float;
+  static constexpr float offmax = 0x1.fffffep-1f;
+  __device__ static float fl(float x) { return floorf(x); }
+  __device__ static float ab(float x) { return fabsf(x); }
+};
+template <>
+struct Num<double> {
+  using acc = unsigned long long;  // int64 fixed point, two's complement
+  static constexpr double offmax = 0x1.fffffffffffffp-1;
+  __device__ static double fl(double x) { return floor(x); }
+  __device__ static double ab(double x) { return fabs(x); }
+};
+
+// A deposit contribution c (already scaled by 2^40 for FP64) in accumulator
+// form. FP64: round-to-nearest-even to an integer by adding 1.5 * 2^52 (exact
+// for |c| < 2^51), the same integer as llrint(c).
+__device__ __forceinline__ float to_acc(float c) { return c; }
+__device__ __forceinline__ unsigned long long to_acc(double c) {
+  const double m = __dadd_rn(c, 0x1.8p52);
+  return (unsigned long long)(__double_as_longlong(m) -
+                              __double_as_longlong(0x1.8p52));
+}
+__device__ __forceinline__ double acc_to_double(float a) { return (double)a; }
+__device__ __forceinline__ double acc_to_double(unsigned long long a) {
+  return (double)(long long)a * 0x1p-40;
+}
+
+template <typename T>
+__device__ __forceinline__ T deposit_weight_scale() {
+  return (T)1;
+}
+template <>
+__device__ __forceinline__ double deposit_weight_scale<double>() {
+  return 0x1p40;
+}
+
+__device__ __forceinline__ void atomic_acc(float* a, float v) { atomicAdd(a, v); }
+__device__ __forceinline__ void atomic_acc(unsigned long long* a,
+                                           unsigned long long v) {
+  atomicAdd(a, v);
+}
+
+__device__ __forceinline__ float shfl_up(float v, int o) {
+  return __shfl_up_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ unsigned long long shfl_up(unsigned long long v,
+                                                      int o) {
+  return __shfl_up_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ float shfl_xor(float v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ unsigned long long shfl_xor(unsigned long long v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+
+__device__ __forceinline__ int wrap(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ double kinetic(double wp, double vx, double vy,
+                                          double vz, double vol) {
+  return __dmul_rn(
+      __dmul_rn(__dmul_rn(wp, 0.5),
+                __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)),
+                          __dmul_rn(vz, vz))),
+      vol);
+}
+
+// ------------------------------------------------------------------------
+// Boris rotation, the written order: half kick, t = B dt/2,
+// s = 2 t / (1 + t.t), v' = v- + v- x t, v+ = v- + v' x s, half kick.
+// ------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void boris(T& vx, T& vy, T& vz, const T E[3],
+                                      const T B[3], T hdt) {
+  const T emx = hdt * E[0], emy = hdt * E[1], emz = hdt * E[2];
+  const T vmx = vx + emx, vmy = vy + emy, vmz = vz + emz;
+  const T tx = hdt * B[0], ty = hdt * B[1], tz = hdt * B[2];
+  const T tt = (tx * tx + ty * ty) + tz * tz;
+  const T f = (T)2 / ((T)1 + tt);
+  const T sx = f * tx, sy = f * ty, sz = f * tz;
+  const T px = vmx + (vmy * tz - vmz * ty);
+  const T py = vmy + (vmz * tx - vmx * tz);
+  const T pz = vmz + (vmx * ty - vmy * tx);
+  const T qx = vmx + (py * sz - pz * sy);
+  const T qy = vmy + (pz * sx - px * sz);
+  const T qz = vmz + (px * sy - py * sx);
+  vx = qx + emx;
+  vy = qy + emy;
+  vz = qz + emz;
+}
+
+// ------------------------------------------------------------------------
+// Faux-shock decision (Sec. 2, Eq. 1) in FP64. Returns true and overwrites v
+// when the particle is returned: P = ((1 - u2/v)/(1 + u2/v))^2 with v the
+// speed in the chosen frame (0 when v <= u2); returned iff U0 < P and the
+// downstream-frame speed |v'| = |v + u2 x| exceeds u2; the new direction has
+// mu' = a + (1 - a) sqrt(U1), a = u2/|v'| (flux-weighted, isotropic in the
+// downstream), azimuth 2 pi U2; |v'| is kept.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ bool fs_return(double& vx, double& vy, double& vz,
+                                          double u2, int frame,
+                                          unsigned long long seed,
+                                          uint32_t pid, long long step) {
+  const double sp = __dsqrt_rn(__dadd_rn(
+      __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
+  const double wx = __dadd_rn(vx, u2);
+  const double w = __dsqrt_rn(__dadd_rn(
+      __dadd_rn(__dmul_rn(wx, wx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
+  const double vp = (frame == FS_FRAME_SHOCK) ? sp : w;
+  double prob = 0.0;
+  if (vp > u2) {
+    const double a = __ddiv_rn(u2, vp);
+    const double q = __ddiv_rn(__dsub_rn(1.0, a), __dadd_rn(1.0, a));
+    prob = __dmul_rn(q, q);
+  }
+  const Philox4 r = draw4(seed, pid, step, kPurposeFS);
+  const double U0 = u01(r.x[0]), U1 = u01(r.x[1]), U2 = u01(r.x[2]);
+  if (!(U0 < prob && w > u2)) return false;
+  const double a = __ddiv_rn(u2, w);
+  const double mu = __dadd_rn(a, __dmul_rn(__dsub_rn(1.0, a), __dsqrt_rn(U1)));
+  const double sn = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(mu, mu)));
+  double c, s;
+  fs_sincos2pi(U2, &c, &s);
+  const double ws = __dmul_rn(w, sn);
+  vx = __dsub_rn(__dmul_rn(w, mu), u2);
+  vy = __dmul_rn(ws, c);
+  vz = __dmul_rn(ws, s);
+  return true;
+}
+
+// ------------------------------------------------------------------------
+// k_movers: append each leaver to its destination tile's bucket.
+// ------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_movers(DevPtrs<T> d, Geo g, int out) {
+  const int nm = min(d.ctr->mover_count, g.mover_cap);
+  const Parts<T> PO = d.P[out];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nm;
+       k += gridDim.x * blockDim.x) {
+    const int cell = d.M.cell[k];
+    const int i = cell & 0xFFFF, j = cell >> 16;
+    const int t = (j / g.TY) * g.ntx + i / g.TX;
+    const int slot = atomicAdd(&d.cnt[out][t], 1);
+    if (slot >= g.tile_cap) {
+      atomicSub(&d.cnt[out][t], 1);
+      atomicOr(&d.ctr->status, kStatusCapacity);
+      continue;
+    }
+    const int gi = d.tile_base[t] + slot;
+    PO.cell[gi] = cell;
+    PO.ox[gi] = d.M.ox[k];
+    if (DIM == 2) PO.oy[gi] = d.M.oy[k];
+    PO.vx[gi] = d.M.vx[k];
+    PO.vy[gi] = d.M.vy[k];
+    PO.vz[gi] = d.M.vz[k];
+    PO.id[gi] = d.M.id[k];
+  }
+}
+
+// Deposit of one particle into the far accumulators (global atomics).
+template <typename T, int DIM>
+__device__ __forceinline__ void deposit_far(const DevPtrs<T>& d, const Geo& g,
+                                            int i, int j, T fx, T fy, T wp,
+                                            T vx, T vy, T vz) {
+  using A = typename Num<T>::acc;
+  A* far = (A*)d.far;
+  const size_t nn = (size_t)g.nxn * g.ny;
+  const int i1 = (g.bc_x == FS_BC_PERIODIC && i + 1 == g.nx) ? 0 : i + 1;
+  if (DIM == 1) {
+    const T c0 = wp * ((T)1 - fx), c1 = wp * fx;
+    atomic_acc(&far[0 * nn + i], to_acc(c0));
+    atomic_acc(&far[1 * nn + i], to_acc(c0 * vx));
+    atomic_acc(&far[2 * nn + i], to_acc(c0 * vy));
+    atomic_acc(&far[3 * nn + i], to_acc(c0 * vz));
+    atomic_acc(&far[0 * nn + i1], to_acc(c1));
+    atomic_acc(&far[1 * nn + i1], to_acc(c1 * vx));
+    atomic_acc(&far[2 * nn + i1], to_acc(c1 * vy));
+    atomic_acc(&far[3 * nn + i1], to_acc(c1 * vz));
+  } else {
+    const int j1 = (j + 1 == g.ny) ? 0 : j + 1;
+    const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
+    const int nd[4] = {j * g.nxn + i, j * g.nxn + i1, j1 * g.nxn + i,
+                       j1 * g.nxn + i1};
+    const T cw[4] = {wp * (gx0 * gy0), wp * (fx * gy0), wp * (gx0 * fy),
+                     wp * (fx * fy)};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      atomic_acc(&far[0 * nn + nd[c]], to_acc(cw[c]));
+      atomic_acc(&far[1 * nn + nd[c]], to_acc(cw[c] * vx));
+      atomic_acc(&far[2 * nn + nd[c]], to_acc(cw[c] * vy));
+      atomic_acc(&far[3 * nn + nd[c]], to_acc(cw[c] * vz));
+    }
+  }
+}
+
+// Place one new particle into the bucket of its tile; deposit it.
+template <typename T, int DIM>
+__device__ __forceinline__ void place_new(const DevPtrs<T>& d, const Geo& g,
+                                          const Phys& ph, int buf, int i, int j,
+                                          T fx, T fy, T vx, T vy, T vz,
+                                          uint32_t id) {
+  const int t = (j / g.TY) * g.ntx + i / g.TX;
+  const int slot = atomicAdd(&d.cnt[buf][t], 1);
+  if (slot >= g.tile_cap) {
+    atomicSub(&d.cnt[buf][t], 1);
+    atomicOr(&d.ctr->status, kStatusCapacity);
+    return;
+  }
+  const int gi = d.tile_base[t] + slot;
+  const Parts<T> P = d.P[buf];
+  P.cell[gi] = (j << 16) | i;
+  P.ox[gi] = fx;
+  if (DIM == 2) P.oy[gi] = fy;
+  P.vx[gi] = vx;
+  P.vy[gi] = vy;
+  P.vz[gi] = vz;
+  P.id[gi] = id;
+  const double ws = deposit_weight_scale<T>();
+  const T wp = (T)(((id & kIdCR) ? ph.w_cr : ph.w_th) * ws);
+  deposit_far<T, DIM>(d, g, i, j, fx, fy, wp, vx, vy, vz);
+}
+
+// ------------------------------------------------------------------------
+// Injection (Sec. 2). k_inject_count (one CTA): per transverse row the
+// accumulator advances by ppc u_sh dt/dx, its integer part is this step's
+// count; a scan over rows gives each row's first id. k_inject_gen: one thread
+// per (row, slot) draws the particle.
+// ------------------------------------------------------------------------
+static __global__ void k_inject_count(double* acc, int* rowcnt, int* rowoff, int ny,
+                               double rate, int per_row_mult) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b = 0; b < ny; b += blockDim.x) {
+    const int j = b + threadIdx.x;
+    int n = 0;
+    if (j < ny) {
+      double v = __dadd_rn(acc[j], rate);
+      const double fl = floor(v);
+      n = (int)fl;
+      acc[j] = __dsub_rn(v, fl);
+      rowcnt[j] = n;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = n * per_row_mult;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      int s = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+      int si = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, si, o);
+        if (lane >= o) si += v;
+      }
+      if (lane < (int)(blockDim.x >> 5)) wsum[lane] = si - s;
+    }
+    __syncthreads();
+    if (j < ny) rowoff[j] = carry + wsum[w] + inc - n * per_row_mult;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += wsum[w] + inc;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rowoff[ny] = carry;
+}
+
+template <typename T, int DIM>
+__global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
+                             long long step, const int* rowcnt,
+                             const int* rowoff, int maxk) {
+  const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = gidx / maxk, k = gidx % maxk;
+  __shared__ unsigned long long s_first;
+  if (threadIdx.x == 0) s_first = d.ctr->next_id;
+  __syncthreads();
+  const unsigned long long first = s_first;
+  long long l_inj = 0;
+  double l_e = 0.0;
+  if (j < g.ny) {
+    const int n = rowcnt[j];
+    if (k < n) {
+      const int nx = g.nx;
+      if (ph.inject_thermal) {
+        const unsigned long long num = first + rowoff[j] + k;
+        if (num > kIdMask) {
+          atomicOr(&d.ctr->status, kStatusIdOverflow);
+        } else {
+          const uint32_t pid = (uint32_t)num;
+          const Philox4 ra = draw4(ph.seed, pid, step, kPurposeInjA);
+          const Philox4 rb = draw4(ph.seed, pid, step, kPurposeInjB);
+          double g0, g1, g2, g3;
+          gauss2(u01(ra.x[0]), u01(ra.x[1]), &g0, &g1);
+          gauss2(u01(ra.x[2]), u01(ra.x[3]), &g2, &g3);
+          const double vx = __dsub_rn(__dmul_rn(ph.vth, g0), ph.mach_a);
+          const double vy = __dmul_rn(ph.vth, g1);
+          const double vz = __dmul_rn(ph.vth, g2);
+          const double X = __dsub_rn(
+              (double)nx, __dmul_rn(__dmul_rn(u01(rb.x[0]), fabs(vx)), ph.dtdx));
+          const double ix = floor(X);
+          int i = (int)ix;
+          double fx = __dsub_rn(X, ix);
+          if (i >= nx) { i = nx - 1; fx = Num<double>::offmax; }
+          if (i < 0) { i = 0; fx = 0.0; }
+          if (fx >= 1.0) fx = Num<double>::offmax;
+          const double fy = (DIM == 2) ? u01(rb.x[1]) : 0.0;
+          T ft = (T)fx;
+          if (ft >= (T)1) ft = Num<T>::offmax;
+          T fyt = (T)fy;
+          if (fyt >= (T)1) fyt = Num<T>::offmax;
+          place_new<T, DIM>(d, g, ph, buf, i, j, ft, fyt, (T)vx, (T)vy, (T)vz, pid);
+          ++l_inj;
+          l_e = __dadd_rn(l_e, kinetic(ph.w_th, vx, vy, vz, ph.cellvol));
+        }
+      }
+      if (ph.cr_enable) {
+        const int thermal_n = ph.inject_thermal ? n : 0;
+        const unsigned long long num = first + rowoff[j] + thermal_n + k;
+        if (num > kIdMask) {
+          atomicOr(&d.ctr->status, kStatusIdOverflow);
+        } else {
+          const uint32_t pid = (uint32_t)num;
+          const Philox4 rc = draw4(ph.seed, pid, step, kPurposeInjCR);
+          const double a = __ddiv_rn(ph.u_cr, ph.p_iso);
+          const double mu =
+              __dadd_rn(a, __dmul_rn(__dsub_rn(1.0, a), __dsqrt_rn(u01(rc.x[0]))));
+          const double sn = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(mu, mu)));
+          double c, s;
+          fs_sincos2pi(u01(rc.x[1]), &c, &s);
+          const double ws = __dmul_rn(ph.p_iso, sn);
+          const double vx = __dsub_rn(__dmul_rn(ph.p_iso, mu), ph.u_cr);
+          const double vy = __dmul_rn(ws, c);
+          const double vz = __dmul_rn(ws, s);
+          const double X = __dmul_rn(__dmul_rn(u01(rc.x[2]), vx), ph.dtdx);
+          const double ix = floor(X);
+          int i = (int)ix;
+          double fx = __dsub_rn(X, ix);
+          if (i >= nx) { i = nx - 1; fx = Num<double>::offmax; }
+          if (i < 0) { i = 0; fx = 0.0; }
+          if (fx >= 1.0) fx = Num<double>::offmax;
+          const double fy = (DIM == 2) ? u01(rc.x[3]) : 0.0;
+          T ft = (T)fx;
+          if (ft >= (T)1) ft = Num<T>::offmax;
+          T fyt = (T)fy;
+          if (fyt >= (T)1) fyt = Num<T>::offmax;
+          place_new<T, DIM>(d, g, ph, buf, i, j, ft, fyt, (T)vx, (T)vy, (T)vz,
+                            pid | kIdCR);
+          ++l_inj;
+          l_e = __dadd_rn(l_e, kinetic(ph.w_cr, vx, vy, vz, ph.cellvol));
+        }
+      }
+    }
+  }
+  if (l_inj) {
+    atomicAdd(&d.ctr->injected, (unsigned long long)l_inj);
+    atomicAdd(&d.ctr->injected_energy, l_e);
+  }
+}
+
+// advance next_id by this step's total (after k_inject_gen has read it)
+static __global__ void k_inject_commit(Counters* ctr, const int* rowoff, int ny) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctr->next_id += rowoff[ny];
+}
+
+// ------------------------------------------------------------------------
+// k_moments: per node, the deposit partials of every tile whose accumulator
+// covers it (tiles in increasing row, then column order; within a tile every
+// accumulator slot that maps to the node), plus the far accumulator; then the
+// wall half-volume correction (x2 at i = 0 and i = nx in the faux-shock box),
+// the density floor and u = J / n.
+// ------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
+  using A = typename Num<T>::acc;
+  const int nn = g.nxn * g.ny;
+  const int AX = g.TX + 3, AY = (DIM == 2) ? g.TY + 3 : 1, NA = AX * AY;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nn;
+       q += gridDim.x * blockDim.x) {
+    const int i = q % g.nxn, j = q / g.nxn;
+    // candidate tile columns / rows (distinct): a tile's accumulator spans
+    // nodes i0 - 1 .. i0 + TX + 1, so tiles home - 2 .. home + 1 can cover i
+    int tcx[4], ncx = 0, tcy[4], ncy = 0;
+    {
+      const int home = min(i / g.TX, g.ntx - 1);
+      for (int dd = -2; dd <= 1; ++dd) {
+        int c = home + dd;
+        if (g.bc_x == FS_BC_PERIODIC) c = wrap(c, g.ntx);
+        else if (c < 0 || c >= g.ntx) continue;
+        bool dup = false;
+        for (int k = 0; k < ncx; ++k) dup |= (tcx[k] == c);
+        if (!dup) tcx[ncx++] = c;
+      }
+    }
+    if (DIM == 2) {
+      const int home = j / g.TY;
+      for (int dd = -2; dd <= 1; ++dd) {
+        const int c = wrap(home + dd, g.nty);
+        bool dup = false;
+        for (int k = 0; k < ncy; ++k) dup |= (tcy[k] == c);
+        if (!dup) tcy[ncy++] = c;
+      }
+    } else {
+      tcy[0] = 0;
+      ncy = 1;
+    }
+    // sort candidates ascending (fixed summation order)
+    for (int a = 0; a < ncx; ++a)
+      for (int b = a + 1; b < ncx; ++b)
+        if (tcx[b] < tcx[a]) { int t = tcx[a]; tcx[a] = tcx[b]; tcx[b] = t; }
+    for (int a = 0; a < ncy; ++a)
+      for (int b = a + 1; b < ncy; ++b)
+        if (tcy[b] < tcy[a]) { int t = tcy[a]; tcy[a] = tcy[b]; tcy[b] = t; }
+    A s[4];
+    const A* far = (const A*)d.far;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c] = far[(size_t)c * nn + q];
+    for (int yy = 0; yy < ncy; ++yy) {
+      const int ty = tcy[yy];
+      for (int xx = 0; xx < ncx; ++xx) {
+        const int tx = tcx[xx];
+        const int t = ty * g.ntx + tx;
+        const A* part = (const A*)d.partial + (size_t)t * 4 * NA;
+        for (int ay = 0; ay < AY; ++ay) {
+          if (DIM == 2 && wrap(ty * g.TY - 1 + ay, g.ny) != j) continue;
+          for (int ax = 0; ax < AX; ++ax) {
+            int gi = tx * g.TX - 1 + ax;
+            if (g.bc_x == FS_BC_PERIODIC) gi = wrap(gi, g.nx);
+            if (gi != i) continue;
+            const int k = ax + ay * AX;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s[c] += part[c * NA + k];
+          }
+        }
+      }
+    }
+    double n = acc_to_double(s[0]);
+    double jx = acc_to_double(s[1]);
+    double jy = acc_to_double(s[2]);
+    double jz = acc_to_double(s[3]);
+    T nt = (T)n, jxt = (T)jx, jyt = (T)jy, jzt = (T)jz;
+    if (g.bc_x == FS_BC_FAUXSHOCK && (i == 0 || i == g.nx)) {
+      nt = nt * (T)2; jxt = jxt * (T)2; jyt = jyt * (T)2; jzt = jzt * (T)2;
+    }
+    d.J[q] = jxt;
+    d.J[(size_t)nn + q] = jyt;
+    d.J[(size_t)2 * nn + q] = jzt;
+    const T nf = (T)ph.n_floor;
+    if (nt < nf) nt = nf;
+    d.n[q] = nt;
+    d.u[q] = jxt / nt;
+    d.u[(size_t)nn + q] = jyt / nt;
+    d.u[(size_t)2 * nn + q] = jzt / nt;
+    A* farw = (A*)d.far;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) farw[(size_t)c * nn + q] = (A)0;
+  }
+}
+
+// ------------------------------------------------------------------------
+// Ohm's law at the nodes (massless isothermal electrons, J = curl B):
+//   E = ((curl B - j_ext x) x Bbar)/n - u x Bbar - T_e grad n / n (+ eta curl B)
+// Bbar is B averaged onto the nodes; derivatives are two-point differences
+// averaged across the transverse direction; x walls use zero-gradient ghost
+// cells (and a mirrored density gradient), periodic boxes wrap.
+// With G != nullptr also packs (E, Bbar) per node, plus a ghost row ny
+// (copy of row 0) and, in a periodic box, a ghost column nx (copy of 0).
+// ------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
+                      const T* __restrict__ uN, T* __restrict__ Eo,
+                      T* __restrict__ Bbo, T* __restrict__ G, Geo g, Phys ph) {
+  const int nx = g.nx, ny = g.ny, nxn = g.nxn;
+  const int nc = nx * ny, nn = nxn * ny;
+  const T hdx = (T)ph.hdx, hdy = (T)ph.hdy, idx = (T)ph.idx, te = (T)ph.te;
+  const T jcr = (T)ph.jcr, eta = (T)ph.eta;
+  const bool per = (g.bc_x == FS_BC_PERIODIC);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nn;
+       q += gridDim.x * blockDim.x) {
+    const int i = q % nxn, j = q / nxn;
+    auto cxo = [&](int c) { return per ? wrap(c, nx) : min(max(c, 0), nx - 1); };
+    auto nxo = [&](int c) {
+      if (per) return wrap(c, nx);
+      if (c < 0) return -c;
+      if (c > nx) return 2 * nx - c;
+      return c;
+    };
+    T bbx, bby, bbz, cxv, cyv, czv, dnx, dny;
+    if (DIM == 1) {
+      const int im = cxo(i - 1), ip = cxo(i);
+      const T bmx = Bc[im], bpx = Bc[ip];
+      const T bmy = Bc[nc + im], bpy = Bc[nc + ip];
+      const T bmz = Bc[2 * nc + im], bpz = Bc[2 * nc + ip];
+      bbx = (T)0.5 * (bmx + bpx);
+      bby = (T)0.5 * (bmy + bpy);
+      bbz = (T)0.5 * (bmz + bpz);
+      const T dby = (bpy - bmy) * idx;
+      const T dbz = (bpz - bmz) * idx;
+      cxv = (T)0;
+      cyv = -dbz;
+      czv = dby;
+      dnx = (nN[nxo(i + 1)] - nN[nxo(i - 1)]) * hdx;
+      dny = (T)0;
+    } else {
+      const int im = cxo(i - 1), ip = cxo(i);
+      const int jm = wrap(j - 1, ny), jp = j;
+      const int cmm = jm * nx + im, cpm = jm * nx + ip;
+      const int cmp = jp * nx + im, cpp = jp * nx + ip;
+      T b[3][4];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        b[c][0] = Bc[c * nc + cmm];
+        b[c][1] = Bc[c * nc + cpm];
+        b[c][2] = Bc[c * nc + cmp];
+        b[c][3] = Bc[c * nc + cpp];
+      }
+      bbx = (T)0.25 * ((b[0][0] + b[0][1]) + (b[0][2] + b[0][3]));
+      bby = (T)0.25 * ((b[1][0] + b[1][1]) + (b[1][2] + b[1][3]));
+      bbz = (T)0.25 * ((b[2][0] + b[2][1]) + (b[2][2] + b[2][3]));
+      const T dxby = ((b[1][3] + b[1][1]) - (b[1][2] + b[1][0])) * hdx;
+      const T dxbz = ((b[2][3] + b[2][1]) - (b[2][2] + b[2][0])) * hdx;
+      const T dybx = ((b[0][3] + b[0][2]) - (b[0][1] + b[0][0])) * hdy;
+      const T dybz = ((b[2][3] + b[2][2]) - (b[2][1] + b[2][0])) * hdy;
+      cxv = dybz;
+      cyv = -dxbz;
+      czv = dxby - dybx;
+      dnx = (nN[j * nxn + nxo(i + 1)] - nN[j * nxn + nxo(i - 1)]) * hdx;
+      dny = (nN[wrap(j + 1, ny) * nxn + i] - nN[wrap(j - 1, ny) * nxn + i]) * hdy;
+    }
+    const T n = nN[q];
+    const T ux = uN[q], uy = uN[nn + q], uz = uN[2 * nn + q];
+    const T ax = cxv - jcr, ay = cyv, az = czv;
+    const T inv_n = (T)1 / n;
+    T ex = ((ay * bbz - az * bby) * inv_n - (uy * bbz - uz * bby)) - (te * dnx) * inv_n;
+    T ey = ((az * bbx - ax * bbz) * inv_n - (uz * bbx - ux * bbz)) - (te * dny) * inv_n;
+    T ez = (ax * bby - ay * bbx) * inv_n - (ux * bby - uy * bbx);
+    if (ph.eta != 0.0) {
+      ex = ex + eta * cxv;
+      ey = ey + eta * cyv;
+      ez = ez + eta * czv;
+    }
+    Eo[q] = ex;
+    Eo[nn + q] = ey;
+    Eo[2 * nn + q] = ez;
+    if (Bbo) {
+      Bbo[q] = bbx;
+      Bbo[nn + q] = bby;
+      Bbo[2 * nn + q] = bbz;
+    }
+    if (G) {
+      const T v[8] = {ex, ey, ez, bbx, bby, bbz, (T)0, (T)0};
+      const int gx = nx + 1;
+      auto put = [&](int gi, int gj) {
+        T* dst = G + ((size_t)gj * gx + gi) * 8;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) dst[c] = v[c];
+      };
+      put(i, j);
+      if (j == 0) put(i, ny);
+      if (per && i == 0) {
+        put(nx, j);
+        if (j == 0) put(nx, ny);
+      }
+    }
+  }
+}
+
+// Faraday at the centres, K = -curl E from the four corner nodes, and the
+// RK4 stage update:
+//   stage 1: Bsum = K;            Bs = B + (h/2) K
+//   stage 2: Bsum = Bsum + 2 K;   Bs = B + (h/2) K
+//   stage 3: Bsum = Bsum + 2 K;   Bs = B + h K
+//   stage 4: Bsum = Bsum + K;     B  = B + (h/6) Bsum
+template <typename T, int DIM>
+__global__ void k_faraday(const T* __restrict__ En, T* __restrict__ B,
+                          T* __restrict__ Bs, T* __restrict__ Bsum, int stage,
+                          Geo g, Phys ph) {
+  const int nx = g.nx, ny = g.ny, nxn = g.nxn;
+  const int nc = nx * ny, nn = nxn * ny;
+  const T hdx = (T)ph.hdx, hdy = (T)ph.hdy, idx = (T)ph.idx;
+  const T h = (T)ph.h, hh = (T)ph.hh, h6 = (T)ph.h6;
+  const bool per = (g.bc_x == FS_BC_PERIODIC);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += gridDim.x * blockDim.x) {
+    const int i = c % nx, j = c / nx;
+    const int i1 = (per && i + 1 == nx) ? 0 : i + 1;
+    T K[3];
+    if (DIM == 1) {
+      const T dxey = (En[nn + i1] - En[nn + i]) * idx;
+      const T dxez = (En[2 * nn + i1] - En[2 * nn + i]) * idx;
+      K[0] = (T)0;
+      K[1] = dxez;
+      K[2] = -dxey;
+    } else {
+      const int j1 = (j + 1 == ny) ? 0 : j + 1;
+      const int q00 = j * nxn + i, q10 = j * nxn + i1;
+      const int q01 = j1 * nxn + i, q11 = j1 * nxn + i1;
+      const T dxey = ((En[nn + q10] + En[nn + q11]) - (En[nn + q00] + En[nn + q01])) * hdx;
+      const T dxez = ((En[2 * nn + q10] + En[2 * nn + q11]) -
+                      (En[2 * nn + q00] + En[2 * nn + q01])) * hdx;
+      const T dyex = ((En[q01] + En[q11]) - (En[q00] + En[q10])) * hdy;
+      const T dyez = ((En[2 * nn + q01] + En[2 * nn + q11]) -
+                      (En[2 * nn + q00] + En[2 * nn + q10])) * hdy;
+      K[0] = -dyez;
+      K[1] = dxez;
+      K[2] = dyex - dxey;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const size_t k = (size_t)q * nc + c;
+      if (stage == 1) {
+        Bsum[k] = K[q];
+        Bs[k] = B[k] + hh * K[q];
+      } else if (stage == 2) {
+        Bsum[k] = Bsum[k] + (T)2 * K[q];
+        Bs[k] = B[k] + hh * K[q];
+      } else if (stage == 3) {
+        Bsum[k] = Bsum[k] + (T)2 * K[q];
+        Bs[k] = B[k] + h * K[q];
+      } else {
+        const T sum = Bsum[k] + K[q];
+        B[k] = B[k] + h6 * sum;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Initial load (Sec. 2 set-up): ppc particles per cell, ids in cell-major
+// order, position uniform in the cell, velocity a Maxwellian of thermal speed
+// sqrt(beta_i/2) drifting at -u_sh x.
+// ------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_init_particles(DevPtrs<T> d, Geo g, Phys ph, int buf, int ppc) {
+  const long long total = (long long)g.nx * g.ny * ppc;
+  const Parts<T> P = d.P[buf];
+  for (long long pidl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       pidl < total; pidl += (long long)gridDim.x * blockDim.x) {
+    const uint32_t pid = (uint32_t)pidl;
+    const long long cidx = pidl / ppc;
+    const int k = (int)(pidl % ppc);
+    const int i = (int)(cidx % g.nx), j = (int)(cidx / g.nx);
+    const int tx = i / g.TX, ty = j / g.TY;
+    const int t = ty * g.ntx + tx;
+    const int lc = (i - tx * g.TX) + (j - ty * g.TY) * g.TX;
+    const int gi = d.tile_base[t] + lc * ppc + k;
+    const Philox4 ra = draw4(ph.seed, pid, 0, kPurposeInitA);
+    const Philox4 rb = draw4(ph.seed, pid, 0, kPurposeInitB);
+    const double fx = u01(ra.x[0]);
+    const double fy = (DIM == 2) ? u01(ra.x[1]) : 0.0;
+    double g0, g1, g2, g3;
+    gauss2(u01(ra.x[2]), u01(ra.x[3]), &g0, &g1);
+    gauss2(u01(rb.x[0]), u01(rb.x[1]), &g2, &g3);
+    const double vx = __dsub_rn(__dmul_rn(ph.vth, g0), ph.mach_a);
+    const double vy = __dmul_rn(ph.vth, g1);
+    const double vz = __dmul_rn(ph.vth, g2);
+    T ft = (T)fx, fyt = (T)fy;
+    if (ft >= (T)1) ft = Num<T>::offmax;
+    if (fyt >= (T)1) fyt = Num<T>::offmax;
+    P.cell[gi] = (j << 16) | i;
+    P.ox[gi] = ft;
+    if (DIM == 2) P.oy[gi] = fyt;
+    P.vx[gi] = (T)vx;
+    P.vy[gi] = (T)vy;
+    P.vz[gi] = (T)vz;
+    P.id[gi] = pid;
+  }
+}
+
+// Deposit every particle of buffer buf into the far accumulators (set-up and
+// after a host injection; the per-tile partials are zero then).
+template <typename T, int DIM>
+__global__ void k_deposit_all(DevPtrs<T> d, Geo g, Phys ph, int buf) {
+  const int t = blockIdx.x;
+  const int cnt = min(d.cnt[buf][t], g.tile_cap);
+  const int base = d.tile_base[t];
+  const Parts<T> P = d.P[buf];
+  const double ws = deposit_weight_scale<T>();
+  const T wth = (T)(ph.w_th * ws), wcr = (T)(ph.w_cr * ws);
+  for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+    const int gi = base + p;
+    const int cell = P.cell[gi];
+    const uint32_t id = P.id[gi];
+    deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, P.ox[gi],
+                        DIM == 2 ? P.oy[gi] : (T)0, (id & kIdCR) ? wcr : wth,
+                        P.vx[gi], P.vy[gi], P.vz[gi]);
+  }
+}
+
+// Insert n staged particles (validated on the host) into buffer buf.
+template <typename T, int DIM>
+__global__ void k_insert_staged(DevPtrs<T> d, Parts<T> src, Geo g, int buf, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += gridDim.x * blockDim.x) {
+    const int cell = src.cell[k];
+    const int i = cell & 0xFFFF, j = cell >> 16;
+    const int t = (j / g.TY) * g.ntx + i / g.TX;
+    const int slot = atomicAdd(&d.cnt[buf][t], 1);
+    if (slot >= g.tile_cap) {
+      atomicSub(&d.cnt[buf][t], 1);
+      atomicOr(&d.ctr->status, kStatusCapacity);
+      continue;
+    }
+    const int gi = d.tile_base[t] + slot;
+    const Parts<T> P = d.P[buf];
+    P.cell[gi] = cell;
+    P.ox[gi] = src.ox[k];
+    if (DIM == 2) P.oy[gi] = src.oy[k];
+    P.vx[gi] = src.vx[k];
+    P.vy[gi] = src.vy[k];
+    P.vz[gi] = src.vz[k];
+    P.id[gi] = src.id[k];
+  }
+}
+
+// ------------------------------------------------------------------------
+// Diagnostics (FP64 sums; order of the block partial sums is not fixed).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, int DIM>
+__global__ void k_diag_particles(DevPtrs<T> d, Geo g, Phys ph, int buf) {
+  const int t = blockIdx.x;
+  const int cnt = min(d.cnt[buf][t], g.tile_cap), base = d.tile_base[t];
+  const Parts<T> P = d.P[buf];
+  double s[4] = {0, 0, 0, 0};
+  for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+    const int gi = base + p;
+    const double wp = (P.id[gi] & kIdCR) ? ph.w_cr : ph.w_th;
+    const double vx = P.vx[gi], vy = P.vy[gi], vz = P.vz[gi];
+    s[0] += kinetic(wp, vx, vy, vz, ph.cellvol);
+    s[1] += (wp * vx) * ph.cellvol;
+    s[2] += (wp * vy) * ph.cellvol;
+    s[3] += (wp * vz) * ph.cellvol;
+  }
+  __shared__ double red[4][kBlock / 32];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double v = warp_sum(s[q]);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+    atomicAdd(&d.ctr->sums[threadIdx.x], v);
+  }
+}
+
+template <typename T>
+__global__ void k_diag_field(DevPtrs<T> d, Geo g, Phys ph) {
+  const int nc = g.nx * g.ny;
+  double s = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += gridDim.x * blockDim.x) {
+    const double bx = d.B[c], by = d.B[nc + c], bz = d.B[2 * nc + c];
+    s += (0.5 * ((bx * bx + by * by) + bz * bz)) * ph.cellvol;
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&d.ctr->sums[4], s);
+}
+
+template <typename T, int DIM>
+__global__ void k_hist(DevPtrs<T> d, Geo g, Phys ph, int buf, int species) {
+  const int t = blockIdx.x;
+  const int cnt = min(d.cnt[buf][t], g.tile_cap), base = d.tile_base[t];
+  const Parts<T> P = d.P[buf];
+  const double hsx = (double)ph.hist_nx / (double)g.nx;
+  const double hsp = (double)ph.hist_np / (ph.hist_pmax - ph.hist_pmin);
+  for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+    const int gi = base + p;
+    const int cr = (P.id[gi] & kIdCR) ? 1 : 0;
+    if (species >= 0 && cr != species) continue;
+    const int cell = P.cell[gi];
+    int bx = (int)floor(((double)(cell & 0xFFFF) + (double)P.ox[gi]) * hsx);
+    bx = min(max(bx, 0), ph.hist_nx - 1);
+    const double bpd = floor(((double)P.vx[gi] - ph.hist_pmin) * hsp);
+    if (!(bpd >= 0.0 && bpd < (double)ph.hist_np)) continue;
+    atomicAdd(&d.hist[(size_t)bx * ph.hist_np + (int)bpd], 1ull);
+  }
+}
+
+// y-averaged n at nodes and |B - B0|^2 at centres (rows summed in order)
+template <typename T>
+__global__ void k_profiles(DevPtrs<T> d, Geo g, Phys ph) {
+  const int nc = g.nx * g.ny, nn = g.nxn * g.ny;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nxn;
+       i += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < g.ny; ++j) acc = acc + (double)d.n[j * g.nxn + i];
+    d.prof[i] = acc / (double)g.ny;
+    if (i < g.nx) {
+      double a2 = 0.0;
+      for (int j = 0; j < g.ny; ++j) {
+        const int c = j * g.nx + i;
+        const double dbx = (double)d.B[c] - ph.b0x;
+        const double dby = (double)d.B[nc + c] - ph.b0y;
+        const double dbz = (double)d.B[2 * nc + c] - ph.b0z;
+        a2 = a2 + ((dbx * dbx + dby * dby) + dbz * dbz);
+      }
+      d.prof[g.nxn + i] = a2 / (double)g.ny;
+    }
+  }
+  (void)nn;
+}
+
+// Grid export / import in FP64 host layout ([row][col][component]).
+template <typename T>
+__global__ void k_export_grid(const T* src, int planes, int cols, int rows,
+                              double* dst) {
+  const int n = cols * rows;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += gridDim.x * blockDim.x)
+    for (int c = 0; c < planes; ++c)
+      dst[(size_t)q * planes + c] = (double)src[(size_t)c * n + q];
+}
+
+template <typename T>
+__global__ void k_import_B(T* B, const double* src, int nc) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc;
+       q += gridDim.x * blockDim.x)
+    for (int c = 0; c < 3; ++c) B[(size_t)c * nc + q] = (T)src[(size_t)q * 3 + c];
+}
+
+// Compact every live particle of buffer buf: dst rows (fx, fy, vx, vy, vz).
+template <typename T, int DIM>
+__global__ void k_export_particles(DevPtrs<T> d, Geo g, int buf, double* dst,
+                                   int* cell_out, uint32_t* id_out,
+                                   int* count) {
+  const int t = blockIdx.x;
+  const int cnt = min(d.cnt[buf][t], g.tile_cap), base = d.tile_base[t];
+  __shared__ int sb;
+  if (threadIdx.x == 0) sb = atomicAdd(count, cnt);
+  __syncthreads();
+  const Parts<T> P = d.P[buf];
+  for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+    const int gi = base + p, o = sb + p;
+    cell_out[o] = P.cell[gi];
+    id_out[o] = P.id[gi];
+    dst[(size_t)o * 5 + 0] = (double)P.ox[gi];
+    dst[(size_t)o * 5 + 1] = DIM == 2 ? (double)P.oy[gi] : 0.0;
+    dst[(size_t)o * 5 + 2] = (double)P.vx[gi];
+    dst[(size_t)o * 5 + 3] = (double)P.vy[gi];
+    dst[(size_t)o * 5 + 4] = (double)P.vz[gi];
+  }
+}
+
+}  // namespace fsx

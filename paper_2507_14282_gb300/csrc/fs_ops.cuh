@@ -1,0 +1,274 @@
+// fs_ops.cuh -- launch side of the kernels for one arithmetic type T:
+// fills the Ops table used by the C ABI. Instantiated by fs_f32.cu and
+// fs_f64.cu (the latter compiled with -fmad=false).
+#pragma once
+#include <algorithm>
+
+#include "fs_push.cuh"
+
+namespace fsx {
+
+inline int grid_for(long long n, int block = kBlock) {
+  long long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152LL * 16) g = 152LL * 16;
+  return (int)g;
+}
+
+template <typename T, int DIM, int CH>
+cudaError_t launch_push(Sim* s, int in, long long step) {
+  constexpr int R = 8;
+  const PushLayout<T, DIM> L(s->g.TX, s->g.TY, CH);
+  static size_t attr_bytes = 0;  // largest dynamic shared memory enabled so far
+  static size_t occ_bytes = 0;
+  static int occ_blocks = 1, n_sm = 0;
+  if (L.bytes > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_push<T, DIM, CH, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L.bytes);
+    if (e != cudaSuccess) return e;
+    attr_bytes = L.bytes;
+  }
+  if (L.bytes != occ_bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, k_push<T, DIM, CH, R>,
+                                                        kBlock, L.bytes);
+    if (e != cudaSuccess) return e;
+    if (occ_blocks < 1) return cudaErrorInvalidConfiguration;
+    occ_bytes = L.bytes;
+  }
+  StepArgs a;
+  a.g = s->g;
+  a.ph = s->ph;
+  a.in = in;
+  a.out = 1 - in;
+  a.step = step;
+  const long long want = (long long)n_sm * occ_blocks;
+  const int grid = (int)std::min<long long>(want, s->g.ntiles);
+  k_push<T, DIM, CH, R><<<grid, kBlock, L.bytes, s->stream>>>(s->ptrs<T>(), a);
+  return cudaGetLastError();
+}
+
+template <typename T, int DIM>
+cudaError_t push_dispatch(Sim* s, int in, long long step) {
+  if (s->g.chunk == 1024) return launch_push<T, DIM, 1024>(s, in, step);
+  return launch_push<T, DIM, 2048>(s, in, step);
+}
+
+template <typename T>
+struct OpsImpl {
+  static DevPtrs<T> P(Sim* s) { return s->ptrs<T>(); }
+
+  static cudaError_t init_particles(Sim* s) {
+    const long long total = (long long)s->g.nx * s->g.ny * s->p.ppc;
+    if (s->g.dim == 1)
+      k_init_particles<T, 1><<<grid_for(total), kBlock, 0, s->stream>>>(P(s), s->g, s->ph, s->cur, s->p.ppc);
+    else
+      k_init_particles<T, 2><<<grid_for(total), kBlock, 0, s->stream>>>(P(s), s->g, s->ph, s->cur, s->p.ppc);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t deposit_all(Sim* s, int buf) {
+    using A = typename Num<T>::acc;
+    const size_t na = (size_t)s->g.ntiles * 4 * s->g.na;
+    cudaError_t e = cudaMemsetAsync(s->base + s->L.partial, 0, na * sizeof(A), s->stream);
+    if (e != cudaSuccess) return e;
+    if (s->g.dim == 1)
+      k_deposit_all<T, 1><<<s->g.ntiles, kBlock, 0, s->stream>>>(P(s), s->g, s->ph, buf);
+    else
+      k_deposit_all<T, 2><<<s->g.ntiles, kBlock, 0, s->stream>>>(P(s), s->g, s->ph, buf);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t moments(Sim* s) {
+    const long long nn = (long long)s->g.nxn * s->g.ny;
+    if (s->g.dim == 1)
+      k_moments<T, 1><<<grid_for(nn), kBlock, 0, s->stream>>>(P(s), s->g, s->ph);
+    else
+      k_moments<T, 2><<<grid_for(nn), kBlock, 0, s->stream>>>(P(s), s->g, s->ph);
+    return cudaGetLastError();
+  }
+
+  static void ohm(Sim* s, const T* Bc, T* Eo, T* Bbo, T* G) {
+    DevPtrs<T> d = P(s);
+    const long long nn = (long long)s->g.nxn * s->g.ny;
+    if (s->g.dim == 1)
+      k_ohm<T, 1><<<grid_for(nn), kBlock, 0, s->stream>>>(Bc, d.n, d.u, Eo, Bbo, G, s->g, s->ph);
+    else
+      k_ohm<T, 2><<<grid_for(nn), kBlock, 0, s->stream>>>(Bc, d.n, d.u, Eo, Bbo, G, s->g, s->ph);
+  }
+
+  static void faraday(Sim* s, int stage) {
+    DevPtrs<T> d = P(s);
+    const long long nc = (long long)s->g.nx * s->g.ny;
+    if (s->g.dim == 1)
+      k_faraday<T, 1><<<grid_for(nc), kBlock, 0, s->stream>>>(d.Es, d.B, d.Bs, d.Bsum, stage, s->g, s->ph);
+    else
+      k_faraday<T, 2><<<grid_for(nc), kBlock, 0, s->stream>>>(d.Es, d.B, d.Bs, d.Bsum, stage, s->g, s->ph);
+  }
+
+  static cudaError_t ohm_final(Sim* s) {
+    DevPtrs<T> d = P(s);
+    ohm(s, d.B, d.E, d.Bb, d.G);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t fields(Sim* s) {
+    DevPtrs<T> d = P(s);
+    for (int sub = 0; sub < s->p.n_sub; ++sub) {
+      ohm(s, d.B, d.Es, nullptr, nullptr);
+      faraday(s, 1);
+      ohm(s, d.Bs, d.Es, nullptr, nullptr);
+      faraday(s, 2);
+      ohm(s, d.Bs, d.Es, nullptr, nullptr);
+      faraday(s, 3);
+      ohm(s, d.Bs, d.Es, nullptr, nullptr);
+      faraday(s, 4);
+    }
+    ohm(s, d.B, d.E, d.Bb, d.G);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t step(Sim* s, int in, long long step, cudaEvent_t* ev) {
+    DevPtrs<T> d = P(s);
+    const int out = 1 - in;
+    auto mark = [&](int k) {
+      if (ev) cudaEventRecord(ev[k], s->stream);
+    };
+    cudaError_t e = cudaMemsetAsync(&d.ctr->mover_count, 0, sizeof(int), s->stream);
+    if (e != cudaSuccess) return e;
+    mark(0);
+    e = (s->g.dim == 1) ? push_dispatch<T, 1>(s, in, step) : push_dispatch<T, 2>(s, in, step);
+    if (e != cudaSuccess) return e;
+    mark(1);
+    const int mg = grid_for(s->g.mover_cap);
+    if (s->g.dim == 1)
+      k_movers<T, 1><<<std::min(mg, 152 * 4), kBlock, 0, s->stream>>>(d, s->g, out);
+    else
+      k_movers<T, 2><<<std::min(mg, 152 * 4), kBlock, 0, s->stream>>>(d, s->g, out);
+    mark(2);
+    if (s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable)) {
+      int* rowcnt = d.inj;
+      int* rowoff = rowcnt + s->g.ny;
+      const int mult = (s->ph.inject_thermal ? 1 : 0) + (s->ph.cr_enable ? 1 : 0);
+      k_inject_count<<<1, 1024, 0, s->stream>>>(d.acc, rowcnt, rowoff, s->g.ny, s->ph.rate, mult);
+      const int maxk = (int)s->ph.rate + 2;
+      const long long nthreads = (long long)s->g.ny * maxk;
+      const int blocks = (int)((nthreads + kBlock - 1) / kBlock);
+      if (s->g.dim == 1)
+        k_inject_gen<T, 1><<<blocks, kBlock, 0, s->stream>>>(d, s->g, s->ph, out, step, rowcnt, rowoff, maxk);
+      else
+        k_inject_gen<T, 2><<<blocks, kBlock, 0, s->stream>>>(d, s->g, s->ph, out, step, rowcnt, rowoff, maxk);
+      k_inject_commit<<<1, 32, 0, s->stream>>>(d.ctr, rowoff, s->g.ny);
+    }
+    mark(3);
+    e = moments(s);
+    if (e != cudaSuccess) return e;
+    mark(4);
+    e = fields(s);
+    mark(5);
+    return e;
+  }
+
+  static cudaError_t insert_staged(Sim* s, int buf, int n, bool from_movers) {
+    DevPtrs<T> d = P(s);
+    const Parts<T> src = from_movers ? d.M : d.S;
+    if (s->g.dim == 1)
+      k_insert_staged<T, 1><<<grid_for(n), kBlock, 0, s->stream>>>(d, src, s->g, buf, n);
+    else
+      k_insert_staged<T, 2><<<grid_for(n), kBlock, 0, s->stream>>>(d, src, s->g, buf, n);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t diag(Sim* s, int buf) {
+    DevPtrs<T> d = P(s);
+    cudaError_t e = cudaMemsetAsync(d.ctr->sums, 0, sizeof(d.ctr->sums), s->stream);
+    if (e != cudaSuccess) return e;
+    if (s->g.dim == 1)
+      k_diag_particles<T, 1><<<s->g.ntiles, kBlock, 0, s->stream>>>(d, s->g, s->ph, buf);
+    else
+      k_diag_particles<T, 2><<<s->g.ntiles, kBlock, 0, s->stream>>>(d, s->g, s->ph, buf);
+    k_diag_field<T><<<grid_for((long long)s->g.nx * s->g.ny), kBlock, 0, s->stream>>>(d, s->g, s->ph);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t hist(Sim* s, int buf, int species) {
+    DevPtrs<T> d = P(s);
+    cudaError_t e = cudaMemsetAsync(d.hist, 0,
+                                    sizeof(unsigned long long) * s->ph.hist_nx * s->ph.hist_np,
+                                    s->stream);
+    if (e != cudaSuccess) return e;
+    if (s->g.dim == 1)
+      k_hist<T, 1><<<s->g.ntiles, kBlock, 0, s->stream>>>(d, s->g, s->ph, buf, species);
+    else
+      k_hist<T, 2><<<s->g.ntiles, kBlock, 0, s->stream>>>(d, s->g, s->ph, buf, species);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t profiles(Sim* s) {
+    k_profiles<T><<<grid_for(s->g.nxn), kBlock, 0, s->stream>>>(P(s), s->g, s->ph);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t export_grid(Sim* s, int what, double* dst) {
+    DevPtrs<T> d = P(s);
+    const T* src = nullptr;
+    int planes = 3, cols = s->g.nxn;
+    switch (what) {
+      case FS_B: src = d.B; cols = s->g.nx; break;
+      case FS_E: src = d.E; break;
+      case FS_BBAR: src = d.Bb; break;
+      case FS_N: src = d.n; planes = 1; break;
+      case FS_J: src = d.J; break;
+      case FS_U: src = d.u; break;
+      default: return cudaErrorInvalidValue;
+    }
+    const long long n = (long long)cols * s->g.ny;
+    k_export_grid<T><<<grid_for(n), kBlock, 0, s->stream>>>(src, planes, cols, s->g.ny, dst);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t import_B(Sim* s, const double* src) {
+    const int nc = s->g.nx * s->g.ny;
+    k_import_B<T><<<grid_for(nc), kBlock, 0, s->stream>>>(P(s).B, src, nc);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t export_particles(Sim* s, int buf, double* dst, int* cell,
+                                      uint32_t* id, int* count) {
+    if (s->g.dim == 1)
+      k_export_particles<T, 1><<<s->g.ntiles, kBlock, 0, s->stream>>>(P(s), s->g, buf, dst, cell, id, count);
+    else
+      k_export_particles<T, 2><<<s->g.ntiles, kBlock, 0, s->stream>>>(P(s), s->g, buf, dst, cell, id, count);
+    return cudaGetLastError();
+  }
+
+  static Ops make() {
+    Ops o;
+    o.init_particles = init_particles;
+    o.deposit_all = deposit_all;
+    o.moments = moments;
+    o.ohm_final = ohm_final;
+    o.step = step;
+    o.fields = fields;
+    o.insert_staged = insert_staged;
+    o.diag = diag;
+    o.hist = hist;
+    o.profiles = profiles;
+    o.export_grid = export_grid;
+    o.import_B = import_B;
+    o.export_particles = export_particles;
+    return o;
+  }
+};
+
+template <typename T>
+size_t push_smem_bytes(int dim, int tx, int ty, int chunk) {
+  return dim == 1 ? PushLayout<T, 1>(tx, ty, chunk).bytes
+                  : PushLayout<T, 2>(tx, ty, chunk).bytes;
+}
+
+}  // namespace fsx

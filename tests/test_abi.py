@@ -1,0 +1,77 @@
+"""CPU-side checks of the C ABI library: it loads, exports every entry point
+include/fs.h declares, and validates parameters without touching a GPU."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fs():
+    from paper_2507_14282_gb300 import build
+    build.build()
+    from paper_2507_14282_gb300 import fs as m
+    return m
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "fs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fs_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(fs):
+    lib = fs.lib()
+    names = declared_symbols()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_defaults_and_query(fs):
+    p = fs.params_default(1)
+    assert p["dim"] == 1 and p["ny"] == 1 and p["r_comp"] == 4.0
+    s = fs.query(dim=1, nx=512, ppc=32)
+    assert s.device_bytes > 0 and s.device_bytes % s.device_alignment == 0
+    assert s.nxn == 513 and s.tiles * s.tile_x == 512
+    s2 = fs.query(dim=2, nx=256, ny=64, ppc=16, precision=fs.FS_FP32)
+    assert s2.tiles == (256 // s2.tile_x) * (64 // s2.tile_y)
+    sp = fs.query(dim=1, nx=64, ppc=8, bc_x=fs.FS_BC_PERIODIC)
+    assert sp.nxn == 64
+
+
+def test_query_scales_with_capacity(fs):
+    a = fs.query(dim=1, nx=512, ppc=32, capacity_factor=2.0)
+    b = fs.query(dim=1, nx=512, ppc=32, capacity_factor=4.0)
+    assert b.device_bytes > a.device_bytes and b.particle_capacity > a.particle_capacity
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=3), dict(nx=1), dict(dim=1, ny=4), dict(dt=0.0), dict(dx=-1.0),
+    dict(precision=7), dict(ppc=0), dict(n_sub=0), dict(bc_x=5),
+    dict(fs_mode_thermal=9), dict(n_floor=0.0), dict(capacity_factor=0.5),
+    dict(cr_enable=1, p_iso=1.0, mach_a=10.0), dict(hist_pmin=5.0, hist_pmax=1.0),
+    dict(nx=70000), dict(tile_x=3, nx=512),
+])
+def test_query_rejects_bad_parameters(fs, bad):
+    kw = dict(dim=1, nx=512, ppc=8)
+    kw.update(bad)
+    with pytest.raises(fs.FsError) as e:
+        fs.query(**kw)
+    assert e.value.code == -1
+
+
+def test_strerror_names(fs):
+    assert fs.strerror(0) == "ok"
+    assert "capacity" in fs.strerror(-2)
+    assert fs.strerror(-99) == "unknown status"
+
+
+def test_oracle_is_not_imported_by_the_package():
+    import subprocess
+    import sys
+    code = ("import sys, paper_2507_14282_gb300; "
+            "assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)")
+    subprocess.run([sys.executable, "-c", code], check=True, cwd=ROOT)

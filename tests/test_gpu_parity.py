@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+FP64: the whole state is compared bit for bit (cell indices, offsets,
+velocities, ids, per-cell binning, counters, every field and moment). FP32:
+fields and moments within relative L2 1e-5 after one step and 1e-3 after 100
+steps; integer bookkeeping exact on the GPU's own counts.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = [(0, O.GRID_B), (1, O.GRID_E), (2, O.GRID_BBAR), (3, O.GRID_N), (4, O.GRID_J),
+         (5, O.GRID_U)]
+COUNTERS = ("n_particles", "incident", "transmitted", "reflected", "escaped", "injected",
+            "next_id")
+
+
+@pytest.fixture(scope="module")
+def fs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_14282_gb300 import build
+    build.build()
+    from paper_2507_14282_gb300 import fs as m
+    return m
+
+
+def by_id(p):
+    o = np.argsort(p["id"], kind="stable")
+    return {k: v[o] for k, v in p.items()}
+
+
+def assert_state_equal(gpu, ref, fs, check_particles=True):
+    for gw, ow in GRIDS:
+        a, b = gpu.grid(gw), ref.grid(ow)
+        assert a.shape == b.shape
+        bad = np.argwhere(a != b)
+        assert bad.size == 0, (gw, bad[:5], a[tuple(bad[0])], b[tuple(bad[0])])
+    dg, dr = gpu.diag(), ref.diag()
+    for k in COUNTERS:
+        assert dg[k] == dr[k], (k, dg[k], dr[k])
+    for k in ("kinetic", "magnetic", "px", "fs_energy", "injected_energy", "removed_energy"):
+        assert dg[k] == pytest.approx(dr[k], rel=1e-12, abs=1e-12), k
+    if check_particles:
+        pg, pr = by_id(gpu.particles()), by_id(ref.particles())
+        assert pg["id"].size == pr["id"].size
+        for k in ("id", "ci", "cj", "fx", "fy", "vx", "vy", "vz"):
+            bad = np.nonzero(pg[k] != pr[k])[0]
+            assert bad.size == 0, (k, bad[:5], pg[k][bad[:3]], pr[k][bad[:3]])
+    assert np.array_equal(gpu.grid(fs.FS_PROFILE_N), ref.grid(O.GRID_PROFILE_N))
+    assert np.array_equal(gpu.grid(fs.FS_PROFILE_DB2), ref.grid(O.GRID_PROFILE_DB2))
+    assert np.array_equal(gpu.histogram(), ref.histogram(-1))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ---------------------------------------------------------------- FP64
+def test_fp64_init_matches(fs):
+    cfg = W.scaled(W.CONFIG_1D, nx=128)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    assert_state_equal(gpu, ref, fs)
+
+
+@pytest.mark.parametrize("steps", [1, 7])
+def test_fp64_1d_few_steps_bit_exact(fs, steps):
+    cfg = W.scaled(W.CONFIG_1D, nx=128)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    gpu.step(steps)
+    ref.step(steps)
+    assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_1d_config_full_1000_steps_bit_exact(fs):
+    # the 1D FP64 configuration at full size and length
+    cfg = W.CONFIG_1D
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    for chunk in (1, 99, 400, 500):
+        gpu.step(chunk)
+        ref.step(chunk)
+        assert_state_equal(gpu, ref, fs, check_particles=(chunk != 99))
+    d = gpu.diag()
+    assert d["reflected"] > 0 and d["incident"] == d["transmitted"] + d["reflected"]
+
+
+@pytest.mark.parametrize("tile", [(4, 2), (8, 4), (16, 1)])
+def test_fp64_2d_bit_exact_several_tiles(fs, tile):
+    cfg = W.scaled(W.CONFIG_2D, nx=64, ny=16, ppc=8, mach_a=10.0, theta_bn_deg=20.0,
+                   tile_x=tile[0], tile_y=tile[1])
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ocfg = {k: v for k, v in cfg.items() if k not in ("tile_x", "tile_y")}
+    ref = O.Oracle(**ocfg)
+    gpu.step(1)
+    ref.step(1)
+    assert_state_equal(gpu, ref, fs)
+    gpu.step(30)
+    ref.step(30)
+    assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_multi_chunk_tiles_bit_exact(fs):
+    # 128 cells x 32 ppc = 4096 particles per tile: several shared-memory chunks
+    cfg = W.scaled(W.CONFIG_1D, nx=256, tile_x=128)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ocfg = {k: v for k, v in cfg.items() if k != "tile_x"}
+    ref = O.Oracle(**ocfg)
+    gpu.step(20)
+    ref.step(20)
+    assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_cosmic_ray_source_and_open_thermal(fs):
+    # the paper's set-up: thermal plasma open at the faux shock, a cosmic-ray
+    # species injected at the faux shock that passes or returns (Sec. 2)
+    cfg = W.scaled(W.CONFIG_1D, nx=128, fs_mode_thermal=O.FS_OPEN, cr_enable=1,
+                   p_iso=40.0, n_cr_ratio=0.01)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    gpu.step(150)
+    ref.step(150)
+    assert_state_equal(gpu, ref, fs)
+    assert gpu.histogram(cr_only=True).sum() > 0
+    assert np.array_equal(gpu.histogram(cr_only=True), ref.histogram(1))
+    # cosmic rays stream away from the wall (no turbulence yet to return them)
+    p = gpu.particles()
+    ncr = int(((p["id"] & fs.ID_CR) != 0).sum())
+    d = gpu.diag()
+    assert ncr > 0 and d["injected"] >= 2 * ncr
+
+
+def test_fp64_downstream_frame_return(fs):
+    cfg = W.scaled(W.CONFIG_1D, nx=64, fs_speed_frame=O.FRAME_DOWNSTREAM, r_comp=3.0)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    gpu.step(60)
+    ref.step(60)
+    assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_periodic_cold_wave_bit_exact(fs):
+    # periodic box, quiet start, seeded circularly polarised mode
+    nx, ppc, k = 64, 8, 2 * np.pi / 32.0
+    cfg = dict(dim=1, nx=nx, dx=0.5, dt=0.01, ppc=ppc, init_plasma=0, bc_x=O.BC_PERIODIC,
+               mach_a=0.0, beta_i=0.0, beta_e=0.5)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    xc = (np.arange(nx) + 0.5) * 0.5
+    B = ref.grid(O.GRID_B)
+    B[0, :, 1] = 1e-2 * np.cos(k * xc)
+    B[0, :, 2] = 1e-2 * np.sin(k * xc)
+    load = W.quiet_load(nx, 1, ppc, vel=lambda x, y: np.stack(
+        [0.01 * np.sin(0.5 * k * x), 0.02 * np.cos(k * x * 0.5), 0 * x]))
+    for sim in (gpu, ref):
+        sim.load_fields(B) if sim is gpu else sim.set_B(B)
+        sim.inject(*load)
+    gpu.step(50)
+    ref.step(50)
+    assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_periodic_2d_bell_current_bit_exact(fs):
+    cfg = dict(dim=2, nx=32, ny=8, dx=0.5, dy=0.5, dt=0.01, ppc=4, bc_x=O.BC_PERIODIC,
+               mach_a=1.0, beta_i=0.5, beta_e=0.5, j_cr_ext=0.2, seed=9)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    gpu.step(40)
+    ref.step(40)
+    assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_fast_particles_far_movers(fs):
+    # particles that cross several cells (and tiles) in one step take the
+    # far-mover path; results must not change
+    cfg = dict(dim=1, nx=128, dx=0.5, dt=0.01, ppc=32, init_plasma=0, bc_x=O.BC_PERIODIC,
+               mach_a=0.0, beta_i=0.0, beta_e=0.5, tile_x=8)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ocfg = {k: v for k, v in cfg.items() if k != "tile_x"}
+    ref = O.Oracle(**ocfg)
+    rng = np.random.default_rng(5)
+    load = W.random_particles(rng, 3000, 128, 1, vscale=150.0)
+    gpu.inject(*load)
+    ref.inject(*load)
+    for _ in range(3):
+        gpu.step(5)
+        ref.step(5)
+        assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_empty_box_and_offsets_at_edges(fs):
+    cfg = dict(dim=2, nx=16, ny=8, dx=0.5, dy=0.5, dt=0.005, ppc=4, init_plasma=0,
+               mach_a=5.0, inject_thermal=0)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    gpu.step(3)
+    ref.step(3)
+    assert gpu.num_particles() == 0
+    assert_state_equal(gpu, ref, fs)
+    # particles sitting on cell edges and just below 1, moving both ways
+    ci = np.array([0, 0, 15, 15, 7, 3], np.int32)
+    cj = np.array([0, 7, 0, 7, 4, 2], np.int32)
+    fx = np.array([0.0, 1 - 2**-53, 0.0, 1 - 2**-53, 0.5, 0.0])
+    fy = np.array([0.0, 1 - 2**-53, 1 - 2**-53, 0.0, 0.5, 0.25])
+    vx = np.array([-30.0, 30.0, -1e-9, 1e-9, 0.0, -200.0])
+    vy = np.array([-5.0, 5.0, 1e-17, -1e-17, 0.0, 77.0])
+    vz = np.zeros(6)
+    gpu.inject(ci, cj, fx, fy, vx, vy, vz)
+    ref.inject(ci, cj, fx, fy, vx, vy, vz)
+    for _ in range(4):
+        gpu.step(1)
+        ref.step(1)
+        assert_state_equal(gpu, ref, fs)
+
+
+def test_capacity_overflow_is_reported_not_faulted(fs):
+    cfg = dict(dim=1, nx=32, ppc=2, capacity_factor=1.0, init_plasma=0, mach_a=0.0,
+               inject_thermal=0, tile_x=16)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    cap = gpu.sizes.particle_capacity
+    n = int(cap) + 100
+    ci = np.zeros(n, np.int32)
+    with pytest.raises(fs.FsError) as e:
+        gpu.inject(ci, ci, np.full(n, 0.5), np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n))
+    assert e.value.code == -2
+    # the handle keeps reporting the sticky error
+    with pytest.raises(fs.FsError):
+        gpu.diag()
+
+
+def test_inject_rejects_out_of_range(fs):
+    gpu = fs.FauxShock(precision=fs.FS_FP64, dim=1, nx=32, ppc=2)
+    for bad in (dict(ci=[32]), dict(ci=[-1]), dict(fx=[1.0]), dict(fx=[-0.1]),
+                dict(vx=[np.nan])):
+        a = dict(ci=[3], cj=[0], fx=[0.5], fy=[0.0], vx=[0.0], vy=[0.0], vz=[0.0])
+        a.update(bad)
+        with pytest.raises(fs.FsError) as e:
+            gpu.inject(**{k: np.array(v) for k, v in a.items()})
+        assert e.value.code == -1
+
+
+# ---------------------------------------------------------------- FP32
+@pytest.mark.parametrize("dim", [1, 2])
+def test_fp32_fields_within_tolerance(fs, dim):
+    if dim == 1:
+        cfg = W.scaled(W.CONFIG_1D, nx=256)
+    else:
+        cfg = W.scaled(W.CONFIG_2D_FP32, nx=64, ny=16, ppc=16)
+    gpu = fs.FauxShock(precision=fs.FS_FP32, **cfg)
+    ref = O.Oracle(**cfg)
+    gpu.step(1)
+    ref.step(1)
+    for gw, ow in GRIDS:
+        assert rel_l2(gpu.grid(gw), ref.grid(ow)) <= 1e-5, gw
+    gpu.step(99)
+    ref.step(99)
+    errs = {gw: rel_l2(gpu.grid(gw), ref.grid(ow)) for gw, ow in GRIDS}
+    for gw, e in errs.items():
+        assert e <= 1e-3, (gw, errs)
+    d = gpu.diag()
+    n0 = cfg["nx"] * cfg["ny"] * cfg["ppc"]
+    assert d["n_particles"] == n0 + d["injected"] - d["transmitted"] - d["escaped"]
+    assert d["incident"] == d["transmitted"] + d["reflected"]
+    dr = ref.diag()
+    assert d["injected"] == dr["injected"]
+    sd = 4 * np.sqrt(max(dr["reflected"], 1)) + 2
+    assert abs(d["reflected"] - dr["reflected"]) <= sd
