@@ -211,6 +211,38 @@ int fs_diag(fs_handle* h, fs_diag_t* out);
 int fs_profile(fs_handle* h, int enable);
 int fs_profile_read(fs_handle* h, double* ms, long long* counts, int nphases);
 
+/* Allocation-free field advance (no counterpart in the paper: an addition
+   of this library). Advances B by one particle step -- p->n_sub classical
+   RK4 substeps of dB/dt = -curl E(B), E from Ohm's law with the moments n,
+   u held fixed -- and writes E at the nodes from the advanced B: the same
+   arithmetic fs_step applies after its deposit, for a caller that holds the
+   moments and the field itself.
+   Meant for callers that cannot allocate device memory and cannot lend the
+   library scratch either: a host framework that owns every device byte
+   through its own fixed pool, or a time-critical loop that must not trigger
+   the implicit device synchronisation an allocation can cause. The RK4
+   stage buffers live in one static device array of 2^20 doubles (8 MiB)
+   that every GPU loading the library holds until the process exits; the
+   function allocates and frees nothing, and the caller passes all inputs and
+   outputs as device pointers on the current device:
+     B_in, B_out  [3][ny][nx]   centre field, one plane per component
+                                (B_out may equal B_in: advanced in place)
+     n            [ny][nxn]     ion density at the nodes (after the floor)
+     u            [3][ny][nxn]  ion bulk velocity at the nodes
+     E_out        [3][ny][nxn]  electric field at the nodes
+   nxn = nx + 1 (faux-shock box) or nx (periodic box). FP64 only.
+   Returns FS_EINVAL for a NULL pointer, FS_FP32, an invalid parameter set,
+   or a grid whose stage buffers (6 nx ny + 3 nxn ny doubles) exceed the
+   static array; FS_ECUDA when a CUDA call fails. Enqueues on cuda_stream.
+   The first call on a device looks up the array's device address (once per
+   device); make that first call before any stream capture. Every call on a
+   device shares the one array, and it keeps the last call's contents (each
+   call writes the stages before reading them): calls that overlap on the GPU
+   -- on different streams, or from different threads -- race. */
+int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
+                             const double* n, const double* u, double* B_out,
+                             double* E_out, void* cuda_stream);
+
 /* Releases the handle (host memory only). The device buffer stays the
    caller's. */
 int fs_destroy(fs_handle* h);

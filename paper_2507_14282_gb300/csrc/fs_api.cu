@@ -280,6 +280,15 @@ int redeposit(Sim* s) {
 
 }  // namespace
 
+namespace fsx {
+// Geometry and derived constants of a parameter set, without a handle (used
+// by the allocation-free field entry point).
+int derive_geometry(const fs_params* p, Geo* g, Phys* ph) {
+  Layout L;
+  return derive(p, g, ph, &L);
+}
+}  // namespace fsx
+
 struct fs_handle {
   Sim sim;
   // phase timing (fs_profile): one set of FS_NPHASES + 1 events per step

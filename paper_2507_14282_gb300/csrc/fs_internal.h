@@ -123,6 +123,7 @@ const Ops& ops_f32();
 const Ops& ops_f64();
 size_t push_smem_bytes_f32(int dim, int tx, int ty, int chunk);
 size_t push_smem_bytes_f64(int dim, int tx, int ty, int chunk);
+int derive_geometry(const fs_params* p, Geo* g, Phys* ph);
 
 struct Sim {
   fs_params p;
