@@ -120,12 +120,15 @@ int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
   g->tile_cap = (int)cap;
   g->cap_total = cap * g->ntiles;
   if (g->cap_total >= (1LL << 31) - 1) return FS_EINVAL;
-  long long mc = (long long)ceil(p->mover_fraction * (double)g->cap_total) + 1024;
-  if (mc > (1LL << 31) - 1) mc = (1LL << 31) - 1;
-  g->mover_cap = (int)mc;
+  long long mpt = (long long)ceil(p->mover_fraction * (double)cap) + 32;
+  mpt = (mpt + 31) / 32 * 32;
+  if (mpt * g->ntiles >= (1LL << 31) - 1) return FS_EINVAL;
+  g->mover_per_tile = (int)mpt;
+  g->mover_cap = (int)(mpt * g->ntiles);
   g->staging_cap = 1 << 16;
-  // shared-memory chunk: 1024 particles, or 2048 when the mean tile is larger
-  g->chunk = (cells_per_tile * p->ppc > 700) ? 2048 : 1024;
+  // shared-memory chunk: 512 particles (deeper prefetch pipeline) when the
+  // mean tile holds at most 256, else 1024
+  g->chunk = (cells_per_tile * p->ppc > 256) ? 1024 : 512;
   g->na = (tx + 3) * (p->dim == 2 ? ty + 3 : 1);
   g->nk = (tx + 2) * (p->dim == 2 ? ty + 2 : 1) + 2;
   const size_t smem = (p->precision == FS_FP64)
@@ -197,6 +200,7 @@ int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
   L->tile_base = take(4 * (size_t)g->ntiles);
   L->cnt[0] = take(4 * (size_t)g->ntiles);
   L->cnt[1] = take(4 * (size_t)g->ntiles);
+  L->mcnt = take(4 * (size_t)g->ntiles);
   const size_t nc = (size_t)p->nx * p->ny, nn = (size_t)g->nxn * p->ny;
   L->B = take(3 * T * nc);
   L->Bs = take(3 * T * nc);

@@ -174,27 +174,33 @@ __device__ __forceinline__ bool fs_return(double& vx, double& vy, double& vz,
 // ------------------------------------------------------------------------
 template <typename T, int DIM>
 __global__ void k_movers(DevPtrs<T> d, Geo g, int out) {
-  const int nm = min(d.ctr->mover_count, g.mover_cap);
+  // one warp per source tile: its leavers go to their destination tiles
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
   const Parts<T> PO = d.P[out];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nm;
-       k += gridDim.x * blockDim.x) {
-    const int cell = d.M.cell[k];
-    const int i = cell & 0xFFFF, j = cell >> 16;
-    const int t = (j / g.TY) * g.ntx + i / g.TX;
-    const int slot = atomicAdd(&d.cnt[out][t], 1);
-    if (slot >= g.tile_cap) {
-      atomicSub(&d.cnt[out][t], 1);
-      atomicOr(&d.ctr->status, kStatusCapacity);
-      continue;
+  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < g.ntiles; t += gridDim.x * wpb) {
+    const int nm = d.mcnt[t];
+    const int mb = t * g.mover_per_tile;
+    for (int k = lane; k < nm; k += 32) {
+      const int src = mb + k;
+      const int cell = d.M.cell[src];
+      const int i = cell & 0xFFFF, j = cell >> 16;
+      const int dt = (j / g.TY) * g.ntx + i / g.TX;
+      const int slot = atomicAdd(&d.cnt[out][dt], 1);
+      if (slot >= g.tile_cap) {
+        atomicSub(&d.cnt[out][dt], 1);
+        atomicOr(&d.ctr->status, kStatusCapacity);
+        continue;
+      }
+      const int gi = d.tile_base[dt] + slot;
+      PO.cell[gi] = cell;
+      PO.ox[gi] = d.M.ox[src];
+      if (DIM == 2) PO.oy[gi] = d.M.oy[src];
+      PO.vx[gi] = d.M.vx[src];
+      PO.vy[gi] = d.M.vy[src];
+      PO.vz[gi] = d.M.vz[src];
+      PO.id[gi] = d.M.id[src];
     }
-    const int gi = d.tile_base[t] + slot;
-    PO.cell[gi] = cell;
-    PO.ox[gi] = d.M.ox[k];
-    if (DIM == 2) PO.oy[gi] = d.M.oy[k];
-    PO.vx[gi] = d.M.vx[k];
-    PO.vy[gi] = d.M.vy[k];
-    PO.vz[gi] = d.M.vz[k];
-    PO.id[gi] = d.M.id[k];
   }
 }
 
@@ -462,16 +468,22 @@ __global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
     for (int c = 0; c < 4; ++c) s[c] = far[(size_t)c * nn + q];
     for (int yy = 0; yy < ncy; ++yy) {
       const int ty = tcy[yy];
-      for (int xx = 0; xx < ncx; ++xx) {
-        const int tx = tcx[xx];
-        const int t = ty * g.ntx + tx;
-        const A* part = (const A*)d.partial + (size_t)t * 4 * NA;
-        for (int ay = 0; ay < AY; ++ay) {
-          if (DIM == 2 && wrap(ty * g.TY - 1 + ay, g.ny) != j) continue;
-          for (int ax = 0; ax < AX; ++ax) {
-            int gi = tx * g.TX - 1 + ax;
-            if (g.bc_x == FS_BC_PERIODIC) gi = wrap(gi, g.nx);
-            if (gi != i) continue;
+      // accumulator rows of node row j (more than one only when the box is
+      // narrower than a tile's accumulator)
+      int ay0 = 0;
+      if (DIM == 2) ay0 = wrap(j - (ty * g.TY - 1), g.ny);
+      for (int ay = ay0; ay < AY; ay += (DIM == 2 ? g.ny : AY)) {
+        for (int xx = 0; xx < ncx; ++xx) {
+          const int tx = tcx[xx];
+          const int t = ty * g.ntx + tx;
+          const A* part = (const A*)d.partial + (size_t)t * 4 * NA;
+          int ax0 = i - (tx * g.TX - 1);
+          int step = AX;
+          if (g.bc_x == FS_BC_PERIODIC) {
+            ax0 = wrap(ax0, g.nx);
+            step = g.nx;
+          }
+          for (int ax = ax0; ax >= 0 && ax < AX; ax += step) {
             const int k = ax + ay * AX;
 #pragma unroll
             for (int c = 0; c < 4; ++c) s[c] += part[c * NA + k];

@@ -55,7 +55,8 @@ struct Geo {
   int chunk;                // particles per shared-memory chunk in the push
   int tile_cap;             // particle slots per tile
   long long cap_total;      // ntiles * tile_cap
-  int mover_cap;            // mover-list slots
+  int mover_per_tile;       // mover-list slots of each tile
+  int mover_cap;            // mover-list slots: ntiles * mover_per_tile
   int staging_cap;          // host-injection staging slots
   int na;                   // accumulator nodes per tile: (TX+3)*(TY+3) or TX+3
   int nk;                   // sort keys per tile
@@ -75,7 +76,7 @@ struct Phys {
 // Byte offsets of every region inside the caller's device buffer.
 struct Layout {
   size_t part[2][7], mov[7], stg[7];
-  size_t tile_base, cnt[2];
+  size_t tile_base, cnt[2], mcnt;
   size_t B, Bs, Bsum, E, Es, Bb, G, n, u, J;
   size_t partial, far, acc, inj, ctr, hist, prof;
   size_t total;
@@ -87,6 +88,7 @@ struct DevPtrs {
   Parts<T> P[2], M, S;
   int* tile_base;
   int* cnt[2];
+  int* mcnt;      // movers written by each tile this step
   T *B, *Bs, *Bsum, *E, *Es, *Bb, *G, *n, *u, *J;
   void* partial;   // float accumulators (FP32) or int64 fixed point (FP64)
   void* far;
@@ -164,6 +166,7 @@ inline DevPtrs<T> Sim::ptrs(int) const {
   d.tile_base = (int*)(base + L.tile_base);
   d.cnt[0] = (int*)(base + L.cnt[0]);
   d.cnt[1] = (int*)(base + L.cnt[1]);
+  d.mcnt = (int*)(base + L.mcnt);
   d.B = (T*)(base + L.B);
   d.Bs = (T*)(base + L.Bs);
   d.Bsum = (T*)(base + L.Bsum);

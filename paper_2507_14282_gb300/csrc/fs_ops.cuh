@@ -15,15 +15,14 @@ inline int grid_for(long long n, int block = kBlock) {
   return (int)g;
 }
 
-template <typename T, int DIM, int CH>
+template <typename T, int DIM, int CH, int NS>
 cudaError_t launch_push(Sim* s, int in, long long step) {
-  constexpr int R = 8;
-  const PushLayout<T, DIM> L(s->g.TX, s->g.TY, CH);
+  const PushLayout<T, DIM> L(s->g.TX, s->g.TY, CH, NS);
   static size_t attr_bytes = 0;  // largest dynamic shared memory enabled so far
   static size_t occ_bytes = 0;
   static int occ_blocks = 1, n_sm = 0;
   if (L.bytes > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_push<T, DIM, CH, R>,
+    cudaError_t e = cudaFuncSetAttribute(k_push<T, DIM, CH, NS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L.bytes);
     if (e != cudaSuccess) return e;
@@ -34,7 +33,7 @@ cudaError_t launch_push(Sim* s, int in, long long step) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, k_push<T, DIM, CH, R>,
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, k_push<T, DIM, CH, NS>,
                                                         kBlock, L.bytes);
     if (e != cudaSuccess) return e;
     if (occ_blocks < 1) return cudaErrorInvalidConfiguration;
@@ -48,14 +47,30 @@ cudaError_t launch_push(Sim* s, int in, long long step) {
   a.step = step;
   const long long want = (long long)n_sm * occ_blocks;
   const int grid = (int)std::min<long long>(want, s->g.ntiles);
-  k_push<T, DIM, CH, R><<<grid, kBlock, L.bytes, s->stream>>>(s->ptrs<T>(), a);
+  k_push<T, DIM, CH, NS><<<grid, kBlock, L.bytes, s->stream>>>(s->ptrs<T>(), a);
   return cudaGetLastError();
 }
 
+// shared-memory chunk (particles) and pipeline stages per precision
+template <typename T>
+struct PushShape;
+template <>
+struct PushShape<float> {
+  static constexpr int kChunkSmall = 512, kStagesSmall = 4;
+  static constexpr int kChunkLarge = 1024, kStagesLarge = 2;
+};
+template <>
+struct PushShape<double> {
+  static constexpr int kChunkSmall = 512, kStagesSmall = 3;
+  static constexpr int kChunkLarge = 1024, kStagesLarge = 2;
+};
+
 template <typename T, int DIM>
 cudaError_t push_dispatch(Sim* s, int in, long long step) {
-  if (s->g.chunk == 1024) return launch_push<T, DIM, 1024>(s, in, step);
-  return launch_push<T, DIM, 2048>(s, in, step);
+  using S = PushShape<T>;
+  if (s->g.chunk == S::kChunkSmall)
+    return launch_push<T, DIM, S::kChunkSmall, S::kStagesSmall>(s, in, step);
+  return launch_push<T, DIM, S::kChunkLarge, S::kStagesLarge>(s, in, step);
 }
 
 template <typename T>
@@ -138,17 +153,16 @@ struct OpsImpl {
     auto mark = [&](int k) {
       if (ev) cudaEventRecord(ev[k], s->stream);
     };
-    cudaError_t e = cudaMemsetAsync(&d.ctr->mover_count, 0, sizeof(int), s->stream);
-    if (e != cudaSuccess) return e;
     mark(0);
+    cudaError_t e;
     e = (s->g.dim == 1) ? push_dispatch<T, 1>(s, in, step) : push_dispatch<T, 2>(s, in, step);
     if (e != cudaSuccess) return e;
     mark(1);
-    const int mg = grid_for(s->g.mover_cap);
+    const int mg = std::min((s->g.ntiles + 7) / 8, 152 * 16);
     if (s->g.dim == 1)
-      k_movers<T, 1><<<std::min(mg, 152 * 4), kBlock, 0, s->stream>>>(d, s->g, out);
+      k_movers<T, 1><<<mg, kBlock, 0, s->stream>>>(d, s->g, out);
     else
-      k_movers<T, 2><<<std::min(mg, 152 * 4), kBlock, 0, s->stream>>>(d, s->g, out);
+      k_movers<T, 2><<<mg, kBlock, 0, s->stream>>>(d, s->g, out);
     mark(2);
     if (s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable)) {
       int* rowcnt = d.inj;
@@ -267,8 +281,10 @@ struct OpsImpl {
 
 template <typename T>
 size_t push_smem_bytes(int dim, int tx, int ty, int chunk) {
-  return dim == 1 ? PushLayout<T, 1>(tx, ty, chunk).bytes
-                  : PushLayout<T, 2>(tx, ty, chunk).bytes;
+  using S = PushShape<T>;
+  const int ns = (chunk == S::kChunkSmall) ? S::kStagesSmall : S::kStagesLarge;
+  return dim == 1 ? PushLayout<T, 1>(tx, ty, chunk, ns).bytes
+                  : PushLayout<T, 2>(tx, ty, chunk, ns).bytes;
 }
 
 }  // namespace fsx

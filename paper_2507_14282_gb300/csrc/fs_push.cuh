@@ -9,13 +9,15 @@
 //   2. push every particle in shared memory in place and give it a sort key:
 //      its new cell in the tile (interior cells first), a halo cell, FAR
 //      (moved more than one cell out of the tile) or REMOVED;
-//   3. counting sort: per-key counts -> offsets -> a permutation (no copy of
-//      the records);
-//   4. deposit: runs of at most R sorted particles of one cell are summed in
-//      registers, a warp segmented reduction combines runs of the same cell,
-//      and one lane per segment adds to the tile's node accumulator;
-//   5. stayers are written to the tile's bucket of the output buffer in cell
-//      order, leavers to the mover list.
+//   3. deposit in push order, warp-cooperatively: the particles of a warp
+//      mostly share one cell, and for each distinct cell a transpose
+//      reduction of the lanes' corner contributions leaves one sum per value
+//      to add to the tile's node accumulator;
+//   4. counting sort: per-key counts and in-key ranks -> offsets by a warp
+//      scan;
+//   5. every thread writes its own particles at offset + rank: stayers to the
+//      tile's bucket of the output buffer in cell order, leavers to the
+//      tile's range of the mover list.
 // When a tile's last chunk is done its node accumulator is written out as
 // the tile's deposit partial (summed per node in a fixed order later).
 #pragma once
@@ -63,6 +65,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// 4-byte asynchronous global -> shared copy (no register holds the value)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // bounded wait: false if the phase did not complete within the limit
 constexpr int kWaitLimit = 1 << 20;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
@@ -79,11 +91,14 @@ struct StepArgs {
 };
 
 // ---------------------------------------------------------------- layout
+constexpr int kMaxStages = 4;
+
 template <typename T, int DIM>
 struct PushLayout {
-  int TX, TY, NFX, NFY, AX, AY, NA, EX, EY, NE, NINT, NK, CH;
-  size_t F[2], cell[2], ox[2], oy[2], vx[2], vy[2], vz[2], id[2];
-  size_t key, perm, acc, kc, ko, ro, e2k, k2e, desc, bar, bytes;
+  int TX, TY, NFX, NFY, AX, AY, NA, EX, EY, NE, NINT, NK, CH, NS;
+  // stage 0's regions; stage b sits b * bstride bytes further
+  size_t F[1], cell[1], ox[1], oy[1], vx[1], vy[1], vz[1], id[1];
+  size_t acc, kc, ko, e2k, k2e, desc, bar, pf, bytes;
   size_t bstride;  // distance between the two chunk buffers
   __host__ __device__ static size_t take(size_t& o, size_t n) {
     o = (o + 15) / 16 * 16;
@@ -91,7 +106,7 @@ struct PushLayout {
     o += n;
     return r;
   }
-  __host__ __device__ PushLayout(int tx_, int ty_, int ch) {
+  __host__ __device__ PushLayout(int tx_, int ty_, int ch, int ns) {
     TX = tx_;
     TY = (DIM == 2) ? ty_ : 1;
     NFX = TX + 1;
@@ -105,26 +120,25 @@ struct PushLayout {
     NINT = TX * TY;
     NK = NE + 2;
     CH = ch;
+    NS = ns;
     size_t o = 0;
-    bar = take(o, 2 * sizeof(unsigned long long));
-    desc = take(o, 2 * sizeof(int4));
-    for (int b = 0; b < 2; ++b) {
-      F[b] = take(o, sizeof(T) * 8 * NFX * NFY);
-      cell[b] = take(o, sizeof(int) * CH);
-      ox[b] = take(o, sizeof(T) * CH);
-      oy[b] = take(o, DIM == 2 ? sizeof(T) * CH : 0);
-      vx[b] = take(o, sizeof(T) * CH);
-      vy[b] = take(o, sizeof(T) * CH);
-      vz[b] = take(o, sizeof(T) * CH);
-      id[b] = take(o, sizeof(uint32_t) * CH);
-    }
-    bstride = F[1] - F[0];
-    key = take(o, sizeof(uint16_t) * CH);
-    perm = take(o, sizeof(uint16_t) * CH);
+    bar = take(o, kMaxStages * sizeof(unsigned long long));
+    desc = take(o, (kMaxStages + 1) * sizeof(int4));
+    F[0] = take(o, sizeof(T) * 8 * NFX * NFY);
+    cell[0] = take(o, sizeof(int) * CH);
+    ox[0] = take(o, sizeof(T) * CH);
+    oy[0] = take(o, DIM == 2 ? sizeof(T) * CH : 0);
+    vx[0] = take(o, sizeof(T) * CH);
+    vy[0] = take(o, sizeof(T) * CH);
+    vz[0] = take(o, sizeof(T) * CH);
+    id[0] = take(o, sizeof(uint32_t) * CH);
+    o = (o + 15) / 16 * 16;
+    bstride = o - F[0];
+    o += (size_t)(NS - 1) * bstride;
+    pf = take(o, 16);
     acc = take(o, sizeof(typename Num<T>::acc) * 4 * NA);
     kc = take(o, sizeof(int) * NK);
     ko = take(o, sizeof(int) * (NK + 1));
-    ro = take(o, sizeof(int) * (NE + 1));
     e2k = take(o, sizeof(uint16_t) * NE);
     k2e = take(o, sizeof(int) * NE);
     bytes = (o + 127) / 128 * 128;
@@ -160,13 +174,18 @@ __device__ __forceinline__ void warp_scan_excl(const int* in, int* out, int n,
 
 // The chunk after c = {tile, first particle, count, tile count} for a CTA
 // that owns tiles blockIdx.x, blockIdx.x + G, ...; tile >= ntiles: done.
+// pf[0] holds the count of tile c.x + G, copied asynchronously into shared
+// memory one tile transition earlier; the count of the tile after it is
+// requested now.
 __device__ __forceinline__ int4 next_chunk(int4 c, int G, int ntiles, int CH,
-                                           const int* cnt_in, int cap) {
+                                           const int* cnt_in, int cap, int* pf) {
   if (c.x >= ntiles) return c;
   if (c.y + CH < c.w) return make_int4(c.x, c.y + CH, min(CH, c.w - c.y - CH), c.w);
   const int t = c.x + G;
   if (t >= ntiles) return make_int4(ntiles, 0, 0, 0);
-  const int n = min(cnt_in[t], cap);
+  cp_async_wait_all();
+  const int n = min(pf[0], cap);
+  if (t + G < ntiles) cp_async4(pf, cnt_in + t + G);
   return make_int4(t, 0, min(CH, n), n);
 }
 
@@ -337,25 +356,100 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
   bulk_g2s(sm + L.id[0] + bo, PI.id + first, 4 * m4, bar);
 }
 
-template <typename T, int DIM, int CH, int R>
+// Warp-cooperative CIC deposit of the lanes' particles (push order): for each
+// distinct cell key among the lanes, the lanes of that cell contribute their
+// corner values and a transpose reduction leaves value q(L) summed over the
+// warp in lane L; the owner lanes add to the tile's node accumulator.
+template <typename T, int DIM>
+__device__ __forceinline__ void warp_deposit(typename Num<T>::acc* ACC, int NA, int AX,
+                                             const int* k2e, int key, bool active, T fx,
+                                             T fy, T wp, T vx, T vy, T vz, int lane) {
+  using A = typename Num<T>::acc;
+  constexpr int NV = 4 * (DIM == 2 ? 4 : 2);
+  unsigned todo = __ballot_sync(0xffffffffu, active);
+  if (!todo) return;
+  A val[NV];
+  if (DIM == 1) {
+    const T c0 = wp * ((T)1 - fx), c1 = wp * fx;
+    val[0] = to_acc(c0); val[1] = to_acc(c0 * vx);
+    val[2] = to_acc(c0 * vy); val[3] = to_acc(c0 * vz);
+    val[4] = to_acc(c1); val[5] = to_acc(c1 * vx);
+    val[6] = to_acc(c1 * vy); val[7] = to_acc(c1 * vz);
+  } else {
+    const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
+    const T cw[4] = {wp * (gx0 * gy0), wp * (fx * gy0), wp * (gx0 * fy), wp * (fx * fy)};
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      val[4 * cc + 0] = to_acc(cw[cc]);
+      val[4 * cc + 1] = to_acc(cw[cc] * vx);
+      val[4 * cc + 2] = to_acc(cw[cc] * vy);
+      val[4 * cc + 3] = to_acc(cw[cc] * vz);
+    }
+  }
+  int qi = 0;
+  {
+    int h = NV / 2, off = 16;
+    while (h >= 1) {
+      if (lane & off) qi += h;
+      h >>= 1;
+      off >>= 1;
+    }
+  }
+  const bool owner = (NV == 16) ? ((lane & 1) == 0) : ((lane & 3) == 0);
+  while (todo) {
+    const int lead = __ffs(todo) - 1;
+    const int kk = __shfl_sync(0xffffffffu, key, lead);
+    const bool mine = active && (key == kk);
+    todo &= ~__ballot_sync(0xffffffffu, mine);
+    A w[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) w[q] = mine ? val[q] : (A)0;
+    int half = NV / 2;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      if (half >= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int q = 0; q < NV / 2; ++q) {
+          if (q < half) {
+            const A send = up ? w[q] : w[q + half];
+            const A keep = up ? w[q + half] : w[q];
+            w[q] = keep + shfl_xor(send, off);
+          }
+        }
+        half >>= 1;
+      } else {
+        w[0] = w[0] + shfl_xor(w[0], off);
+      }
+    }
+    if (owner) {
+      const int le = k2e[kk];
+      const int a00 = (le & 0xFFFF) + (le >> 16) * AX;
+      const int corner = qi >> 2, qty = qi & 3;
+      const int an = (DIM == 1) ? a00 + corner : a00 + (corner & 1) + (corner >> 1) * AX;
+      atomic_acc(&ACC[qty * NA + an], w[0]);
+    }
+  }
+}
+
+template <typename T, int DIM, int CH, int NS>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPtrs<T> d, StepArgs a) {
   using A = typename Num<T>::acc;
   constexpr int PPT = CH / kBlock;
   extern __shared__ __align__(128) unsigned char sm[];
   const Geo g = a.g;
   const Phys ph = a.ph;
-  const PushLayout<T, DIM> L(g.TX, g.TY, CH);
+  const PushLayout<T, DIM> L(g.TX, g.TY, CH, NS);
   const int TX = L.TX, TY = L.TY, EX = L.EX, EY = L.EY, NE = L.NE, NINT = L.NINT,
             NK = L.NK, NA = L.NA, AX = L.AX;
   uint64_t* bar = (uint64_t*)(sm + L.bar);
   int4* desc = (int4*)(sm + L.desc);
-  uint16_t* skey = (uint16_t*)(sm + L.key);
-  uint16_t* perm = (uint16_t*)(sm + L.perm);
   A* ACC = (A*)(sm + L.acc);
   int* kcount = (int*)(sm + L.kc);
   int* koff = (int*)(sm + L.ko);
   uint16_t* e2k = (uint16_t*)(sm + L.e2k);
   int* k2e = (int*)(sm + L.k2e);
+  int* pf = (int*)(sm + L.pf);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
   const int* cnt_in = d.cnt[a.in];
@@ -386,41 +480,46 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
   for (int k = tid; k < NK; k += kBlock) kcount[k] = 0;
 
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < NS; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
   }
   __syncthreads();
   if (tid == 0) {
-    int4 c0;
+    // prologue: the CTA's first NS chunks, one per stage
+    int4 c;
     if ((int)blockIdx.x < g.ntiles) {
       const int n = min(cnt_in[blockIdx.x], g.tile_cap);
-      c0 = make_int4(blockIdx.x, 0, min(CH, n), n);
+      c = make_int4(blockIdx.x, 0, min(CH, n), n);
     } else {
-      c0 = make_int4(g.ntiles, 0, 0, 0);
+      c = make_int4(g.ntiles, 0, 0, 0);
     }
-    issue_chunk<T, DIM>(sm, L, 0, c0, d, PI, g);
-    issue_chunk<T, DIM>(sm, L, 1, next_chunk(c0, G, g.ntiles, CH, cnt_in, g.tile_cap), d,
-                        PI, g);
+    if ((int)blockIdx.x + G < g.ntiles) cp_async4(pf, cnt_in + blockIdx.x + G);
+    for (int b = 0; b < NS; ++b) {
+      issue_chunk<T, DIM>(sm, L, b, c, d, PI, g);
+      if (b + 1 < NS) c = next_chunk(c, G, g.ntiles, CH, cnt_in, g.tile_cap, pf);
+    }
+    *(int4*)(sm + L.desc + NS * sizeof(int4)) = c;  // the last chunk issued
   }
   __syncthreads();
 
-  uint32_t parity0 = 0, parity1 = 0;
-  int outRun = 0;
+  uint32_t parity = 0;  // bit b: phase parity expected next on stage b
+  int outRun = 0, movRun = 0;
   PushTally tl = {0, 0, 0, 0, 0.0, 0.0, 0};
 
-  for (int k = 0;; ++k) {
-    const int b = k & 1;
+  for (int b = 0;; b = (b + 1 == NS) ? 0 : b + 1) {
     const int4 c = desc[b];
     if (c.x >= g.ntiles) break;
     const int t = c.x, m = c.z;
     if (m > 0) {
-      const bool ok = mbar_wait(&bar[b], b ? parity1 : parity0);
-      if (b) parity1 ^= 1u; else parity0 ^= 1u;
+      const bool ok = mbar_wait(&bar[b], (parity >> b) & 1u);
+      parity ^= 1u << b;
       if (__syncthreads_or(!ok)) {
         if (tid == 0) {
           atomicOr(&d.ctr->status, kStatusTimeout);
-          mbar_wait(&bar[b ^ 1], b ? parity0 : parity1);
+          // let the other stages' copies land before the CTA exits (bounded)
+          for (int o = 0; o < NS; ++o)
+            if (o != b && desc[o].x < g.ntiles && desc[o].z > 0)
+              mbar_wait(&bar[o], (parity >> o) & 1u);
         }
         return;
       }
@@ -437,20 +536,27 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
     T* svz = (T*)(sm + L.vz[0] + bo);
     uint32_t* sid = (uint32_t*)(sm + L.id[0] + bo);
 
-    // ---- push in place, key and rank
-    int rk[PPT];
+    // ---- push in place, deposit (warp-cooperative, push order), key, rank
+    int rk[PPT], ky[PPT];
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
       const int p = tid + r * kBlock;
       rk[r] = 0;
+      ky[r] = NE + 1;
+      if (r * kBlock >= m) continue;  // whole block past the chunk: uniform skip
+      int key = NE + 1;
+      T fx = (T)0, fy = (T)0, vx = (T)0, vy = (T)0, vz = (T)0;
+      uint32_t id = 0;
       if (p < m) {
         int cell = sc[p];
-        T fx = sx[p], fy = (DIM == 2) ? sy[p] : (T)0;
-        T vx = svx[p], vy = svy[p], vz = svz[p];
-        uint32_t id = sid[p];
-        const int key = push_one<T, DIM>(F, L.NFX, cell, fx, fy, vx, vy, vz, id, i0, j0,
-                                         TX, TY, EX, EY, NE, e2k, g, ph, dtdx, dtdy, hdt,
-                                         a.step, tl);
+        fx = sx[p];
+        fy = (DIM == 2) ? sy[p] : (T)0;
+        vx = svx[p];
+        vy = svy[p];
+        vz = svz[p];
+        id = sid[p];
+        key = push_one<T, DIM>(F, L.NFX, cell, fx, fy, vx, vy, vz, id, i0, j0, TX, TY, EX,
+                               EY, NE, e2k, g, ph, dtdx, dtdy, hdt, a.step, tl);
         sc[p] = cell;
         sx[p] = fx;
         if (DIM == 2) sy[p] = fy;
@@ -458,142 +564,44 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
         svy[p] = vy;
         svz[p] = vz;
         sid[p] = id;
-        skey[p] = (uint16_t)key;
         rk[r] = atomicAdd(&kcount[key], 1);
+        ky[r] = key;
+        if (key == NE) {  // far mover: deposit straight to the global far sums
+          deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, fx, fy,
+                              (id & kIdCR) ? wcr : wth, vx, vy, vz);
+        }
       }
+      const T wp = (id & kIdCR) ? wcr : wth;
+      warp_deposit<T, DIM>(ACC, NA, AX, k2e, key, key < NE, fx, fy, wp, vx, vy, vz, lane);
     }
     __syncthreads();
-    __shared__ int s_mb;
-    if (warp == 0) {
-      warp_scan_excl(kcount, koff, NK, lane);
-      __syncwarp();
-      if (lane == 0) {
-        const int Lv0 = koff[NE + 1] - koff[NINT];
-        s_mb = Lv0 > 0 ? atomicAdd(&d.ctr->mover_count, Lv0) : 0;
-      }
-    }
+    if (warp == 0) warp_scan_excl(kcount, koff, NK, lane);
     __syncthreads();
+
+    // ---- write: stayers to the tile's bucket in cell order, leavers to the
+    //      tile's range of the mover list
+    const int S = koff[NINT];
+    const int Lv = koff[NE + 1] - S;
+    const int obase = d.tile_base[t] + outRun;
+    const int mbase = t * g.mover_per_tile + movRun;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
       const int p = tid + r * kBlock;
-      if (p < m) perm[koff[skey[p]] + rk[r]] = (uint16_t)p;
-    }
-    __syncthreads();
-
-    // ---- deposit: one sorted particle per lane; for each distinct cell in
-    //      the warp, a transpose reduction of its corner contributions
-    {
-      const int ndep = koff[NE];  // particles that stay within the halo
-      for (int pb = warp * 32; pb < ndep; pb += kBlock) {
-        const int pos = pb + lane;
-        int key = -1;
-        constexpr int NV = 4 * (DIM == 2 ? 4 : 2);
-        A val[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) val[q] = (A)0;
-        if (pos < ndep) {
-          const int p = perm[pos];
-          key = skey[p];
-          const T fx = sx[p];
-          const T wp = (sid[p] & kIdCR) ? wcr : wth;
-          const T vx = svx[p], vy = svy[p], vz = svz[p];
-          if (DIM == 1) {
-            const T c0 = wp * ((T)1 - fx), c1 = wp * fx;
-            val[0] = to_acc(c0); val[1] = to_acc(c0 * vx);
-            val[2] = to_acc(c0 * vy); val[3] = to_acc(c0 * vz);
-            val[4] = to_acc(c1); val[5] = to_acc(c1 * vx);
-            val[6] = to_acc(c1 * vy); val[7] = to_acc(c1 * vz);
-          } else {
-            const T fy = sy[p];
-            const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
-            const T cw[4] = {wp * (gx0 * gy0), wp * (fx * gy0), wp * (gx0 * fy),
-                             wp * (fx * fy)};
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-              val[4 * cc + 0] = to_acc(cw[cc]);
-              val[4 * cc + 1] = to_acc(cw[cc] * vx);
-              val[4 * cc + 2] = to_acc(cw[cc] * vy);
-              val[4 * cc + 3] = to_acc(cw[cc] * vz);
-            }
-          }
-        }
-        unsigned todo = __ballot_sync(0xffffffffu, key >= 0);
-        while (todo) {
-          const int lead = __ffs(todo) - 1;
-          const int kk = __shfl_sync(0xffffffffu, key, lead);
-          const bool mine = (key == kk);
-          todo &= ~__ballot_sync(0xffffffffu, mine);
-          A w[NV];
-#pragma unroll
-          for (int q = 0; q < NV; ++q) w[q] = mine ? val[q] : (A)0;
-          // transpose reduction: halve the value set at each exchange; lane L
-          // ends with the warp sum of value q(L)
-          int half = NV / 2;
-#pragma unroll
-          for (int off = 16; off >= 1; off >>= 1) {
-            if (half >= 1) {
-              const bool up = (lane & off) != 0;
-#pragma unroll
-              for (int q = 0; q < NV / 2; ++q) {
-                if (q < half) {
-                  const A send = up ? w[q] : w[q + half];
-                  const A keep = up ? w[q + half] : w[q];
-                  w[q] = keep + shfl_xor(send, off);
-                }
-              }
-              half >>= 1;
-            } else {
-              w[0] = w[0] + shfl_xor(w[0], off);
-            }
-          }
-          // value index held by this lane: bits of the "up" choices
-          int qi = 0;
-          {
-            int h = NV / 2, off = 16;
-            while (h >= 1) {
-              if (lane & off) qi += h;
-              h >>= 1;
-              off >>= 1;
-            }
-          }
-          const int owner = (NV == 16) ? ((lane & 1) == 0) : ((lane & 3) == 0);
-          if (owner) {
-            const int le = k2e[kk];
-            const int a00 = (le & 0xFFFF) + (le >> 16) * AX;
-            const int corner = qi >> 2, qty = qi & 3;
-            const int an = (DIM == 1) ? a00 + corner
-                                      : a00 + (corner & 1) + (corner >> 1) * AX;
-            atomic_acc(&ACC[qty * NA + an], w[0]);
-          }
-        }
-      }
-    }
-    // ---- far movers: global atomics into the far accumulators
-    for (int pos = koff[NE] + tid; pos < koff[NE + 1]; pos += kBlock) {
-      const int p = perm[pos];
-      const int cell = sc[p];
-      deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, sx[p],
-                          DIM == 2 ? sy[p] : (T)0, (sid[p] & kIdCR) ? wcr : wth, svx[p],
-                          svy[p], svz[p]);
-    }
-    // ---- stayers to the tile's bucket, leavers to the mover list
-    const int S = koff[NINT];
-    const int Lv = koff[NE + 1] - S;
-    const int mb = s_mb;
-    const int obase = d.tile_base[t] + outRun;
-    for (int pos = tid; pos < S + Lv; pos += kBlock) {
-      const int p = perm[pos];
+      const int key = ky[r];
+      if (p >= m || key > NE) continue;
+      const int pos = koff[key] + rk[r];
       int gi;
       Parts<T> dst;
       if (pos < S) {
         gi = obase + pos;
         dst = PO;
       } else {
-        gi = mb + (pos - S);
-        if (gi >= g.mover_cap) {
+        const int slot = movRun + (pos - S);
+        if (slot >= g.mover_per_tile) {
           tl.status |= kStatusCapacity;
           continue;
         }
+        gi = mbase + (pos - S);
         dst = d.M;
       }
       dst.cell[gi] = sc[p];
@@ -605,25 +613,30 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
       dst.id[gi] = sid[p];
     }
     outRun += S;
-    __syncthreads();
+    movRun += Lv;
     for (int q = tid; q < NK; q += kBlock) kcount[q] = 0;
     if (c.y + m >= c.w) {
-      // last chunk of tile t: its deposit partial and output count
+      // last chunk of tile t: its deposit partial, output and mover counts
       A* part = (A*)d.partial + (size_t)t * 4 * NA;
       for (int q = tid; q < 4 * NA; q += kBlock) {
         part[q] = ACC[q];
         ACC[q] = (A)0;
       }
-      if (tid == 0) d.cnt[a.out][t] = outRun;
+      if (tid == 0) {
+        d.cnt[a.out][t] = outRun;
+        d.mcnt[t] = min(movRun, g.mover_per_tile);
+      }
       outRun = 0;
+      movRun = 0;
     }
     __syncthreads();
-    // buffer b is free: prefetch the chunk after the one in buffer b ^ 1
+    // stage b is free: prefetch the chunk after the most recently issued one
     if (tid == 0) {
       fence_proxy_async_smem();
-      issue_chunk<T, DIM>(sm, L, b,
-                          next_chunk(desc[b ^ 1], G, g.ntiles, CH, cnt_in, g.tile_cap), d,
-                          PI, g);
+      int4* lastc = (int4*)(sm + L.desc + NS * sizeof(int4));
+      const int4 nc = next_chunk(*lastc, G, g.ntiles, CH, cnt_in, g.tile_cap, pf);
+      *lastc = nc;
+      issue_chunk<T, DIM>(sm, L, b, nc, d, PI, g);
     }
   }
 

@@ -93,7 +93,7 @@ def test_fp64_1d_config_full_1000_steps_bit_exact(fs):
     assert d["reflected"] > 0 and d["incident"] == d["transmitted"] + d["reflected"]
 
 
-@pytest.mark.parametrize("tile", [(4, 2), (8, 4), (16, 1)])
+@pytest.mark.parametrize("tile", [(4, 2), (8, 4), (16, 1), (2, 8)])
 def test_fp64_2d_bit_exact_several_tiles(fs, tile):
     cfg = W.scaled(W.CONFIG_2D, nx=64, ny=16, ppc=8, mach_a=10.0, theta_bn_deg=20.0,
                    tile_x=tile[0], tile_y=tile[1])
@@ -106,6 +106,67 @@ def test_fp64_2d_bit_exact_several_tiles(fs, tile):
     gpu.step(30)
     ref.step(30)
     assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_2d_many_tiles_per_cta_bit_exact(fs):
+    # 2x2-cell tiles on 256 x 128 cells: 8192 tiles, several per persistent CTA
+    cfg = W.scaled(W.CONFIG_2D, nx=256, ny=128, ppc=8, mach_a=15.0, theta_bn_deg=10.0,
+                   tile_x=2, tile_y=2)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    assert gpu.sizes.tiles == 8192
+    ocfg = {k: v for k, v in cfg.items() if k not in ("tile_x", "tile_y")}
+    ref = O.Oracle(**ocfg)
+    for n in (1, 9):
+        gpu.step(n)
+        ref.step(n)
+        assert_state_equal(gpu, ref, fs)
+
+
+def test_fp64_full_size_2d_workload_bit_exact(fs):
+    # the FP64 2D workload at full size (4096 x 256 cells, 16 ppc, 16.8 M
+    # particles) in the launch configuration the benchmark times: after one
+    # and three steps every field, moment and counter equals the oracle's, and
+    # a sample of particles (by id) is identical
+    cfg = W.CONFIG_2D
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    for n in (1, 2):
+        gpu.step(n)
+        ref.step(n)
+        for gw, ow in GRIDS:
+            assert np.array_equal(gpu.grid(gw), ref.grid(ow)), gw
+        dg, dr = gpu.diag(), ref.diag()
+        for k in COUNTERS:
+            assert dg[k] == dr[k], (k, dg[k], dr[k])
+    pg, pr = by_id(gpu.particles()), by_id(ref.particles())
+    assert pg["id"].size == pr["id"].size
+    sel = np.arange(0, pg["id"].size, 997)
+    for k in ("id", "ci", "cj", "fx", "fy", "vx", "vy", "vz"):
+        assert np.array_equal(pg[k][sel], pr[k][sel]), k
+
+
+def test_fp32_full_size_precision_form_invariants(fs):
+    # the FP32 2D precision form at full size (8192 x 512 cells, 64 ppc,
+    # 268 M particles): properties that hold at any size -- exact integer
+    # bookkeeping, total charge equal to the particle weight sum, finite
+    # fields, and the uniform-drift equilibrium kept (E_z ~ M_A sin theta)
+    cfg = W.CONFIG_2D_FP32
+    gpu = fs.FauxShock(precision=fs.FS_FP32, **cfg)
+    n0 = gpu.num_particles()
+    assert n0 == 8192 * 512 * 64
+    gpu.step(5)
+    d = gpu.diag()
+    assert d["status"] == 0
+    assert d["n_particles"] == n0 + d["injected"] - d["transmitted"] - d["escaped"]
+    assert d["incident"] == d["transmitted"] + d["reflected"]
+    n = gpu.grid(fs.FS_N)
+    vol = np.ones(gpu.nxn); vol[0] = vol[-1] = 0.5
+    total = float((n * vol[None, :]).sum())
+    assert total == pytest.approx(d["n_particles"] / 64.0, rel=2e-4)
+    E = gpu.grid(fs.FS_E)
+    assert np.isfinite(E).all() and np.isfinite(gpu.grid(fs.FS_B)).all()
+    ez = E[:, 50:-50, 2].mean()
+    assert ez == pytest.approx(30.0 * np.sin(np.radians(30.0)), rel=0.02)
 
 
 def test_fp64_multi_chunk_tiles_bit_exact(fs):
