@@ -99,6 +99,9 @@ typedef struct fs_params {
   int tile_x, tile_y;      /* cells per tile (0: chosen by the library) */
   int hist_nx, hist_np;    /* x - p_x histogram bins */
   double hist_pmin, hist_pmax;
+  int use_graph;           /* replay fs_step as a captured CUDA graph (default 1;
+                              the first step runs directly, later ones replay;
+                              steps with fs_profile enabled run directly) */
 } fs_params;
 
 /* sizes reported by fs_query */

@@ -11,9 +11,10 @@
  * The paper states no numerics for the host hybrid code; the step below is
  * the textbook scheme this project adopts (CIC gather, non-relativistic Boris
  * push, cell sort, CIC deposit, RK4 Ohm + Faraday). Every arithmetic
- * expression is written in one fixed order, compiled without contraction
- * (-ffp-contract=off), so that a GPU implementation that writes the same
- * expressions in the same order reproduces every FP64 bit.
+ * expression is written in one fixed order, with fused multiply-adds (C99
+ * fma(), one IEEE-754 rounding) where the scheme says so and no other
+ * contraction (-ffp-contract=off), so that a GPU implementation that writes
+ * the same expressions in the same order reproduces every FP64 bit.
  *
  * Particle state per macroparticle: integer cell (i, j), in-cell offset
  * (fx, fy) in [0, 1), velocity (vx, vy, vz) at the half step, and a 32-bit
@@ -43,6 +44,8 @@
 /* deposit fixed point: each contribution is rounded to a multiple of 2^-40 */
 #define FP_SCALE 0x1p40
 #define FP_UNSCALE 0x1p-40
+/* adding 1.5 * 2^52 rounds a double of magnitude below 2^51 to an integer */
+#define ROUND_MAGIC 0x1.8p52
 #define PI_DEC 3.14159265358979323846264338327950288
 
 /* ------------------------------------------------------------------------ */
@@ -175,15 +178,16 @@ static void boris(double* v, const double* E, const double* B, double hdt) {
   double emx = hdt * E[0], emy = hdt * E[1], emz = hdt * E[2];
   double vmx = v[0] + emx, vmy = v[1] + emy, vmz = v[2] + emz;
   double tx = hdt * B[0], ty = hdt * B[1], tz = hdt * B[2];
-  double tt = (tx * tx + ty * ty) + tz * tz;
+  double tt = fma(tz, tz, fma(ty, ty, tx * tx));
   double f = 2.0 / (1.0 + tt);
   double sx = f * tx, sy = f * ty, sz = f * tz;
-  double px = vmx + (vmy * tz - vmz * ty);
-  double py = vmy + (vmz * tx - vmx * tz);
-  double pz = vmz + (vmx * ty - vmy * tx);
-  double qx = vmx + (py * sz - pz * sy);
-  double qy = vmy + (pz * sx - px * sz);
-  double qz = vmz + (px * sy - py * sx);
+  /* v' = v- + v- x t, v+ = v- + v' x s, each component as two fused steps */
+  double px = fma(vmy, tz, fma(-vmz, ty, vmx));
+  double py = fma(vmz, tx, fma(-vmx, tz, vmy));
+  double pz = fma(vmx, ty, fma(-vmy, tx, vmz));
+  double qx = fma(py, sz, fma(-pz, sy, vmx));
+  double qy = fma(pz, sx, fma(-px, sz, vmy));
+  double qz = fma(px, sy, fma(-py, sx, vmz));
   v[0] = qx + emx;
   v[1] = qy + emy;
   v[2] = qz + emz;
@@ -361,8 +365,8 @@ static void gather(const or_sim* s, int i, int j, double fx, double fy,
     const double* B0 = s->Bb + 3 * nidx(s, i, 0);
     const double* B1 = s->Bb + 3 * nidx(s, i1, 0);
     for (int c = 0; c < 3; ++c) {
-      Ep[c] = g0 * E0[c] + fx * E1[c];
-      Bp[c] = g0 * B0[c] + fx * B1[c];
+      Ep[c] = fma(fx, E1[c], g0 * E0[c]);
+      Bp[c] = fma(fx, B1[c], g0 * B0[c]);
     }
     return;
   }
@@ -372,10 +376,10 @@ static void gather(const or_sim* s, int i, int j, double fx, double fy,
   long long n00 = 3 * nidx(s, i, j), n10 = 3 * nidx(s, i1, j);
   long long n01 = 3 * nidx(s, i, j1), n11 = 3 * nidx(s, i1, j1);
   for (int c = 0; c < 3; ++c) {
-    Ep[c] = ((w00 * s->E[n00 + c] + w10 * s->E[n10 + c]) +
-             w01 * s->E[n01 + c]) + w11 * s->E[n11 + c];
-    Bp[c] = ((w00 * s->Bb[n00 + c] + w10 * s->Bb[n10 + c]) +
-             w01 * s->Bb[n01 + c]) + w11 * s->Bb[n11 + c];
+    Ep[c] = fma(w11, s->E[n11 + c],
+                fma(w01, s->E[n01 + c], fma(w10, s->E[n10 + c], w00 * s->E[n00 + c])));
+    Bp[c] = fma(w11, s->Bb[n11 + c],
+                fma(w01, s->Bb[n01 + c], fma(w10, s->Bb[n10 + c], w00 * s->Bb[n00 + c])));
   }
 }
 
@@ -386,17 +390,26 @@ void or_gather(const or_sim* s, int i, int j, double fx, double fy,
 
 /* ------------------------------------------------------------------------ */
 /* Moments: CIC deposit of n and J = n u_i at the new positions with the    */
-/* half-step velocities, each contribution rounded to a multiple of 2^-40   */
-/* and summed in int64, so that the node sums do not depend on the order of */
-/* the particles. Then the wall half-volume correction, the density floor  */
-/* and u_i = J / n.                                                          */
+/* half-step velocities, each contribution rounded to the nearest multiple  */
+/* of 2^-40 and summed in int64, so that the node sums do not depend on the */
+/* order of the particles. The weight is carried scaled by 2^40 (exact), the*/
+/* current terms are rounded from the exact product (one fused rounding).   */
+/* Then the wall half-volume correction, the density floor and u_i = J / n. */
 /* ------------------------------------------------------------------------ */
-static void dep1(or_sim* s, long long node, double cn, double vx, double vy,
+static int64_t to_fixed(double scaled) {
+  return (int64_t)((scaled + ROUND_MAGIC) - ROUND_MAGIC);
+}
+static int64_t to_fixed_prod(double a, double b) {
+  return (int64_t)(fma(a, b, ROUND_MAGIC) - ROUND_MAGIC);
+}
+
+/* cns: the particle weight times the corner weight, scaled by 2^40 */
+static void dep1(or_sim* s, long long node, double cns, double vx, double vy,
                  double vz) {
-  s->qn[node] += llrint(cn * FP_SCALE);
-  s->qj[3 * node + 0] += llrint((cn * vx) * FP_SCALE);
-  s->qj[3 * node + 1] += llrint((cn * vy) * FP_SCALE);
-  s->qj[3 * node + 2] += llrint((cn * vz) * FP_SCALE);
+  s->qn[node] += to_fixed(cns);
+  s->qj[3 * node + 0] += to_fixed_prod(cns, vx);
+  s->qj[3 * node + 1] += to_fixed_prod(cns, vy);
+  s->qj[3 * node + 2] += to_fixed_prod(cns, vz);
 }
 
 static void deposit_and_finish(or_sim* s) {
@@ -404,7 +417,7 @@ static void deposit_and_finish(or_sim* s) {
   memset(s->qn, 0, nn * sizeof(int64_t));
   memset(s->qj, 0, 3 * nn * sizeof(int64_t));
   for (long long k = 0; k < s->np; ++k) {
-    double wp = weight_of(s, s->id[k]);
+    double wp = weight_of(s, s->id[k]) * FP_SCALE;
     int i = s->ci[k], j = s->cj[k];
     int i1 = node_col(s, i + 1);
     double fx = s->fx[k];
@@ -500,11 +513,16 @@ static void ohm(const or_sim* s, const double* Bc, double* Eo, double* Bbo) {
       double ux = s->u[3 * q + 0], uy = s->u[3 * q + 1], uz = s->u[3 * q + 2];
       double ax = cxv - jcr, ay = cyv, az = czv;
       double inv_n = 1.0 / n;
-      double ex = ((ay * bbz - az * bby) * inv_n - (uy * bbz - uz * bby)) -
-                  (te * dnx) * inv_n;
-      double ey = ((az * bbx - ax * bbz) * inv_n - (uz * bbx - ux * bbz)) -
-                  (te * dny) * inv_n;
-      double ez = (ax * bby - ay * bbx) * inv_n - (ux * bby - uy * bbx);
+      /* (a x Bbar) and (u x Bbar), each component as one fused step */
+      double cax = fma(ay, bbz, -(az * bby));
+      double cay = fma(az, bbx, -(ax * bbz));
+      double caz = fma(ax, bby, -(ay * bbx));
+      double cux = fma(uy, bbz, -(uz * bby));
+      double cuy = fma(uz, bbx, -(ux * bbz));
+      double cuz = fma(ux, bby, -(uy * bbx));
+      double ex = fma(-(te * dnx), inv_n, fma(cax, inv_n, -cux));
+      double ey = fma(-(te * dny), inv_n, fma(cay, inv_n, -cuy));
+      double ez = fma(caz, inv_n, -cuz);
       if (eta != 0.0) {
         ex = ex + eta * cxv;
         ey = ey + eta * cyv;
@@ -564,28 +582,28 @@ static void advance_fields(or_sim* s) {
     faraday(s, s->Es, s->K);
     for (long long k = 0; k < nc3; ++k) {
       s->Bsum[k] = s->K[k];
-      s->Bs[k] = s->B[k] + s->hh * s->K[k];
+      s->Bs[k] = fma(s->hh, s->K[k], s->B[k]);
     }
     /* stage 2 */
     ohm(s, s->Bs, s->Es, NULL);
     faraday(s, s->Es, s->K);
     for (long long k = 0; k < nc3; ++k) {
-      s->Bsum[k] = s->Bsum[k] + 2.0 * s->K[k];
-      s->Bs[k] = s->B[k] + s->hh * s->K[k];
+      s->Bsum[k] = fma(2.0, s->K[k], s->Bsum[k]);
+      s->Bs[k] = fma(s->hh, s->K[k], s->B[k]);
     }
     /* stage 3 */
     ohm(s, s->Bs, s->Es, NULL);
     faraday(s, s->Es, s->K);
     for (long long k = 0; k < nc3; ++k) {
-      s->Bsum[k] = s->Bsum[k] + 2.0 * s->K[k];
-      s->Bs[k] = s->B[k] + s->h * s->K[k];
+      s->Bsum[k] = fma(2.0, s->K[k], s->Bsum[k]);
+      s->Bs[k] = fma(s->h, s->K[k], s->B[k]);
     }
     /* stage 4 */
     ohm(s, s->Bs, s->Es, NULL);
     faraday(s, s->Es, s->K);
     for (long long k = 0; k < nc3; ++k) {
       s->Bsum[k] = s->Bsum[k] + s->K[k];
-      s->B[k] = s->B[k] + s->h6 * s->Bsum[k];
+      s->B[k] = fma(s->h6, s->Bsum[k], s->B[k]);
     }
   }
   ohm(s, s->B, s->E, s->Bb);
@@ -717,7 +735,7 @@ static void push_all(or_sim* s, long long step) {
     gather(s, i, j, fx, fy, Ep, Bp);
     boris(v, Ep, Bp, s->hdt);
     /* move in x */
-    double fxr = fx + v[0] * s->dtdx;
+    double fxr = fma(v[0], s->dtdx, fx);
     double kx = floor(fxr);
     if (!(fabs(kx) < 1.0e9)) { s->err = 1; continue; }
     int inew = i + (int)kx;
@@ -727,7 +745,7 @@ static void push_all(or_sim* s, long long step) {
     int jnew = j;
     double fyn = fy;
     if (s->p.dim == 2) {
-      double fyr = fy + v[1] * s->dtdy;
+      double fyr = fma(v[1], s->dtdy, fy);
       double ky = floor(fyr);
       if (!(fabs(ky) < 1.0e9)) { s->err = 1; continue; }
       jnew = wrapj(s, j + (int)ky);

@@ -270,6 +270,52 @@ int grid_blocks(long long n) {
   return (int)g;
 }
 
+// Capture one step for each ping-pong parity on a private stream (the legacy
+// default stream cannot be captured); the graphs replay on the caller's stream.
+int build_graphs(Sim* s) {
+  if (!s->cap_stream &&
+      cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return FS_ECUDA;
+  // the captured work must follow everything already queued on the caller's stream
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return FS_ECUDA;
+  cudaStream_t user = s->stream;
+  s->stream = s->cap_stream;
+  int rc = FS_OK;
+  for (int par = 0; par < 2 && rc == FS_OK; ++par) {
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = FS_ECUDA;
+      break;
+    }
+    const cudaError_t e = s->ops->step(s, par, 0, nullptr);
+    const cudaError_t e2 = cudaStreamEndCapture(s->stream, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess || !gr) {
+      rc = FS_ECUDA;
+      if (gr) cudaGraphDestroy(gr);
+      break;
+    }
+    if (cudaGraphInstantiate(&s->graph[par], gr, 0) != cudaSuccess) rc = FS_ECUDA;
+    cudaGraphDestroy(gr);
+  }
+  s->stream = user;
+  cudaGetLastError();
+  if (rc == FS_OK) s->graphs_ready = true;
+  return rc;
+}
+
+void release_graphs(Sim* s) {
+  for (int par = 0; par < 2; ++par)
+    if (s->graph[par]) {
+      cudaGraphExecDestroy(s->graph[par]);
+      s->graph[par] = nullptr;
+    }
+  if (s->cap_stream) {
+    cudaStreamDestroy(s->cap_stream);
+    s->cap_stream = nullptr;
+  }
+  s->graphs_ready = false;
+}
+
 int redeposit(Sim* s) {
   cudaError_t e = cudaMemsetAsync(s->base + s->L.far, 0,
                                   (s->p.precision == FS_FP64 ? 8 : 4) * 4 *
@@ -344,6 +390,7 @@ int fs_params_default(int dim, fs_params* out) {
   out->j_cr_ext = 0.0;
   out->init_plasma = 1;
   out->seed = 1;
+  out->use_graph = 1;
   out->capacity_factor = 3.0;
   out->mover_fraction = 0.25;
   out->tile_x = 0;
@@ -446,8 +493,22 @@ int fs_step(fs_handle* h, int nsteps) {
   Sim* s = &h->sim;
   if (s->sticky) return s->sticky;
   const bool inj = s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable);
-  const long long per_step = 1 + 1 + (inj ? 3 : 0) + 1 + 8LL * s->p.n_sub + 1;
+  const long long per_step = 1 + 1 + (inj ? 3 : 0) + 1 + 8LL * s->p.n_sub + 1 + 1;
   constexpr int kSet = FS_NPHASES + 1;
+  if (!h->profiling && s->p.use_graph && s->steps_direct > 0 && !s->graphs_ready) {
+    int r = build_graphs(s);
+    if (r) return s->sticky = r;
+  }
+  if (!h->profiling && s->graphs_ready) {
+    for (int k = 0; k < nsteps; ++k) {
+      if (cudaGraphLaunch(s->graph[s->cur], s->stream) != cudaSuccess)
+        return s->sticky = FS_ECUDA;
+      s->cur = 1 - s->cur;
+      s->step++;
+      s->launches += per_step;
+    }
+    return FS_OK;
+  }
   for (int k = 0; k < nsteps; ++k) {
     cudaEvent_t* ev = nullptr;
     if (h->profiling) {
@@ -463,6 +524,7 @@ int fs_step(fs_handle* h, int nsteps) {
     s->cur = 1 - s->cur;
     s->step++;
     s->launches += per_step;
+    s->steps_direct++;
   }
   return FS_OK;
 }
@@ -776,6 +838,7 @@ int fs_destroy(fs_handle* h) {
   if (!h) return FS_EINVAL;
   cudaStreamSynchronize(h->sim.stream);
   release_events(h);
+  release_graphs(&h->sim);
   delete h;
   return FS_OK;
 }

@@ -58,6 +58,16 @@ __device__ __forceinline__ unsigned long long to_acc(double c) {
   return (unsigned long long)(__double_as_longlong(m) -
                               __double_as_longlong(0x1.8p52));
 }
+// a * b in accumulator form. FP64: rounded once from the exact product to
+// the nearest integer (fma with 1.5 * 2^52), as the written scheme states.
+__device__ __forceinline__ float to_acc_prod(float a, float b) { return a * b; }
+__device__ __forceinline__ unsigned long long to_acc_prod(double a, double b) {
+  const double m = __fma_rn(a, b, 0x1.8p52);
+  return (unsigned long long)(__double_as_longlong(m) -
+                              __double_as_longlong(0x1.8p52));
+}
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double acc_to_double(float a) { return (double)a; }
 __device__ __forceinline__ double acc_to_double(unsigned long long a) {
   return (double)(long long)a * 0x1p-40;
@@ -108,7 +118,8 @@ __device__ __forceinline__ double kinetic(double wp, double vx, double vy,
 
 // ------------------------------------------------------------------------
 // Boris rotation, the written order: half kick, t = B dt/2,
-// s = 2 t / (1 + t.t), v' = v- + v- x t, v+ = v- + v' x s, half kick.
+// s = 2 t / (1 + t.t), v' = v- + v- x t, v+ = v- + v' x s (each component as
+// two fused multiply-adds), half kick.
 // ------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void boris(T& vx, T& vy, T& vz, const T E[3],
@@ -116,15 +127,15 @@ __device__ __forceinline__ void boris(T& vx, T& vy, T& vz, const T E[3],
   const T emx = hdt * E[0], emy = hdt * E[1], emz = hdt * E[2];
   const T vmx = vx + emx, vmy = vy + emy, vmz = vz + emz;
   const T tx = hdt * B[0], ty = hdt * B[1], tz = hdt * B[2];
-  const T tt = (tx * tx + ty * ty) + tz * tz;
+  const T tt = fmaT(tz, tz, fmaT(ty, ty, tx * tx));
   const T f = (T)2 / ((T)1 + tt);
   const T sx = f * tx, sy = f * ty, sz = f * tz;
-  const T px = vmx + (vmy * tz - vmz * ty);
-  const T py = vmy + (vmz * tx - vmx * tz);
-  const T pz = vmz + (vmx * ty - vmy * tx);
-  const T qx = vmx + (py * sz - pz * sy);
-  const T qy = vmy + (pz * sx - px * sz);
-  const T qz = vmz + (px * sy - py * sx);
+  const T px = fmaT(vmy, tz, fmaT(-vmz, ty, vmx));
+  const T py = fmaT(vmz, tx, fmaT(-vmx, tz, vmy));
+  const T pz = fmaT(vmx, ty, fmaT(-vmy, tx, vmz));
+  const T qx = fmaT(py, sz, fmaT(-pz, sy, vmx));
+  const T qy = fmaT(pz, sx, fmaT(-px, sz, vmy));
+  const T qz = fmaT(px, sy, fmaT(-py, sx, vmz));
   vx = qx + emx;
   vy = qy + emy;
   vz = qz + emz;
@@ -216,13 +227,13 @@ __device__ __forceinline__ void deposit_far(const DevPtrs<T>& d, const Geo& g,
   if (DIM == 1) {
     const T c0 = wp * ((T)1 - fx), c1 = wp * fx;
     atomic_acc(&far[0 * nn + i], to_acc(c0));
-    atomic_acc(&far[1 * nn + i], to_acc(c0 * vx));
-    atomic_acc(&far[2 * nn + i], to_acc(c0 * vy));
-    atomic_acc(&far[3 * nn + i], to_acc(c0 * vz));
+    atomic_acc(&far[1 * nn + i], to_acc_prod(c0, vx));
+    atomic_acc(&far[2 * nn + i], to_acc_prod(c0, vy));
+    atomic_acc(&far[3 * nn + i], to_acc_prod(c0, vz));
     atomic_acc(&far[0 * nn + i1], to_acc(c1));
-    atomic_acc(&far[1 * nn + i1], to_acc(c1 * vx));
-    atomic_acc(&far[2 * nn + i1], to_acc(c1 * vy));
-    atomic_acc(&far[3 * nn + i1], to_acc(c1 * vz));
+    atomic_acc(&far[1 * nn + i1], to_acc_prod(c1, vx));
+    atomic_acc(&far[2 * nn + i1], to_acc_prod(c1, vy));
+    atomic_acc(&far[3 * nn + i1], to_acc_prod(c1, vz));
   } else {
     const int j1 = (j + 1 == g.ny) ? 0 : j + 1;
     const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
@@ -233,9 +244,9 @@ __device__ __forceinline__ void deposit_far(const DevPtrs<T>& d, const Geo& g,
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       atomic_acc(&far[0 * nn + nd[c]], to_acc(cw[c]));
-      atomic_acc(&far[1 * nn + nd[c]], to_acc(cw[c] * vx));
-      atomic_acc(&far[2 * nn + nd[c]], to_acc(cw[c] * vy));
-      atomic_acc(&far[3 * nn + nd[c]], to_acc(cw[c] * vz));
+      atomic_acc(&far[1 * nn + nd[c]], to_acc_prod(cw[c], vx));
+      atomic_acc(&far[2 * nn + nd[c]], to_acc_prod(cw[c], vy));
+      atomic_acc(&far[3 * nn + nd[c]], to_acc_prod(cw[c], vz));
     }
   }
 }
@@ -319,8 +330,8 @@ static __global__ void k_inject_count(double* acc, int* rowcnt, int* rowoff, int
 
 template <typename T, int DIM>
 __global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
-                             long long step, const int* rowcnt,
-                             const int* rowoff, int maxk) {
+                             const int* rowcnt, const int* rowoff, int maxk) {
+  const long long step = d.ctr->step;
   const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = gidx / maxk, k = gidx % maxk;
   __shared__ unsigned long long s_first;
@@ -407,6 +418,11 @@ __global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
     atomicAdd(&d.ctr->injected, (unsigned long long)l_inj);
     atomicAdd(&d.ctr->injected_energy, l_e);
   }
+}
+
+// end of a step: advance the device step counter
+static __global__ void k_step_end(Counters* ctr) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctr->step += 1;
 }
 
 // advance next_id by this step's total (after k_inject_gen has read it)
@@ -515,7 +531,8 @@ __global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
 }
 
 // ------------------------------------------------------------------------
-// Ohm's law at the nodes (massless isothermal electrons, J = curl B):
+// Ohm's law at the nodes (massless isothermal electrons, J = curl B), the
+// cross products and the 1/n scaling written as fused multiply-adds:
 //   E = ((curl B - j_ext x) x Bbar)/n - u x Bbar - T_e grad n / n (+ eta curl B)
 // Bbar is B averaged onto the nodes; derivatives are two-point differences
 // averaged across the transverse direction; x walls use zero-gradient ghost
@@ -588,9 +605,15 @@ __global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
     const T ux = uN[q], uy = uN[nn + q], uz = uN[2 * nn + q];
     const T ax = cxv - jcr, ay = cyv, az = czv;
     const T inv_n = (T)1 / n;
-    T ex = ((ay * bbz - az * bby) * inv_n - (uy * bbz - uz * bby)) - (te * dnx) * inv_n;
-    T ey = ((az * bbx - ax * bbz) * inv_n - (uz * bbx - ux * bbz)) - (te * dny) * inv_n;
-    T ez = (ax * bby - ay * bbx) * inv_n - (ux * bby - uy * bbx);
+    const T cax = fmaT(ay, bbz, -(az * bby));
+    const T cay = fmaT(az, bbx, -(ax * bbz));
+    const T caz = fmaT(ax, bby, -(ay * bbx));
+    const T cux = fmaT(uy, bbz, -(uz * bby));
+    const T cuy = fmaT(uz, bbx, -(ux * bbz));
+    const T cuz = fmaT(ux, bby, -(uy * bbx));
+    T ex = fmaT(-(te * dnx), inv_n, fmaT(cax, inv_n, -cux));
+    T ey = fmaT(-(te * dny), inv_n, fmaT(cay, inv_n, -cuy));
+    T ez = fmaT(caz, inv_n, -cuz);
     if (ph.eta != 0.0) {
       ex = ex + eta * cxv;
       ey = ey + eta * cyv;
@@ -667,16 +690,16 @@ __global__ void k_faraday(const T* __restrict__ En, T* __restrict__ B,
       const size_t k = (size_t)q * nc + c;
       if (stage == 1) {
         Bsum[k] = K[q];
-        Bs[k] = B[k] + hh * K[q];
+        Bs[k] = fmaT(hh, K[q], B[k]);
       } else if (stage == 2) {
-        Bsum[k] = Bsum[k] + (T)2 * K[q];
-        Bs[k] = B[k] + hh * K[q];
+        Bsum[k] = fmaT((T)2, K[q], Bsum[k]);
+        Bs[k] = fmaT(hh, K[q], B[k]);
       } else if (stage == 3) {
-        Bsum[k] = Bsum[k] + (T)2 * K[q];
-        Bs[k] = B[k] + h * K[q];
+        Bsum[k] = fmaT((T)2, K[q], Bsum[k]);
+        Bs[k] = fmaT(h, K[q], B[k]);
       } else {
         const T sum = Bsum[k] + K[q];
-        B[k] = B[k] + h6 * sum;
+        B[k] = fmaT(h6, sum, B[k]);
       }
     }
   }

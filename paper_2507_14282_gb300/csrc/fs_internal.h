@@ -31,8 +31,8 @@ struct Counters {
   double fs_energy, injected_energy, removed_energy;
   double sums[8];        // diagnostics: kinetic, px, py, pz, magnetic
   int status;            // kStatus* bits
-  int mover_count;       // movers written this step
-  int pad[2];
+  int mover_count;       // unused
+  long long step;        // step being taken (the Philox step counter)
 };
 
 // Structure-of-arrays particle buffer. cell packs (j << 16) | i.
@@ -139,6 +139,11 @@ struct Sim {
   int sticky;          // first error code reported
   long long launches;  // kernels launched through this handle
   const Ops* ops;
+  // one captured step per ping-pong parity (replayed by fs_step)
+  cudaGraphExec_t graph[2];
+  cudaStream_t cap_stream;
+  bool graphs_ready;
+  int steps_direct;    // steps launched directly (graphs are captured after one)
   template <typename T>
   DevPtrs<T> ptrs(int dummy = 0) const;
 };

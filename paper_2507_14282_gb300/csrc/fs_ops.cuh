@@ -173,9 +173,9 @@ struct OpsImpl {
       const long long nthreads = (long long)s->g.ny * maxk;
       const int blocks = (int)((nthreads + kBlock - 1) / kBlock);
       if (s->g.dim == 1)
-        k_inject_gen<T, 1><<<blocks, kBlock, 0, s->stream>>>(d, s->g, s->ph, out, step, rowcnt, rowoff, maxk);
+        k_inject_gen<T, 1><<<blocks, kBlock, 0, s->stream>>>(d, s->g, s->ph, out, rowcnt, rowoff, maxk);
       else
-        k_inject_gen<T, 2><<<blocks, kBlock, 0, s->stream>>>(d, s->g, s->ph, out, step, rowcnt, rowoff, maxk);
+        k_inject_gen<T, 2><<<blocks, kBlock, 0, s->stream>>>(d, s->g, s->ph, out, rowcnt, rowoff, maxk);
       k_inject_commit<<<1, 32, 0, s->stream>>>(d.ctr, rowoff, s->g.ny);
     }
     mark(3);
@@ -183,6 +183,7 @@ struct OpsImpl {
     if (e != cudaSuccess) return e;
     mark(4);
     e = fields(s);
+    k_step_end<<<1, 32, 0, s->stream>>>(d.ctr);
     mark(5);
     return e;
   }

@@ -219,8 +219,8 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
     const T* n1 = n0 + 8;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      Ep[q] = g0 * n0[q] + fx * n1[q];
-      Bp[q] = g0 * n0[3 + q] + fx * n1[3 + q];
+      Ep[q] = fmaT(fx, n1[q], g0 * n0[q]);
+      Bp[q] = fmaT(fx, n1[3 + q], g0 * n0[3 + q]);
     }
   } else {
     const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
@@ -231,15 +231,15 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
     const T* n11 = n01 + 8;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      Ep[q] = ((w00 * n00[q] + w10 * n10[q]) + w01 * n01[q]) + w11 * n11[q];
-      Bp[q] = ((w00 * n00[3 + q] + w10 * n10[3 + q]) + w01 * n01[3 + q]) +
-              w11 * n11[3 + q];
+      Ep[q] = fmaT(w11, n11[q], fmaT(w01, n01[q], fmaT(w10, n10[q], w00 * n00[q])));
+      Bp[q] = fmaT(w11, n11[3 + q],
+                   fmaT(w01, n01[3 + q], fmaT(w10, n10[3 + q], w00 * n00[3 + q])));
     }
   }
   boris<T>(vx, vy, vz, Ep, Bp, hdt);
-  const T fxr = fx + vx * dtdx;
+  const T fxr = fmaT(vx, dtdx, fx);
   T fyr = fy;
-  if (DIM == 2) fyr = fy + vy * dtdy;
+  if (DIM == 2) fyr = fmaT(vy, dtdy, fy);
   // whole-cell shift floor(f): by comparison for |shift| <= 1 (the common
   // case), by floor otherwise; the same value either way
   T kx, ky = (T)0;
@@ -371,19 +371,19 @@ __device__ __forceinline__ void warp_deposit(typename Num<T>::acc* ACC, int NA, 
   A val[NV];
   if (DIM == 1) {
     const T c0 = wp * ((T)1 - fx), c1 = wp * fx;
-    val[0] = to_acc(c0); val[1] = to_acc(c0 * vx);
-    val[2] = to_acc(c0 * vy); val[3] = to_acc(c0 * vz);
-    val[4] = to_acc(c1); val[5] = to_acc(c1 * vx);
-    val[6] = to_acc(c1 * vy); val[7] = to_acc(c1 * vz);
+    val[0] = to_acc(c0); val[1] = to_acc_prod(c0, vx);
+    val[2] = to_acc_prod(c0, vy); val[3] = to_acc_prod(c0, vz);
+    val[4] = to_acc(c1); val[5] = to_acc_prod(c1, vx);
+    val[6] = to_acc_prod(c1, vy); val[7] = to_acc_prod(c1, vz);
   } else {
     const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
     const T cw[4] = {wp * (gx0 * gy0), wp * (fx * gy0), wp * (gx0 * fy), wp * (fx * fy)};
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
       val[4 * cc + 0] = to_acc(cw[cc]);
-      val[4 * cc + 1] = to_acc(cw[cc] * vx);
-      val[4 * cc + 2] = to_acc(cw[cc] * vy);
-      val[4 * cc + 3] = to_acc(cw[cc] * vz);
+      val[4 * cc + 1] = to_acc_prod(cw[cc], vx);
+      val[4 * cc + 2] = to_acc_prod(cw[cc], vy);
+      val[4 * cc + 3] = to_acc_prod(cw[cc], vz);
     }
   }
   int qi = 0;
@@ -458,6 +458,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
   const T dtdx = (T)ph.dtdx, dtdy = (T)ph.dtdy, hdt = (T)ph.hdt;
   const T wth = (T)(ph.w_th * (double)deposit_weight_scale<T>());
   const T wcr = (T)(ph.w_cr * (double)deposit_weight_scale<T>());
+  const long long step = d.ctr->step;  // device step counter (graph-replayable)
 
   // ---- per-CTA tables: extended cell <-> sort key; zero accumulators
   for (int e = tid; e < NE; e += kBlock) {
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
         vz = svz[p];
         id = sid[p];
         key = push_one<T, DIM>(F, L.NFX, cell, fx, fy, vx, vy, vz, id, i0, j0, TX, TY, EX,
-                               EY, NE, e2k, g, ph, dtdx, dtdy, hdt, a.step, tl);
+                               EY, NE, e2k, g, ph, dtdx, dtdy, hdt, step, tl);
         sc[p] = cell;
         sx[p] = fx;
         if (DIM == 2) sy[p] = fy;

@@ -44,6 +44,7 @@ class FsParams(C.Structure):
         ("tile_x", C.c_int), ("tile_y", C.c_int),
         ("hist_nx", C.c_int), ("hist_np", C.c_int),
         ("hist_pmin", C.c_double), ("hist_pmax", C.c_double),
+        ("use_graph", C.c_int),
     ]
 
 

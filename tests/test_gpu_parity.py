@@ -199,6 +199,17 @@ def test_fp64_cosmic_ray_source_and_open_thermal(fs):
     assert ncr > 0 and d["injected"] >= 2 * ncr
 
 
+def test_fp64_direct_launches_equal_graph_replay(fs):
+    # fs_step replays a captured CUDA graph after its first step; with
+    # use_graph = 0 every step launches directly: both equal the oracle
+    cfg = W.scaled(W.CONFIG_1D, nx=128)
+    direct = fs.FauxShock(precision=fs.FS_FP64, use_graph=0, **cfg)
+    ref = O.Oracle(**cfg)
+    direct.step(40)
+    ref.step(40)
+    assert_state_equal(direct, ref, fs)
+
+
 def test_fp64_downstream_frame_return(fs):
     cfg = W.scaled(W.CONFIG_1D, nx=64, fs_speed_frame=O.FRAME_DOWNSTREAM, r_comp=3.0)
     gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
