@@ -53,12 +53,38 @@ def particle_bytes(prec_bytes: int, dim: int) -> int:
 # Grid traffic per cell per step on a single pass (moments write + read 8
 # words, B read + write 6, E write 3, E + Bbar read by the gather 6).
 GRID_WORDS_PER_CELL = 23
-# FP64 operations of the written scheme per particle-step in 2D (gather 48,
-# Boris 46 + one division, move 8, deposit 38).
-FP64_OPS_PER_PARTICLE_STEP = 140
+# FP64 operations of the written scheme per particle-step in 2D, each add,
+# multiply, fused multiply-add, compare and the reciprocal counted once:
+# gather weights 6 + sums 24, Boris 33, move ~10, deposit 26.
+FP64_OPS_PER_PARTICLE_STEP = 100
 # FP64 throughput of GB300: 1.25 TFLOP/s nominal counts an FMA as two; the
 # scheme issues unfused adds and multiplies, one operation per pipe slot.
 FP64_PEAK_OPS = 0.625e12
+
+
+# DRAM bytes per particle of one k_push launch, from ncu (dram__bytes_read.sum
+# + dram__bytes_write.sum) on a 1024 x 256-cell case of the same kernel, scaled
+# by the particles of a launch; valid only while the kernel sources are the
+# ones the counters were taken on (their hash below), else reported as null.
+PUSH_TRAFFIC = {"fp32": 949.1e6 / 16777216, "fp64": 396.0e6 / 4194304}
+PUSH_SOURCES = ("paper_2507_14282_gb300/csrc/fs_push.cuh",
+                "paper_2507_14282_gb300/csrc/fs_engine.cuh")
+PUSH_SOURCES_SHA1 = "d64b0a2c3719b76d085a814436372f3d5a43dcf0"
+
+
+def push_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in PUSH_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(prec: str, n: float):
+    if push_sources_sha1() != PUSH_SOURCES_SHA1:
+        return None
+    return PUSH_TRAFFIC[prec] * n
 
 
 def load_peaks() -> dict:
@@ -208,7 +234,8 @@ def ours(args):
                 "achieved": achieved_ops, "peak": FP64_PEAK_OPS / 1e12,
                 "unit": "TFLOP/s (FP64 ops)",
                 "frac": achieved_ops / (FP64_PEAK_OPS / 1e12),
-                "traffic": None,
+                "traffic": traffic_per_launch("fp64", res64["n_mean"]),
+                "traffic_unit": "bytes per launch",
                 "kernel_ms": kern64,
                 "hbm_achieved_gbs": res64["n_mean"] * pb64 / (kern64 * 1e-3) / 1e9,
                 "hbm_peak_gbs": hbm, "hbm_frac": res64["n_mean"] * pb64 / (kern64 * 1e-3) / 1e9 / hbm,
@@ -240,7 +267,9 @@ def ours(args):
                 "bytes_per_particle_step": pb32 + gb32,
                 "step_roofline_frac": res32["n_mean"] * (pb32 + gb32) / (ms32 * 1e-3) / 1e9 / hbm,
                 "roofline": {"bound": "hbm", "kernel": "k_push<float,2>", "achieved": ach,
-                             "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                             "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                             "traffic": traffic_per_launch("fp32", res32["n_mean"]),
+                             "traffic_unit": "bytes per launch",
                              "kernel_ms": kern32, "peak_source": peak_src},
                 "phases_ms": res32["phases"],
                 "vs_fp64": v32 / value, "gpu_launches": res32["launches"]}
@@ -378,18 +407,46 @@ def reference(args):
     }))
 
 
+def ncu_case(args):
+    """A small run of the benchmark's kernels for ncu captures: the FP64 or
+    FP32 workload on a smaller grid, init then a few steps, no timing."""
+    import torch
+    from paper_2507_14282_gb300 import fs
+    base = FP64_WORKLOAD if args.ncu_case == "fp64" else FP32_WORKLOAD
+    p = dict(base)
+    if args.nx:
+        p["nx"] = args.nx
+    if args.ny:
+        p["ny"] = args.ny
+    prec = fs.FS_FP64 if args.ncu_case == "fp64" else fs.FS_FP32
+    sim = fs.FauxShock(precision=prec, capacity_factor=1.5, mover_fraction=0.1, **p)
+    sim.step(args.steps)
+    torch.cuda.synchronize()
+    d = sim.diag()
+    print(json.dumps({"ncu_case": args.ncu_case, "nx": p["nx"], "ny": p["ny"],
+                      "steps": args.steps, "n_particles": d["n_particles"],
+                      "status": d["status"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--ncu-case", choices=["fp64", "fp32"], default=None,
+                    help="run a small case of the benchmark kernels for ncu")
+    ap.add_argument("--nx", type=int, default=0)
+    ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--steps32", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=50)
-    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=300)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
+    if args.ncu_case:
+        ncu_case(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

@@ -68,6 +68,8 @@ __device__ __forceinline__ unsigned long long to_acc_prod(double a, double b) {
 }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rcpT(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcpT(double a) { return __drcp_rn(a); }
 __device__ __forceinline__ double acc_to_double(float a) { return (double)a; }
 __device__ __forceinline__ double acc_to_double(unsigned long long a) {
   return (double)(long long)a * 0x1p-40;
@@ -128,7 +130,9 @@ __device__ __forceinline__ void boris(T& vx, T& vy, T& vz, const T E[3],
   const T vmx = vx + emx, vmy = vy + emy, vmz = vz + emz;
   const T tx = hdt * B[0], ty = hdt * B[1], tz = hdt * B[2];
   const T tt = fmaT(tz, tz, fmaT(ty, ty, tx * tx));
-  const T f = (T)2 / ((T)1 + tt);
+  // 2 / (1 + t.t) as 2 * (correctly rounded reciprocal): doubling is exact,
+  // so this is the same number as the rounded quotient
+  const T f = (T)2 * rcpT((T)1 + tt);
   const T sx = f * tx, sy = f * ty, sz = f * tz;
   const T px = fmaT(vmy, tz, fmaT(-vmz, ty, vmx));
   const T py = fmaT(vmz, tx, fmaT(-vmx, tz, vmy));

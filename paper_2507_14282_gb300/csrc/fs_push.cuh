@@ -243,17 +243,19 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
   // whole-cell shift floor(f): by comparison for |shift| <= 1 (the common
   // case), by floor otherwise; the same value either way
   T kx, ky = (T)0;
+  bool far_shift = false;
   if (fxr >= (T)0 && fxr < (T)1) kx = (T)0;
   else if (fxr >= (T)1 && fxr < (T)2) kx = (T)1;
   else if (fxr < (T)0 && fxr >= (T)-1) kx = (T)-1;
-  else kx = Num<T>::fl(fxr);
+  else { kx = Num<T>::fl(fxr); far_shift = true; }
   if (DIM == 2) {
     if (fyr >= (T)0 && fyr < (T)1) ky = (T)0;
     else if (fyr >= (T)1 && fyr < (T)2) ky = (T)1;
     else if (fyr < (T)0 && fyr >= (T)-1) ky = (T)-1;
-    else ky = Num<T>::fl(fyr);
+    else { ky = Num<T>::fl(fyr); far_shift = true; }
   }
-  if (!(Num<T>::ab(kx) < (T)1.0e9) || !(Num<T>::ab(ky) < (T)1.0e9)) {
+  // a shift of more than one cell: reject non-finite or absurd motion
+  if (far_shift && (!(Num<T>::ab(kx) < (T)1.0e9) || !(Num<T>::ab(ky) < (T)1.0e9))) {
     tl.status |= kStatusNaN;
     return NE + 1;
   }
