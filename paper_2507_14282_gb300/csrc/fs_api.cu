@@ -126,9 +126,10 @@ int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
   g->mover_per_tile = (int)mpt;
   g->mover_cap = (int)(mpt * g->ntiles);
   g->staging_cap = 1 << 16;
-  // shared-memory chunk: 512 particles (deeper prefetch pipeline) when the
-  // mean tile holds at most 256, else 1024
-  g->chunk = (cells_per_tile * p->ppc > 256) ? 1024 : 512;
+  // shared-memory chunk: FP32 takes 640 particles (a 512-particle mean tile
+  // in one chunk) unless the mean tile holds at most 256; FP64 takes 512
+  // (two CTAs per SM with its wider particles)
+  g->chunk = (p->precision == FS_FP32 && cells_per_tile * p->ppc > 256) ? 640 : 512;
   g->na = (tx + 3) * (p->dim == 2 ? ty + 3 : 1);
   g->nk = (tx + 2) * (p->dim == 2 ? ty + 2 : 1) + 2;
   const size_t smem = (p->precision == FS_FP64)

@@ -56,13 +56,13 @@ template <typename T>
 struct PushShape;
 template <>
 struct PushShape<float> {
-  static constexpr int kChunkSmall = 512, kStagesSmall = 4;
-  static constexpr int kChunkLarge = 1024, kStagesLarge = 2;
+  static constexpr int kChunkSmall = 512, kStagesSmall = 3;
+  static constexpr int kChunkLarge = 640, kStagesLarge = 2;
 };
 template <>
 struct PushShape<double> {
-  static constexpr int kChunkSmall = 512, kStagesSmall = 3;
-  static constexpr int kChunkLarge = 1024, kStagesLarge = 2;
+  static constexpr int kChunkSmall = 512, kStagesSmall = 2;
+  static constexpr int kChunkLarge = 512, kStagesLarge = 2;
 };
 
 template <typename T, int DIM>

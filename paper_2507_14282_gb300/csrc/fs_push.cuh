@@ -1,25 +1,24 @@
 // fs_push.cuh -- the fused particle step (gather, Boris, move, open wall,
 // faux shock, in-tile counting sort, CIC deposit), one persistent CTA per
-// group of tiles with the next chunk of particles prefetched into shared
+// group of tiles with the next chunks of particles prefetched into shared
 // memory by the TMA bulk-copy engine while the current one is processed.
 //
 // Per chunk (at most CH particles of one tile):
 //   1. wait for the chunk's bulk copies (its particle columns and the tile's
 //      packed E / Bbar nodes) on an mbarrier;
-//   2. push every particle in shared memory in place and give it a sort key:
-//      its new cell in the tile (interior cells first), a halo cell, FAR
-//      (moved more than one cell out of the tile) or REMOVED;
-//   3. deposit in push order, warp-cooperatively: the particles of a warp
-//      mostly share one cell, and for each distinct cell a transpose
-//      reduction of the lanes' corner contributions leaves one sum per value
-//      to add to the tile's node accumulator;
-//   4. counting sort: per-key counts and in-key ranks -> offsets by a warp
-//      scan;
-//   5. every thread writes its own particles at offset + rank: stayers to the
-//      tile's bucket of the output buffer in cell order, leavers to the
-//      tile's range of the mover list.
-// When a tile's last chunk is done its node accumulator is written out as
-// the tile's deposit partial (summed per node in a fixed order later).
+//   2. push every particle in place and give it a sort key: its new cell in
+//      the tile (interior cells first), a halo cell, FAR (moved more than
+//      one cell out of the tile) or REMOVED; lanes with the same key take
+//      consecutive ranks after one shared atomic per key;
+//   3. (barrier) each warp scans the key counts; every thread copies its
+//      particles into the key-sorted buffer;
+//   4. (barrier) the stage is refilled with a later chunk; coalesced writes
+//      from the sorted buffer: stayers to the tile's bucket of the output
+//      buffer, leavers to the tile's range of the mover list; the CIC deposit
+//      walks each key's contiguous range with a corner x split team per warp.
+// A tile's node accumulator is written out as its deposit partial during the
+// next chunk (two accumulators alternate between tiles), so each chunk costs
+// two block-wide barriers.
 #pragma once
 #include "fs_engine.cuh"
 
@@ -92,14 +91,16 @@ struct StepArgs {
 
 // ---------------------------------------------------------------- layout
 constexpr int kMaxStages = 4;
+constexpr int kWarps = kBlock / 32;
 
 template <typename T, int DIM>
 struct PushLayout {
   int TX, TY, NFX, NFY, AX, AY, NA, EX, EY, NE, NINT, NK, CH, NS;
   // stage 0's regions; stage b sits b * bstride bytes further
   size_t F[1], cell[1], ox[1], oy[1], vx[1], vy[1], vz[1], id[1];
-  size_t acc, kc, ko, e2k, k2e, desc, bar, pf, bytes;
-  size_t bstride;  // distance between the two chunk buffers
+  size_t sW, sV, sF, scell, sid;  // key-sorted buffer
+  size_t acc, kc, wk, e2k, k2e, desc, bar, pf, tally, bytes;
+  size_t bstride;  // distance between two chunk buffers
   __host__ __device__ static size_t take(size_t& o, size_t n) {
     o = (o + 15) / 16 * 16;
     const size_t r = o;
@@ -135,10 +136,18 @@ struct PushLayout {
     o = (o + 15) / 16 * 16;
     bstride = o - F[0];
     o += (size_t)(NS - 1) * bstride;
+    // the key-sorted copy of the chunk being finished: the four CIC corner
+    // weights, {vx, vy, vz, 0}, {fx, fy}, cell and id per particle
+    sW = take(o, sizeof(T) * 4 * CH);
+    sV = take(o, sizeof(T) * 4 * CH);
+    sF = take(o, sizeof(T) * 2 * CH);
+    scell = take(o, sizeof(int) * CH);
+    sid = take(o, sizeof(uint32_t) * CH);
     pf = take(o, 16);
-    acc = take(o, sizeof(typename Num<T>::acc) * 4 * NA);
-    kc = take(o, sizeof(int) * NK);
-    ko = take(o, sizeof(int) * (NK + 1));
+    tally = take(o, sizeof(unsigned long long) * 4 + sizeof(double) * 2);
+    acc = take(o, sizeof(typename Num<T>::acc) * 2 * 4 * NA);  // two tiles in flight
+    kc = take(o, sizeof(int) * 2 * NK);                         // two chunks in flight
+    wk = take(o, sizeof(int) * kWarps * (NK + 1));              // key offsets per warp
     e2k = take(o, sizeof(uint16_t) * NE);
     k2e = take(o, sizeof(int) * NE);
     bytes = (o + 127) / 128 * 128;
@@ -193,10 +202,57 @@ __device__ __forceinline__ int4 next_chunk(int4 c, int G, int ntiles, int CH,
 // One particle: CIC gather from the tile's node block F (local cell lx, ly),
 // Boris, move, x walls / faux shock. Returns the sort key. Counters and
 // energies are accumulated in the caller's registers.
+// One node of the packed field block (Ex Ey Ez Bx By Bz, two pad words) in
+// 16-byte loads; node blocks are 16-byte aligned in shared memory.
+__device__ __forceinline__ void load_node(const float* n, float (&v)[6]) {
+  const float4 a = reinterpret_cast<const float4*>(n)[0];
+  const float4 b = reinterpret_cast<const float4*>(n)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+__device__ __forceinline__ void load_node(const double* n, double (&v)[6]) {
+  const double2 a = reinterpret_cast<const double2*>(n)[0];
+  const double2 b = reinterpret_cast<const double2*>(n)[1];
+  const double2 c = reinterpret_cast<const double2*>(n)[2];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
+// 4- and 2-wide shared-memory accesses of T (16-byte aligned)
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st2(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void ld2(const float* p, float (&v)[2]) {
+  const float2 a = *reinterpret_cast<const float2*>(p);
+  v[0] = a.x; v[1] = a.y;
+}
+__device__ __forceinline__ void ld2(const double* p, double (&v)[2]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  v[0] = a.x; v[1] = a.y;
+}
+
+// Faux-shock and open-wall bookkeeping of one CTA (rare events): shared
+// memory, added to the global counters once at the end.
 struct PushTally {
-  long long inc, tr, ref, esc;
+  unsigned long long inc, tr, ref, esc;
   double fse, rem;
-  int status;
 };
 
 template <typename T, int DIM>
@@ -205,41 +261,82 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
                                         uint32_t& id, int i0, int j0, int TX, int TY,
                                         int EX, int EY, int NE, const uint16_t* e2k,
                                         const Geo& g, const Phys& ph, T dtdx, T dtdy,
-                                        T hdt, long long step, PushTally& tl) {
+                                        T hdt, long long step, PushTally* tl,
+                                        int& status, bool inner) {
   const int i = cell & 0xFFFF, j = cell >> 16;
   const int lx = i - i0, ly = j - j0;
-  if (lx < 0 || lx >= TX || ly < 0 || ly >= TY) {
-    tl.status |= kStatusBadCell;
+  if ((unsigned)lx >= (unsigned)TX || (unsigned)ly >= (unsigned)TY) {
+    status |= kStatusBadCell;
     return NE + 1;
   }
   T Ep[3], Bp[3];
   if (DIM == 1) {
     const T g0 = (T)1 - fx;
-    const T* n0 = F + lx * 8;
-    const T* n1 = n0 + 8;
+    T a[6], b[6];
+    load_node(F + lx * 8, a);
+    load_node(F + lx * 8 + 8, b);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      Ep[q] = fmaT(fx, n1[q], g0 * n0[q]);
-      Bp[q] = fmaT(fx, n1[3 + q], g0 * n0[3 + q]);
+      Ep[q] = fmaT(fx, b[q], g0 * a[q]);
+      Bp[q] = fmaT(fx, b[3 + q], g0 * a[3 + q]);
     }
   } else {
     const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
     const T w00 = gx0 * gy0, w10 = fx * gy0, w01 = gx0 * fy, w11 = fx * fy;
+    // node by node, in the order w00, w10, w01, w11 of the nested fma
     const T* n00 = F + (ly * NFX + lx) * 8;
-    const T* n10 = n00 + 8;
-    const T* n01 = n00 + NFX * 8;
-    const T* n11 = n01 + 8;
+    T v[6];
+    load_node(n00, v);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      Ep[q] = fmaT(w11, n11[q], fmaT(w01, n01[q], fmaT(w10, n10[q], w00 * n00[q])));
-      Bp[q] = fmaT(w11, n11[3 + q],
-                   fmaT(w01, n01[3 + q], fmaT(w10, n10[3 + q], w00 * n00[3 + q])));
+      Ep[q] = w00 * v[q];
+      Bp[q] = w00 * v[3 + q];
+    }
+    load_node(n00 + 8, v);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      Ep[q] = fmaT(w10, v[q], Ep[q]);
+      Bp[q] = fmaT(w10, v[3 + q], Bp[q]);
+    }
+    load_node(n00 + NFX * 8, v);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      Ep[q] = fmaT(w01, v[q], Ep[q]);
+      Bp[q] = fmaT(w01, v[3 + q], Bp[q]);
+    }
+    load_node(n00 + NFX * 8 + 8, v);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      Ep[q] = fmaT(w11, v[q], Ep[q]);
+      Bp[q] = fmaT(w11, v[3 + q], Bp[q]);
     }
   }
   boris<T>(vx, vy, vz, Ep, Bp, hdt);
   const T fxr = fmaT(vx, dtdx, fx);
   T fyr = fy;
   if (DIM == 2) fyr = fmaT(vy, dtdy, fy);
+  // Common case: a tile away from every box edge and a shift of at most one
+  // cell: no wall, wrap or far-mover handling can apply. Same values as the
+  // general path below (shift in {-1, 0, 1}, subtracted exactly).
+  if (inner && fxr >= (T)-1 && fxr < (T)2 && (DIM == 1 || (fyr >= (T)-1 && fyr < (T)2))) {
+    const bool xp = fxr >= (T)1, xm = fxr < (T)0;
+    const int ikx = xp ? 1 : (xm ? -1 : 0);
+    T fxn = fxr - (xp ? (T)1 : (xm ? (T)-1 : (T)0));
+    if (fxn >= (T)1) fxn = Num<T>::offmax;
+    int iky = 0;
+    if (DIM == 2) {
+      const bool yp = fyr >= (T)1, ym = fyr < (T)0;
+      iky = yp ? 1 : (ym ? -1 : 0);
+      T fyn = fyr - (yp ? (T)1 : (ym ? (T)-1 : (T)0));
+      if (fyn >= (T)1) fyn = Num<T>::offmax;
+      fy = fyn;
+    }
+    cell = ((j + iky) << 16) | (i + ikx);
+    fx = fxn;
+    const int lxn = lx + ikx, lyn = ly + iky;  // interior-relative
+    if ((unsigned)lxn < (unsigned)TX && (unsigned)lyn < (unsigned)TY) return lxn + lyn * TX;
+    return e2k[(lxn + 1) + (DIM == 2 ? (lyn + 1) * EX : 0)];
+  }
   // whole-cell shift floor(f): by comparison for |shift| <= 1 (the common
   // case), by floor otherwise; the same value either way
   T kx, ky = (T)0;
@@ -256,7 +353,7 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
   }
   // a shift of more than one cell: reject non-finite or absurd motion
   if (far_shift && (!(Num<T>::ab(kx) < (T)1.0e9) || !(Num<T>::ab(ky) < (T)1.0e9))) {
-    tl.status |= kStatusNaN;
+    status |= kStatusNaN;
     return NE + 1;
   }
   const T offmax = Num<T>::offmax;
@@ -283,20 +380,20 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
   if (g.bc_x == FS_BC_PERIODIC) {
     if (inew < 0 || inew >= g.nx) inew = wrap(inew, g.nx);
   } else if (inew >= g.nx) {
-    ++tl.esc;
-    tl.rem += kinetic(cr ? ph.w_cr : ph.w_th, (double)vx, (double)vy, (double)vz,
-                      ph.cellvol);
+    atomicAdd(&tl->esc, 1ull);
+    atomicAdd(&tl->rem, kinetic(cr ? ph.w_cr : ph.w_th, (double)vx, (double)vy, (double)vz,
+                                ph.cellvol));
     return NE + 1;
   } else if (inew < 0) {
     const int mode = cr ? FS_SHOCK : ph.fs_mode_thermal;
     const double wpd = cr ? ph.w_cr : ph.w_th;
-    ++tl.inc;
+    atomicAdd(&tl->inc, 1ull);
     double dvx = vx, dvy = vy, dvz = vz;
     const double e0 = kinetic(wpd, dvx, dvy, dvz, ph.cellvol);
     if (mode == FS_SHOCK &&
         fs_return(dvx, dvy, dvz, ph.u2, ph.fs_frame, ph.seed, id & kIdMask, step)) {
-      ++tl.ref;
-      tl.fse = __dadd_rn(tl.fse, __dsub_rn(kinetic(wpd, dvx, dvy, dvz, ph.cellvol), e0));
+      atomicAdd(&tl->ref, 1ull);
+      atomicAdd(&tl->fse, __dsub_rn(kinetic(wpd, dvx, dvy, dvz, ph.cellvol), e0));
       const double Xo = __dadd_rn((double)i, (double)fx);
       const double Xn = __dadd_rn((double)i, (double)fxr);
       const double gfr = __ddiv_rn(Xn, __dsub_rn(Xn, Xo));
@@ -313,8 +410,8 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
       vz = (T)dvz;
       id |= kIdReturned;
     } else {
-      ++tl.tr;
-      tl.rem = __dadd_rn(tl.rem, e0);
+      atomicAdd(&tl->tr, 1ull);
+      atomicAdd(&tl->rem, e0);
       return NE + 1;
     }
   }
@@ -358,86 +455,82 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
   bulk_g2s(sm + L.id[0] + bo, PI.id + first, 4 * m4, bar);
 }
 
-// Warp-cooperative CIC deposit of the lanes' particles (push order): for each
-// distinct cell key among the lanes, the lanes of that cell contribute their
-// corner values and a transpose reduction leaves value q(L) summed over the
-// warp in lane L; the owner lanes add to the tile's node accumulator.
+
+// CIC deposit of one key's particles, which sit contiguously in [b0, b1) of
+// the key-sorted chunk (W: corner weights, V: {vx, vy, vz, 0}). The warp
+// works as NC corners x SPL splits: lane (corner c, split s) sums corner c's
+// four quantities (weight, weight * v) over particles b0 + s, b0 + s + SPL,
+// ...; a transpose reduction over the splits then leaves each quantity's
+// total in one lane, which adds it to the tile's node accumulator. Each
+// contribution is formed as in the per-particle scheme, so in fixed point
+// the sums do not depend on the order.
+template <typename T>
+__device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T* W,
+                                         const T* V, int i, int c) {
+  const T cw = W[4 * i + c];
+  T v[4];
+  ld4(V + 4 * i, v);
+  acc[0] = acc[0] + to_acc(cw);
+  acc[1] = acc[1] + to_acc_prod(cw, v[0]);
+  acc[2] = acc[2] + to_acc_prod(cw, v[1]);
+  acc[3] = acc[3] + to_acc_prod(cw, v[2]);
+}
+
 template <typename T, int DIM>
-__device__ __forceinline__ void warp_deposit(typename Num<T>::acc* ACC, int NA, int AX,
-                                             const int* k2e, int key, bool active, T fx,
-                                             T fy, T wp, T vx, T vy, T vz, int lane) {
-  using A = typename Num<T>::acc;
-  constexpr int NV = 4 * (DIM == 2 ? 4 : 2);
-  unsigned todo = __ballot_sync(0xffffffffu, active);
-  if (!todo) return;
-  A val[NV];
-  if (DIM == 1) {
-    const T c0 = wp * ((T)1 - fx), c1 = wp * fx;
-    val[0] = to_acc(c0); val[1] = to_acc_prod(c0, vx);
-    val[2] = to_acc_prod(c0, vy); val[3] = to_acc_prod(c0, vz);
-    val[4] = to_acc(c1); val[5] = to_acc_prod(c1, vx);
-    val[6] = to_acc_prod(c1, vy); val[7] = to_acc_prod(c1, vz);
-  } else {
-    const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
-    const T cw[4] = {wp * (gx0 * gy0), wp * (fx * gy0), wp * (gx0 * fy), wp * (fx * fy)};
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      val[4 * cc + 0] = to_acc(cw[cc]);
-      val[4 * cc + 1] = to_acc_prod(cw[cc], vx);
-      val[4 * cc + 2] = to_acc_prod(cw[cc], vy);
-      val[4 * cc + 3] = to_acc_prod(cw[cc], vz);
-    }
+__device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, int AX,
+                                             int le, int b0, int b1, const T* W, const T* V,
+                                             int lane) {
+  using A_t = typename Num<T>::acc;
+  constexpr int NC = (DIM == 2) ? 4 : 2;
+  constexpr int SPL = 32 / NC;
+  const int s = lane % SPL, c = lane / SPL;
+  A_t acc[4] = {(A_t)0, (A_t)0, (A_t)0, (A_t)0};
+  int i = b0 + s;
+  for (; i + SPL < b1; i += 2 * SPL) {  // two particles in flight per lane
+    team_add<T>(acc, W, V, i, c);
+    team_add<T>(acc, W, V, i + SPL, c);
   }
-  int qi = 0;
+  if (i < b1) team_add<T>(acc, W, V, i, c);
+  // two halving levels leave one quantity per lane, the rest add pairs
   {
-    int h = NV / 2, off = 16;
-    while (h >= 1) {
-      if (lane & off) qi += h;
-      h >>= 1;
-      off >>= 1;
+    const bool up = (s & (SPL / 2)) != 0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const A_t send = up ? acc[q] : acc[q + 2];
+      const A_t keep = up ? acc[q + 2] : acc[q];
+      acc[q] = keep + shfl_xor(send, SPL / 2);
     }
   }
-  const bool owner = (NV == 16) ? ((lane & 1) == 0) : ((lane & 3) == 0);
-  while (todo) {
-    const int lead = __ffs(todo) - 1;
-    const int kk = __shfl_sync(0xffffffffu, key, lead);
-    const bool mine = active && (key == kk);
-    todo &= ~__ballot_sync(0xffffffffu, mine);
-    A w[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) w[q] = mine ? val[q] : (A)0;
-    int half = NV / 2;
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      if (half >= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int q = 0; q < NV / 2; ++q) {
-          if (q < half) {
-            const A send = up ? w[q] : w[q + half];
-            const A keep = up ? w[q + half] : w[q];
-            w[q] = keep + shfl_xor(send, off);
-          }
-        }
-        half >>= 1;
-      } else {
-        w[0] = w[0] + shfl_xor(w[0], off);
-      }
-    }
-    if (owner) {
-      const int le = k2e[kk];
-      const int a00 = (le & 0xFFFF) + (le >> 16) * AX;
-      const int corner = qi >> 2, qty = qi & 3;
-      const int an = (DIM == 1) ? a00 + corner : a00 + (corner & 1) + (corner >> 1) * AX;
-      atomic_acc(&ACC[qty * NA + an], w[0]);
-    }
+  {
+    const bool up = (s & (SPL / 4)) != 0;
+    const A_t send = up ? acc[0] : acc[1];
+    const A_t keep = up ? acc[1] : acc[0];
+    acc[0] = keep + shfl_xor(send, SPL / 4);
   }
+#pragma unroll
+  for (int off = SPL / 8; off >= 1; off >>= 1) acc[0] = acc[0] + shfl_xor(acc[0], off);
+  if ((s & (SPL / 4 - 1)) == 0) {
+    const int q = ((s & (SPL / 2)) ? 2 : 0) + ((s & (SPL / 4)) ? 1 : 0);
+    const int a00 = (le & 0xFFFF) + (le >> 16) * AX;
+    const int an = a00 + (c & 1) + ((DIM == 2) ? (c >> 1) * AX : 0);
+    atomic_acc(&ACC[q * NA + an], acc[0]);
+  }
+}
+
+// Every stage holds a chunk not yet consumed.
+template <typename T, int DIM>
+__device__ __forceinline__ void drain_stages(unsigned char* sm, const PushLayout<T, DIM>& L,
+                                             uint32_t parity, int ntiles) {
+  const int4* desc = (const int4*)(sm + L.desc);
+  uint64_t* bar = (uint64_t*)(sm + L.bar);
+  for (int o = 0; o < L.NS; ++o)
+    if (desc[o].x < ntiles && desc[o].z > 0) mbar_wait(&bar[o], (parity >> o) & 1u);
 }
 
 template <typename T, int DIM, int CH, int NS>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPtrs<T> d, StepArgs a) {
   using A = typename Num<T>::acc;
-  constexpr int PPT = CH / kBlock;
+  constexpr int PPT = (CH + kBlock - 1) / kBlock;
   extern __shared__ __align__(128) unsigned char sm[];
   const Geo g = a.g;
   const Phys ph = a.ph;
@@ -446,13 +539,14 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
             NK = L.NK, NA = L.NA, AX = L.AX;
   uint64_t* bar = (uint64_t*)(sm + L.bar);
   int4* desc = (int4*)(sm + L.desc);
-  A* ACC = (A*)(sm + L.acc);
-  int* kcount = (int*)(sm + L.kc);
-  int* koff = (int*)(sm + L.ko);
+  A* ACC0 = (A*)(sm + L.acc);
+  int* kc0 = (int*)(sm + L.kc);
   uint16_t* e2k = (uint16_t*)(sm + L.e2k);
   int* k2e = (int*)(sm + L.k2e);
   int* pf = (int*)(sm + L.pf);
+  PushTally* tl = (PushTally*)(sm + L.tally);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int* wk = (int*)(sm + L.wk) + warp * (NK + 1);
   const int G = gridDim.x;
   const int* cnt_in = d.cnt[a.in];
   const Parts<T> PI = d.P[a.in];
@@ -479,12 +573,13 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
     e2k[e] = (uint16_t)key;
     k2e[key] = lx | (ly << 16);
   }
-  for (int k = tid; k < 4 * NA; k += kBlock) ACC[k] = (A)0;
-  for (int k = tid; k < NK; k += kBlock) kcount[k] = 0;
+  for (int k = tid; k < 2 * 4 * NA; k += kBlock) ACC0[k] = (A)0;
+  for (int k = tid; k < 2 * NK; k += kBlock) kc0[k] = 0;
 
   if (tid == 0) {
     for (int b = 0; b < NS; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
+    *tl = PushTally{0, 0, 0, 0, 0.0, 0.0};
   }
   __syncthreads();
   if (tid == 0) {
@@ -507,28 +602,27 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
 
   uint32_t parity = 0;  // bit b: phase parity expected next on stage b
   int outRun = 0, movRun = 0;
-  PushTally tl = {0, 0, 0, 0, 0.0, 0.0, 0};
+  int tiles_seen = 0, tpar = 0;  // accumulator buffer of the current tile
+  int pend = -1, pend_par = 0;   // tile whose partial is written next chunk
+  int status = 0;
 
-  for (int b = 0;; b = (b + 1 == NS) ? 0 : b + 1) {
+  int b = 0;
+  for (int ci = 0;; ++ci, b = (b + 1 == NS) ? 0 : b + 1) {
     const int4 c = desc[b];
     if (c.x >= g.ntiles) break;
     const int t = c.x, m = c.z;
+    if (c.y == 0) tpar = (tiles_seen++) & 1;
+    bool ok = true;
     if (m > 0) {
-      const bool ok = mbar_wait(&bar[b], (parity >> b) & 1u);
+      ok = mbar_wait(&bar[b], (parity >> b) & 1u);
       parity ^= 1u << b;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-          atomicOr(&d.ctr->status, kStatusTimeout);
-          // let the other stages' copies land before the CTA exits (bounded)
-          for (int o = 0; o < NS; ++o)
-            if (o != b && desc[o].x < g.ntiles && desc[o].z > 0)
-              mbar_wait(&bar[o], (parity >> o) & 1u);
-        }
-        return;
-      }
     }
+    const int mloc = ok ? m : 0;  // a thread whose wait gave up touches nothing
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int i0 = tx * TX, j0 = ty * TY;
+    // no particle of this tile can reach a box edge by a one-cell shift
+    const bool inner =
+        i0 >= 1 && i0 + TX < g.nx && (DIM == 1 || (j0 >= 1 && j0 + TY < g.ny));
     const size_t bo = (size_t)b * L.bstride;
     const T* F = (const T*)(sm + L.F[0] + bo);
     int* sc = (int*)(sm + L.cell[0] + bo);
@@ -538,28 +632,30 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
     T* svy = (T*)(sm + L.vy[0] + bo);
     T* svz = (T*)(sm + L.vz[0] + bo);
     uint32_t* sid = (uint32_t*)(sm + L.id[0] + bo);
+    int* kc = kc0 + (ci & 1) * NK;
+    A* ACC = ACC0 + tpar * 4 * NA;
 
-    // ---- push in place, deposit (warp-cooperative, push order), key, rank
-    int rk[PPT], ky[PPT];
+    // ---- push in place, key, rank within the key
+    int ky[PPT], rk[PPT];
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
       const int p = tid + r * kBlock;
-      rk[r] = 0;
       ky[r] = NE + 1;
+      rk[r] = 0;
       if (r * kBlock >= m) continue;  // whole block past the chunk: uniform skip
-      int key = NE + 1;
-      T fx = (T)0, fy = (T)0, vx = (T)0, vy = (T)0, vz = (T)0;
-      uint32_t id = 0;
-      if (p < m) {
+      int key = -1;
+      if (p < mloc) {
         int cell = sc[p];
-        fx = sx[p];
-        fy = (DIM == 2) ? sy[p] : (T)0;
-        vx = svx[p];
-        vy = svy[p];
-        vz = svz[p];
-        id = sid[p];
+        T fx = sx[p];
+        T fy = (DIM == 2) ? sy[p] : (T)0;
+        T vx = svx[p], vy = svy[p], vz = svz[p];
+        uint32_t id = sid[p];
         key = push_one<T, DIM>(F, L.NFX, cell, fx, fy, vx, vy, vz, id, i0, j0, TX, TY, EX,
-                               EY, NE, e2k, g, ph, dtdx, dtdy, hdt, step, tl);
+                               EY, NE, e2k, g, ph, dtdx, dtdy, hdt, step, tl,
+                               status, inner);
+        if (key == NE)  // far mover: straight to the global far sums
+          deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, fx, fy,
+                              (id & kIdCR) ? wcr : wth, vx, vy, vz);
         sc[p] = cell;
         sx[p] = fx;
         if (DIM == 2) sy[p] = fy;
@@ -567,73 +663,67 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
         svy[p] = vy;
         svz[p] = vz;
         sid[p] = id;
-        rk[r] = atomicAdd(&kcount[key], 1);
         ky[r] = key;
-        if (key == NE) {  // far mover: deposit straight to the global far sums
-          deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, fx, fy,
-                              (id & kIdCR) ? wcr : wth, vx, vy, vz);
-        }
       }
-      const T wp = (id & kIdCR) ? wcr : wth;
-      warp_deposit<T, DIM>(ACC, NA, AX, k2e, key, key < NE, fx, fy, wp, vx, vy, vz, lane);
+      // lanes with equal keys take consecutive ranks after one atomic
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      int base = 0;
+      if (lane == leader && key >= 0) base = atomicAdd(&kc[key], __popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      rk[r] = base + __popc(peers & ((1u << lane) - 1u));
     }
-    __syncthreads();
-    if (warp == 0) warp_scan_excl(kcount, koff, NK, lane);
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(&d.ctr->status, kStatusTimeout);
+        drain_stages<T, DIM>(sm, L, parity ^ (1u << b), g.ntiles);
+      }
+      return;
+    }
 
-    // ---- write: stayers to the tile's bucket in cell order, leavers to the
-    //      tile's range of the mover list
-    const int S = koff[NINT];
-    const int Lv = koff[NE + 1] - S;
-    const int obase = d.tile_base[t] + outRun;
-    const int mbase = t * g.mover_per_tile + movRun;
+    // ---- the previous tile's deposit partial is complete: write it out
+    if (pend >= 0) {
+      A* part = (A*)d.partial + (size_t)pend * 4 * NA;
+      A* Q = ACC0 + pend_par * 4 * NA;
+      for (int q = tid; q < 4 * NA; q += kBlock) {
+        part[q] = Q[q];
+        Q[q] = (A)0;
+      }
+      pend = -1;
+    }
+    for (int q = tid; q < NK; q += kBlock) kc0[((ci + 1) & 1) * NK + q] = 0;
+    // ---- key offsets (each warp its own copy); copy into key order
+    warp_scan_excl(kc, wk, NK, lane);
+    __syncwarp();
+    int* oc = (int*)(sm + L.scell);
+    uint32_t* oid = (uint32_t*)(sm + L.sid);
+    T* oW = (T*)(sm + L.sW);
+    T* oV = (T*)(sm + L.sV);
+    T* oF = (T*)(sm + L.sF);
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
-      const int p = tid + r * kBlock;
       const int key = ky[r];
-      if (p >= m || key > NE) continue;
-      const int pos = koff[key] + rk[r];
-      int gi;
-      Parts<T> dst;
-      if (pos < S) {
-        gi = obase + pos;
-        dst = PO;
+      if (key > NE) continue;
+      const int p = tid + r * kBlock;
+      const int pos = wk[key] + rk[r];
+      const uint32_t id = sid[p];
+      const T fx = sx[p], fy = (DIM == 2) ? sy[p] : (T)0;
+      const T wp = (id & kIdCR) ? wcr : wth;
+      oc[pos] = sc[p];
+      oid[pos] = id;
+      st2(oF + 2 * pos, fx, fy);
+      st4(oV + 4 * pos, svx[p], svy[p], svz[p], (T)0);
+      // corner weights: wp * (gx * gy), corners (0,0) (1,0) (0,1) (1,1)
+      const T gx0 = (T)1 - fx;
+      if (DIM == 2) {
+        const T gy0 = (T)1 - fy;
+        st4(oW + 4 * pos, wp * (gx0 * gy0), wp * (fx * gy0), wp * (gx0 * fy), wp * (fx * fy));
       } else {
-        const int slot = movRun + (pos - S);
-        if (slot >= g.mover_per_tile) {
-          tl.status |= kStatusCapacity;
-          continue;
-        }
-        gi = mbase + (pos - S);
-        dst = d.M;
+        st4(oW + 4 * pos, wp * gx0, wp * fx, (T)0, (T)0);
       }
-      dst.cell[gi] = sc[p];
-      dst.ox[gi] = sx[p];
-      if (DIM == 2) dst.oy[gi] = sy[p];
-      dst.vx[gi] = svx[p];
-      dst.vy[gi] = svy[p];
-      dst.vz[gi] = svz[p];
-      dst.id[gi] = sid[p];
-    }
-    outRun += S;
-    movRun += Lv;
-    for (int q = tid; q < NK; q += kBlock) kcount[q] = 0;
-    if (c.y + m >= c.w) {
-      // last chunk of tile t: its deposit partial, output and mover counts
-      A* part = (A*)d.partial + (size_t)t * 4 * NA;
-      for (int q = tid; q < 4 * NA; q += kBlock) {
-        part[q] = ACC[q];
-        ACC[q] = (A)0;
-      }
-      if (tid == 0) {
-        d.cnt[a.out][t] = outRun;
-        d.mcnt[t] = min(movRun, g.mover_per_tile);
-      }
-      outRun = 0;
-      movRun = 0;
     }
     __syncthreads();
-    // stage b is free: prefetch the chunk after the most recently issued one
+    // ---- stage b is free: prefetch the chunk after the most recently issued one
     if (tid == 0) {
       fence_proxy_async_smem();
       int4* lastc = (int4*)(sm + L.desc + NS * sizeof(int4));
@@ -641,17 +731,96 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
       *lastc = nc;
       issue_chunk<T, DIM>(sm, L, b, nc, d, PI, g);
     }
+
+    // ---- write: stayers to the tile's bucket in cell order, leavers to the
+    //      tile's range of the mover list
+    const int S = wk[NINT];
+    const int Lv = wk[NE + 1] - S;
+    {
+      const int obase = d.tile_base[t] + outRun;
+      for (int i = tid; i < S; i += kBlock) {
+        const int gi = obase + i;
+        T vf[2], vv[4];
+        ld2(oF + 2 * i, vf);
+        ld4(oV + 4 * i, vv);
+        PO.cell[gi] = oc[i];
+        PO.ox[gi] = vf[0];
+        if (DIM == 2) PO.oy[gi] = vf[1];
+        PO.vx[gi] = vv[0];
+        PO.vy[gi] = vv[1];
+        PO.vz[gi] = vv[2];
+        PO.id[gi] = oid[i];
+      }
+      const int room = g.mover_per_tile - movRun;
+      const int nm = Lv < room ? Lv : (room > 0 ? room : 0);
+      if (nm < Lv) status |= kStatusCapacity;
+      const int mb = t * g.mover_per_tile + movRun;
+      for (int i = tid; i < nm; i += kBlock) {
+        const int gi = mb + i, si = S + i;
+        T vf[2], vv[4];
+        ld2(oF + 2 * si, vf);
+        ld4(oV + 4 * si, vv);
+        d.M.cell[gi] = oc[si];
+        d.M.ox[gi] = vf[0];
+        if (DIM == 2) d.M.oy[gi] = vf[1];
+        d.M.vx[gi] = vv[0];
+        d.M.vy[gi] = vv[1];
+        d.M.vz[gi] = vv[2];
+        d.M.id[gi] = oid[si];
+      }
+    }
+    // ---- deposit in key order: warp w takes an equal share of the sorted
+    //      deposited range [0, offset of FAR) and each key's part of it
+    {
+      const int nd = wk[NE];
+      const int r0 = (int)(((long long)nd * warp) / kWarps);
+      const int r1 = (int)(((long long)nd * (warp + 1)) / kWarps);
+      // first key whose range reaches past r0
+      int k = 0;
+      for (int kb = 0; kb < NE; kb += 32) {
+        const int kk = kb + lane;
+        const unsigned hit = __ballot_sync(0xffffffffu, kk < NE && wk[kk + 1] > r0);
+        if (hit) {
+          k = kb + __ffs(hit) - 1;
+          break;
+        }
+        k = NE;
+      }
+      for (; k < NE && wk[k] < r1; ++k) {
+        const int b0 = max(wk[k], r0), b1 = min(wk[k + 1], r1);
+        if (b0 < b1) team_deposit<T, DIM>(ACC, NA, AX, k2e[k], b0, b1, oW, oV, lane);
+      }
+    }
+    outRun += S;
+    movRun += Lv;
+    if (c.y + m >= c.w) {
+      // last chunk of tile t: output and mover counts now, partial next chunk
+      if (tid == 0) {
+        d.cnt[a.out][t] = outRun;
+        d.mcnt[t] = min(movRun, g.mover_per_tile);
+      }
+      pend = t;
+      pend_par = tpar;
+      outRun = 0;
+      movRun = 0;
+    }
+  }
+  __syncthreads();
+  if (pend >= 0) {
+    A* part = (A*)d.partial + (size_t)pend * 4 * NA;
+    const A* Q = ACC0 + pend_par * 4 * NA;
+    for (int q = tid; q < 4 * NA; q += kBlock) part[q] = Q[q];
   }
 
-  if (tl.inc | tl.esc) {
-    if (tl.inc) atomicAdd(&d.ctr->incident, (unsigned long long)tl.inc);
-    if (tl.tr) atomicAdd(&d.ctr->transmitted, (unsigned long long)tl.tr);
-    if (tl.ref) atomicAdd(&d.ctr->reflected, (unsigned long long)tl.ref);
-    if (tl.esc) atomicAdd(&d.ctr->escaped, (unsigned long long)tl.esc);
-    if (tl.fse != 0.0) atomicAdd(&d.ctr->fs_energy, tl.fse);
-    if (tl.rem != 0.0) atomicAdd(&d.ctr->removed_energy, tl.rem);
+  if (status) atomicOr(&d.ctr->status, status);
+  if (tid == 0 && (tl->inc | tl->esc)) {
+    if (tl->inc) atomicAdd(&d.ctr->incident, tl->inc);
+    if (tl->tr) atomicAdd(&d.ctr->transmitted, tl->tr);
+    if (tl->ref) atomicAdd(&d.ctr->reflected, tl->ref);
+    if (tl->esc) atomicAdd(&d.ctr->escaped, tl->esc);
+    if (tl->fse != 0.0) atomicAdd(&d.ctr->fs_energy, tl->fse);
+    if (tl->rem != 0.0) atomicAdd(&d.ctr->removed_energy, tl->rem);
   }
-  if (tl.status) atomicOr(&d.ctr->status, tl.status);
 }
 
 }  // namespace fsx
