@@ -124,7 +124,9 @@ struct PushLayout {
     NS = ns;
     size_t o = 0;
     bar = take(o, kMaxStages * sizeof(unsigned long long));
-    desc = take(o, (kMaxStages + 1) * sizeof(int4));
+    // per stage {tile, first particle, count, tile count} and {i0, j0,
+    // inner-tile flag, tile base}; then the last chunk issued
+    desc = take(o, (2 * kMaxStages + 1) * sizeof(int4));
     F[0] = take(o, sizeof(T) * 8 * NFX * NFY);
     cell[0] = take(o, sizeof(int) * CH);
     ox[0] = take(o, sizeof(T) * CH);
@@ -434,10 +436,15 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
                                             const Parts<T>& PI, const Geo& g) {
   int4* desc = (int4*)(sm + L.desc);
   uint64_t* bar = (uint64_t*)(sm + L.bar) + b;
-  desc[b] = c;
-  if (c.x >= g.ntiles || c.z <= 0) return;
+  desc[2 * b] = c;
+  if (c.x >= g.ntiles) return;
   const int tx = c.x % g.ntx, ty = c.x / g.ntx;
   const int i0 = tx * L.TX, j0 = ty * L.TY;
+  // no particle of the tile can reach a box edge by a one-cell shift
+  const int inner =
+      i0 >= 1 && i0 + L.TX < g.nx && (DIM == 1 || (j0 >= 1 && j0 + L.TY < g.ny));
+  desc[2 * b + 1] = make_int4(i0, j0, inner, d.tile_base[c.x]);
+  if (c.z <= 0) return;
   const size_t bo = (size_t)b * L.bstride;
   mbar_arrive_expect_tx(bar, L.chunk_bytes(c.z));
   const uint32_t row = (uint32_t)(sizeof(T) * 8 * L.NFX);
@@ -524,7 +531,7 @@ __device__ __forceinline__ void drain_stages(unsigned char* sm, const PushLayout
   const int4* desc = (const int4*)(sm + L.desc);
   uint64_t* bar = (uint64_t*)(sm + L.bar);
   for (int o = 0; o < L.NS; ++o)
-    if (desc[o].x < ntiles && desc[o].z > 0) mbar_wait(&bar[o], (parity >> o) & 1u);
+    if (desc[2 * o].x < ntiles && desc[2 * o].z > 0) mbar_wait(&bar[o], (parity >> o) & 1u);
 }
 
 template <typename T, int DIM, int CH, int NS>
@@ -596,7 +603,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
       issue_chunk<T, DIM>(sm, L, b, c, d, PI, g);
       if (b + 1 < NS) c = next_chunk(c, G, g.ntiles, CH, cnt_in, g.tile_cap, pf);
     }
-    *(int4*)(sm + L.desc + NS * sizeof(int4)) = c;  // the last chunk issued
+    *(int4*)(sm + L.desc + 2 * NS * sizeof(int4)) = c;  // the last chunk issued
   }
   __syncthreads();
 
@@ -608,8 +615,10 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
 
   int b = 0;
   for (int ci = 0;; ++ci, b = (b + 1 == NS) ? 0 : b + 1) {
-    const int4 c = desc[b];
+    const int4 c = desc[2 * b];
     if (c.x >= g.ntiles) break;
+    const int i0 = desc[2 * b + 1].x, j0 = desc[2 * b + 1].y;
+    const bool inner = desc[2 * b + 1].z != 0;
     const int t = c.x, m = c.z;
     if (c.y == 0) tpar = (tiles_seen++) & 1;
     bool ok = true;
@@ -618,11 +627,6 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
       parity ^= 1u << b;
     }
     const int mloc = ok ? m : 0;  // a thread whose wait gave up touches nothing
-    const int tx = t % g.ntx, ty = t / g.ntx;
-    const int i0 = tx * TX, j0 = ty * TY;
-    // no particle of this tile can reach a box edge by a one-cell shift
-    const bool inner =
-        i0 >= 1 && i0 + TX < g.nx && (DIM == 1 || (j0 >= 1 && j0 + TY < g.ny));
     const size_t bo = (size_t)b * L.bstride;
     const T* F = (const T*)(sm + L.F[0] + bo);
     int* sc = (int*)(sm + L.cell[0] + bo);
@@ -692,6 +696,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
       pend = -1;
     }
     for (int q = tid; q < NK; q += kBlock) kc0[((ci + 1) & 1) * NK + q] = 0;
+    const int tbase = desc[2 * b + 1].w;  // read before the stage is refilled
     // ---- key offsets (each warp its own copy); copy into key order
     warp_scan_excl(kc, wk, NK, lane);
     __syncwarp();
@@ -726,7 +731,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
     // ---- stage b is free: prefetch the chunk after the most recently issued one
     if (tid == 0) {
       fence_proxy_async_smem();
-      int4* lastc = (int4*)(sm + L.desc + NS * sizeof(int4));
+      int4* lastc = (int4*)(sm + L.desc + 2 * NS * sizeof(int4));
       const int4 nc = next_chunk(*lastc, G, g.ntiles, CH, cnt_in, g.tile_cap, pf);
       *lastc = nc;
       issue_chunk<T, DIM>(sm, L, b, nc, d, PI, g);
@@ -737,7 +742,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
     const int S = wk[NINT];
     const int Lv = wk[NE + 1] - S;
     {
-      const int obase = d.tile_base[t] + outRun;
+      const int obase = tbase + outRun;
       for (int i = tid; i < S; i += kBlock) {
         const int gi = obase + i;
         T vf[2], vv[4];
