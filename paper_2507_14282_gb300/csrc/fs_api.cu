@@ -213,6 +213,8 @@ int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
   L->n = take(T * nn);
   L->u = take(3 * T * nn);
   L->J = take(3 * T * nn);
+  // FP64 only: per-step Ohm's-law terms that depend on n alone
+  L->pre = take(p->precision == FS_FP64 ? 3 * T * nn : 0);
   L->partial = take(A * 4 * (size_t)g->na * g->ntiles);
   L->far = take(A * 4 * nn);
   L->acc = take(8 * (size_t)p->ny);
@@ -494,7 +496,10 @@ int fs_step(fs_handle* h, int nsteps) {
   Sim* s = &h->sim;
   if (s->sticky) return s->sticky;
   const bool inj = s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable);
-  const long long per_step = 1 + 1 + (inj ? 3 : 0) + 1 + 8LL * s->p.n_sub + 1 + 1;
+  // push, movers, injection (3), moments, [FP64: Ohm density terms],
+  // 2 x 4 x n_sub field stages, final Ohm, step end
+  const long long per_step = 1 + 1 + (inj ? 3 : 0) + 1 + (s->p.precision == FS_FP64 ? 1 : 0) +
+                             8LL * s->p.n_sub + 1 + 1;
   constexpr int kSet = FS_NPHASES + 1;
   if (!h->profiling && s->p.use_graph && s->steps_direct > 0 && !s->graphs_ready) {
     int r = build_graphs(s);

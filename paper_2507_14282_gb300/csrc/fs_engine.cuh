@@ -543,27 +543,68 @@ __global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
 // cells (and a mirrored density gradient), periodic boxes wrap.
 // With G != nullptr also packs (E, Bbar) per node, plus a ghost row ny
 // (copy of row 0) and, in a periodic box, a ghost column nx (copy of 0).
+// With pre != nullptr the density terms come from k_ohm_pre (same values).
 // ------------------------------------------------------------------------
+// The density terms of Ohm's law at node (i, j), fixed while n is: 1/n and
+// the pressure terms -(T_e dn/dx), -(T_e dn/dy) (two-point differences, a
+// mirrored density gradient at the x walls, periodic wrap).
+template <typename T, int DIM>
+__device__ __forceinline__ void density_terms(const T* __restrict__ nN, int i, int j,
+                                              const Geo& g, const Phys& ph, T& inv_n,
+                                              T& pgx, T& pgy) {
+  const int nx = g.nx, ny = g.ny, nxn = g.nxn;
+  const bool per = (g.bc_x == FS_BC_PERIODIC);
+  const T te = (T)ph.te;
+  auto nxo = [&](int c) {
+    if (per) return wrap(c, nx);
+    if (c < 0) return -c;
+    if (c > nx) return 2 * nx - c;
+    return c;
+  };
+  T dnx, dny;
+  if (DIM == 1) {
+    dnx = (nN[nxo(i + 1)] - nN[nxo(i - 1)]) * (T)ph.hdx;
+    dny = (T)0;
+  } else {
+    dnx = (nN[j * nxn + nxo(i + 1)] - nN[j * nxn + nxo(i - 1)]) * (T)ph.hdx;
+    dny = (nN[wrap(j + 1, ny) * nxn + i] - nN[wrap(j - 1, ny) * nxn + i]) * (T)ph.hdy;
+  }
+  inv_n = (T)1 / nN[j * nxn + i];
+  pgx = -(te * dnx);
+  pgy = -(te * dny);
+}
+
+// Writes density_terms for every node once per step (n is fixed during the
+// field substeps): pre = [1/n][-(T_e dn/dx)][-(T_e dn/dy)] planes.
+template <typename T, int DIM>
+__global__ void k_ohm_pre(const T* __restrict__ nN, T* __restrict__ pre, Geo g, Phys ph) {
+  const int nxn = g.nxn;
+  const int nn = nxn * g.ny;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += gridDim.x * blockDim.x) {
+    const int i = q % nxn, j = q / nxn;
+    T inv_n, pgx, pgy;
+    density_terms<T, DIM>(nN, i, j, g, ph, inv_n, pgx, pgy);
+    pre[q] = inv_n;
+    pre[nn + q] = pgx;
+    pre[2 * nn + q] = pgy;
+  }
+}
+
 template <typename T, int DIM>
 __global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
-                      const T* __restrict__ uN, T* __restrict__ Eo,
-                      T* __restrict__ Bbo, T* __restrict__ G, Geo g, Phys ph) {
+                      const T* __restrict__ uN, const T* __restrict__ pre,
+                      T* __restrict__ Eo, T* __restrict__ Bbo, T* __restrict__ G, Geo g,
+                      Phys ph) {
   const int nx = g.nx, ny = g.ny, nxn = g.nxn;
   const int nc = nx * ny, nn = nxn * ny;
-  const T hdx = (T)ph.hdx, hdy = (T)ph.hdy, idx = (T)ph.idx, te = (T)ph.te;
+  const T hdx = (T)ph.hdx, hdy = (T)ph.hdy, idx = (T)ph.idx;
   const T jcr = (T)ph.jcr, eta = (T)ph.eta;
   const bool per = (g.bc_x == FS_BC_PERIODIC);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nn;
        q += gridDim.x * blockDim.x) {
     const int i = q % nxn, j = q / nxn;
     auto cxo = [&](int c) { return per ? wrap(c, nx) : min(max(c, 0), nx - 1); };
-    auto nxo = [&](int c) {
-      if (per) return wrap(c, nx);
-      if (c < 0) return -c;
-      if (c > nx) return 2 * nx - c;
-      return c;
-    };
-    T bbx, bby, bbz, cxv, cyv, czv, dnx, dny;
+    T bbx, bby, bbz, cxv, cyv, czv;
     if (DIM == 1) {
       const int im = cxo(i - 1), ip = cxo(i);
       const T bmx = Bc[im], bpx = Bc[ip];
@@ -577,8 +618,6 @@ __global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
       cxv = (T)0;
       cyv = -dbz;
       czv = dby;
-      dnx = (nN[nxo(i + 1)] - nN[nxo(i - 1)]) * hdx;
-      dny = (T)0;
     } else {
       const int im = cxo(i - 1), ip = cxo(i);
       const int jm = wrap(j - 1, ny), jp = j;
@@ -602,21 +641,25 @@ __global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
       cxv = dybz;
       cyv = -dxbz;
       czv = dxby - dybx;
-      dnx = (nN[j * nxn + nxo(i + 1)] - nN[j * nxn + nxo(i - 1)]) * hdx;
-      dny = (nN[wrap(j + 1, ny) * nxn + i] - nN[wrap(j - 1, ny) * nxn + i]) * hdy;
     }
-    const T n = nN[q];
+    T inv_n, pgx, pgy;
+    if (pre) {
+      inv_n = pre[q];
+      pgx = pre[nn + q];
+      pgy = pre[2 * nn + q];
+    } else {
+      density_terms<T, DIM>(nN, i, j, g, ph, inv_n, pgx, pgy);
+    }
     const T ux = uN[q], uy = uN[nn + q], uz = uN[2 * nn + q];
     const T ax = cxv - jcr, ay = cyv, az = czv;
-    const T inv_n = (T)1 / n;
     const T cax = fmaT(ay, bbz, -(az * bby));
     const T cay = fmaT(az, bbx, -(ax * bbz));
     const T caz = fmaT(ax, bby, -(ay * bbx));
     const T cux = fmaT(uy, bbz, -(uz * bby));
     const T cuy = fmaT(uz, bbx, -(ux * bbz));
     const T cuz = fmaT(ux, bby, -(uy * bbx));
-    T ex = fmaT(-(te * dnx), inv_n, fmaT(cax, inv_n, -cux));
-    T ey = fmaT(-(te * dny), inv_n, fmaT(cay, inv_n, -cuy));
+    T ex = fmaT(pgx, inv_n, fmaT(cax, inv_n, -cux));
+    T ey = fmaT(pgy, inv_n, fmaT(cay, inv_n, -cuy));
     T ez = fmaT(caz, inv_n, -cuz);
     if (ph.eta != 0.0) {
       ex = ex + eta * cxv;

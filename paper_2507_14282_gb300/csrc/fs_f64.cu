@@ -59,16 +59,16 @@ void noalloc_launch(const fsx::Geo& g, const fsx::Phys& ph, int n_sub, double* B
   double* Es = scr + 6 * nc;
   const int gn = grid_for(nn), gc = grid_for(nc);
   for (int sub = 0; sub < n_sub; ++sub) {
-    k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(B, n, u, Es, nullptr, nullptr, g, ph);
+    k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(B, n, u, nullptr, Es, nullptr, nullptr, g, ph);
     k_faraday<double, DIM><<<gc, kBlock, 0, st>>>(Es, B, Bs, Bsum, 1, g, ph);
-    k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(Bs, n, u, Es, nullptr, nullptr, g, ph);
+    k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(Bs, n, u, nullptr, Es, nullptr, nullptr, g, ph);
     k_faraday<double, DIM><<<gc, kBlock, 0, st>>>(Es, B, Bs, Bsum, 2, g, ph);
-    k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(Bs, n, u, Es, nullptr, nullptr, g, ph);
+    k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(Bs, n, u, nullptr, Es, nullptr, nullptr, g, ph);
     k_faraday<double, DIM><<<gc, kBlock, 0, st>>>(Es, B, Bs, Bsum, 3, g, ph);
-    k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(Bs, n, u, Es, nullptr, nullptr, g, ph);
+    k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(Bs, n, u, nullptr, Es, nullptr, nullptr, g, ph);
     k_faraday<double, DIM><<<gc, kBlock, 0, st>>>(Es, B, Bs, Bsum, 4, g, ph);
   }
-  k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(B, n, u, E, nullptr, nullptr, g, ph);
+  k_ohm<double, DIM><<<gn, kBlock, 0, st>>>(B, n, u, nullptr, E, nullptr, nullptr, g, ph);
 }
 
 }  // namespace

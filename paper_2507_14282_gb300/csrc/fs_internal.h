@@ -77,7 +77,7 @@ struct Phys {
 struct Layout {
   size_t part[2][7], mov[7], stg[7];
   size_t tile_base, cnt[2], mcnt;
-  size_t B, Bs, Bsum, E, Es, Bb, G, n, u, J;
+  size_t B, Bs, Bsum, E, Es, Bb, G, n, u, J, pre;
   size_t partial, far, acc, inj, ctr, hist, prof;
   size_t total;
 };
@@ -90,6 +90,7 @@ struct DevPtrs {
   int* cnt[2];
   int* mcnt;      // movers written by each tile this step
   T *B, *Bs, *Bsum, *E, *Es, *Bb, *G, *n, *u, *J;
+  T* pre;          // FP64: 1/n and the two pressure terms per node, per step
   void* partial;   // float accumulators (FP32) or int64 fixed point (FP64)
   void* far;
   double* acc;
@@ -182,6 +183,7 @@ inline DevPtrs<T> Sim::ptrs(int) const {
   d.n = (T*)(base + L.n);
   d.u = (T*)(base + L.u);
   d.J = (T*)(base + L.J);
+  d.pre = (T*)(base + L.pre);
   d.partial = (void*)(base + L.partial);
   d.far = (void*)(base + L.far);
   d.acc = (double*)(base + L.acc);

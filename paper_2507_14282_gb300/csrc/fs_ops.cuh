@@ -107,13 +107,16 @@ struct OpsImpl {
     return cudaGetLastError();
   }
 
-  static void ohm(Sim* s, const T* Bc, T* Eo, T* Bbo, T* G) {
+  // pre: the per-step density terms (k_ohm_pre), or nullptr to form them here
+  static void ohm(Sim* s, const T* Bc, T* Eo, T* Bbo, T* G, const T* pre = nullptr) {
     DevPtrs<T> d = P(s);
     const long long nn = (long long)s->g.nxn * s->g.ny;
     if (s->g.dim == 1)
-      k_ohm<T, 1><<<grid_for(nn), kBlock, 0, s->stream>>>(Bc, d.n, d.u, Eo, Bbo, G, s->g, s->ph);
+      k_ohm<T, 1><<<grid_for(nn), kBlock, 0, s->stream>>>(Bc, d.n, d.u, pre, Eo, Bbo, G, s->g,
+                                                          s->ph);
     else
-      k_ohm<T, 2><<<grid_for(nn), kBlock, 0, s->stream>>>(Bc, d.n, d.u, Eo, Bbo, G, s->g, s->ph);
+      k_ohm<T, 2><<<grid_for(nn), kBlock, 0, s->stream>>>(Bc, d.n, d.u, pre, Eo, Bbo, G, s->g,
+                                                          s->ph);
   }
 
   static void faraday(Sim* s, int stage) {
@@ -133,17 +136,28 @@ struct OpsImpl {
 
   static cudaError_t fields(Sim* s) {
     DevPtrs<T> d = P(s);
+    // FP64 (bound by the FP64 pipe): 1/n and the pressure terms once per
+    // step; FP32 (bound by memory) forms them in every stage instead
+    const T* pre = nullptr;
+    if (sizeof(T) == 8) {
+      const long long nn = (long long)s->g.nxn * s->g.ny;
+      if (s->g.dim == 1)
+        k_ohm_pre<T, 1><<<grid_for(nn), kBlock, 0, s->stream>>>(d.n, d.pre, s->g, s->ph);
+      else
+        k_ohm_pre<T, 2><<<grid_for(nn), kBlock, 0, s->stream>>>(d.n, d.pre, s->g, s->ph);
+      pre = d.pre;
+    }
     for (int sub = 0; sub < s->p.n_sub; ++sub) {
-      ohm(s, d.B, d.Es, nullptr, nullptr);
+      ohm(s, d.B, d.Es, nullptr, nullptr, pre);
       faraday(s, 1);
-      ohm(s, d.Bs, d.Es, nullptr, nullptr);
+      ohm(s, d.Bs, d.Es, nullptr, nullptr, pre);
       faraday(s, 2);
-      ohm(s, d.Bs, d.Es, nullptr, nullptr);
+      ohm(s, d.Bs, d.Es, nullptr, nullptr, pre);
       faraday(s, 3);
-      ohm(s, d.Bs, d.Es, nullptr, nullptr);
+      ohm(s, d.Bs, d.Es, nullptr, nullptr, pre);
       faraday(s, 4);
     }
-    ohm(s, d.B, d.E, d.Bb, d.G);
+    ohm(s, d.B, d.E, d.Bb, d.G, pre);
     return cudaGetLastError();
   }
 
