@@ -139,6 +139,7 @@ typedef struct fs_diag_t {
 #define FS_HIST_XPX_CR 9  /* the same for the cosmic-ray species only */
 
 typedef struct fs_handle fs_handle;
+typedef struct fs_batch fs_batch;   /* ensemble of handles stepped together */
 
 /* Fills *out with defaults for a dim-dimensional faux-shock box.
    Returns FS_EINVAL if out is NULL or dim is not 1 or 2. */
@@ -245,6 +246,53 @@ int fs_profile_read(fs_handle* h, double* ms, long long* counts, int nphases);
 int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
                              const double* n, const double* u, double* B_out,
                              double* E_out, void* cuda_stream);
+
+/* ---- Batched ensembles: independent runs stepped together (Sec. 2 setup
+   per run; the batch is an execution schedule, not a different method).
+   A batch steps several handles -- faux-shock runs of any size, one
+   precision and dimension, created on one CUDA stream -- with one push
+   launch per step: each run gets a group of persistent CTAs about
+   proportional to its particles (a (run, tile) work list, each run's
+   pointers, geometry and physics read from a device table), and the rest of
+   every run's step (movers, injection, moments, field advance) runs in
+   parallel branches of one CUDA graph. Each run's results are those of
+   fs_step on that handle alone (bit-identical in FP64).
+
+   fs_batch_plan: host-only planner of the CTA groups. Runs of
+   n_particles[r] particles in ntiles[r] tiles share ncta_max CTAs:
+   ncta_out[r] is at least 1 and at most ntiles[r], the sum is at most
+   ncta_max, and ncta_out[r] / n_particles[r] is as even as integer
+   counts allow. FS_EINVAL for NULL arrays, nruns < 1, nruns > ncta_max, a
+   negative count or a tile count < 1. */
+int fs_batch_plan(int nruns, const long long* n_particles, const int* ntiles,
+                  int ncta_max, int* ncta_out);
+
+/* Device bytes of the run table of a batch of nruns runs of the given
+   precision (FS_FP32 / FS_FP64). The caller allocates them (256-byte
+   aligned) and keeps them until fs_batch_destroy. FS_EINVAL for nruns < 1
+   or an unknown precision. */
+int fs_batch_query(int nruns, int precision, size_t* table_bytes);
+
+/* Creates a batch over runs[0..nruns-1]. The handles are not owned: each
+   stays valid, and is not stepped on its own, until fs_batch_destroy.
+   Synchronises the stream and sizes the CTA groups from the current
+   particle counts. FS_EINVAL: NULL arguments, handles of mixed precision,
+   dimension or stream, a table smaller than fs_batch_query's size, or more
+   runs than the GPU holds persistent CTAs; a handle's sticky error is
+   returned as it is. */
+int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev,
+                  size_t table_bytes, fs_batch** out);
+
+/* Advances every run of the batch by nsteps, asynchronously on the runs'
+   stream. The first step is launched directly; later ones replay a
+   captured CUDA graph (two, one per particle-buffer parity). Device
+   conditions surface per run through fs_diag and the other synchronising
+   calls; a failed launch marks every run with FS_ECUDA. */
+int fs_batch_step(fs_batch* b, int nsteps);
+
+/* Releases the batch (host state, its streams, events and graphs). The
+   handles and the table buffer stay the caller's. */
+int fs_batch_destroy(fs_batch* b);
 
 /* Releases the handle (host memory only). The device buffer stays the
    caller's. */

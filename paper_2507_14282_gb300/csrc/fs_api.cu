@@ -275,6 +275,14 @@ int grid_blocks(long long n) {
 
 // Capture one step for each ping-pong parity on a private stream (the legacy
 // default stream cannot be captured); the graphs replay on the caller's stream.
+// Kernels one step launches: push, movers, injection (3), moments, [FP64:
+// Ohm density terms], 2 x 4 x n_sub field stages, final Ohm, step end.
+long long launches_per_step(const Sim* s) {
+  const bool inj = s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable);
+  return 1 + 1 + (inj ? 3 : 0) + 1 + (s->p.precision == FS_FP64 ? 1 : 0) +
+         8LL * s->p.n_sub + 1 + 1;
+}
+
 int build_graphs(Sim* s) {
   if (!s->cap_stream &&
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -495,11 +503,7 @@ int fs_step(fs_handle* h, int nsteps) {
   if (!h || nsteps < 0) return FS_EINVAL;
   Sim* s = &h->sim;
   if (s->sticky) return s->sticky;
-  const bool inj = s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable);
-  // push, movers, injection (3), moments, [FP64: Ohm density terms],
-  // 2 x 4 x n_sub field stages, final Ohm, step end
-  const long long per_step = 1 + 1 + (inj ? 3 : 0) + 1 + (s->p.precision == FS_FP64 ? 1 : 0) +
-                             8LL * s->p.n_sub + 1 + 1;
+  const long long per_step = launches_per_step(s);
   constexpr int kSet = FS_NPHASES + 1;
   if (!h->profiling && s->p.use_graph && s->steps_direct > 0 && !s->graphs_ready) {
     int r = build_graphs(s);
@@ -848,6 +852,284 @@ int fs_destroy(fs_handle* h) {
   delete h;
   return FS_OK;
 }
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+// (definitions keep the C linkage of their declarations in fs.h)
+
+namespace {
+constexpr int kBatchMaxCtas = 4096;  // CTA map entries the table holds
+constexpr int kBatchBranches = 8;    // parallel graph branches for the per-run work
+
+// the kernel indexes the table by record, so the stride is the record size
+size_t batch_rec_bytes(int precision) {
+  const Ops& o = (precision == FS_FP64) ? ops_f64() : ops_f32();
+  return o.batch_run_bytes();
+}
+size_t batch_map_offset(int nruns, int precision) {
+  return up(2 * (size_t)nruns * batch_rec_bytes(precision), kAlign);
+}
+}  // namespace
+
+struct fs_batch {
+  std::vector<fs_handle*> runs;
+  std::vector<int> cur0;  // each run's particle buffer when the batch was made
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private capture stream
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  char* table = nullptr;
+  size_t rec = 0;
+  int2* map = nullptr;
+  int ncta = 0;
+  size_t smem = 0;
+  int dim = 1;
+  const Ops* ops = nullptr;
+  int parity = 0;  // steps taken, mod 2
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graphs_ready = false;
+  int steps_direct = 0;
+};
+
+namespace {
+// One batched step on stream st for table half p: the push of every run in
+// one launch, then each run's remaining kernels on its branch.
+cudaError_t batch_enqueue(fs_batch* b, int p, cudaStream_t st) {
+  const int nr = (int)b->runs.size();
+  cudaError_t e = b->ops->push_batch(b->dim, b->table + (size_t)p * nr * b->rec, b->map,
+                                     b->ncta, b->smem, st);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
+  const int K = (int)b->branch.size();
+  for (int k = 0; k < K; ++k)
+    if ((e = cudaStreamWaitEvent(b->branch[k], b->fork, 0)) != cudaSuccess) return e;
+  for (int r = 0; r < nr; ++r) {
+    Sim* s = &b->runs[r]->sim;
+    cudaStream_t user = s->stream;
+    s->stream = b->branch[r % K];
+    e = s->ops->step_rest(s, (b->cur0[r] + p) & 1, nullptr);
+    s->stream = user;
+    if (e != cudaSuccess) return e;
+  }
+  for (int k = 0; k < K; ++k) {
+    if ((e = cudaEventRecord(b->join[k], b->branch[k])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, b->join[k], 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int batch_build_graphs(fs_batch* b) {
+  if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return FS_ECUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return FS_ECUDA;
+  int rc = FS_OK;
+  for (int par = 0; par < 2 && rc == FS_OK; ++par) {
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = FS_ECUDA;
+      break;
+    }
+    const cudaError_t e = batch_enqueue(b, par, b->cap);
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess || !gr) {
+      rc = FS_ECUDA;
+      if (gr) cudaGraphDestroy(gr);
+      break;
+    }
+    if (cudaGraphInstantiate(&b->graph[par], gr, 0) != cudaSuccess) rc = FS_ECUDA;
+    cudaGraphDestroy(gr);
+  }
+  cudaGetLastError();
+  if (rc == FS_OK) b->graphs_ready = true;
+  return rc;
+}
+
+void batch_fail(fs_batch* b, int code) {
+  for (fs_handle* h : b->runs)
+    if (!h->sim.sticky) h->sim.sticky = code;
+}
+}  // namespace
+
+int fs_batch_plan(int nruns, const long long* n_particles, const int* ntiles, int ncta_max,
+                  int* ncta_out) {
+  if (nruns < 1 || !n_particles || !ntiles || !ncta_out || nruns > ncta_max) return FS_EINVAL;
+  long double total = 0;
+  for (int r = 0; r < nruns; ++r) {
+    if (n_particles[r] < 0 || ntiles[r] < 1) return FS_EINVAL;
+    total += (long double)n_particles[r];
+  }
+  long long sum = 0;
+  for (int r = 0; r < nruns; ++r) {
+    long long a = 1;
+    if (total > 0) a = (long long)((long double)n_particles[r] * ncta_max / total);
+    a = std::max(1LL, std::min<long long>(a, ntiles[r]));
+    ncta_out[r] = (int)a;
+    sum += a;
+  }
+  // load of a run per CTA; equal loads are broken by the lower run index
+  auto load = [&](int r, int a) { return (long double)n_particles[r] / a; };
+  while (sum > ncta_max) {  // take from the lightest group that has more than one CTA
+    int best = -1;
+    for (int r = 0; r < nruns; ++r)
+      if (ncta_out[r] > 1 && (best < 0 || load(r, ncta_out[r] - 1) < load(best, ncta_out[best] - 1)))
+        best = r;
+    if (best < 0) return FS_EINVAL;
+    --ncta_out[best];
+    --sum;
+  }
+  while (sum < ncta_max) {  // give to the heaviest group that can still grow
+    int best = -1;
+    for (int r = 0; r < nruns; ++r)
+      if (ncta_out[r] < ntiles[r] && (best < 0 || load(r, ncta_out[r]) > load(best, ncta_out[best])))
+        best = r;
+    if (best < 0) break;
+    ++ncta_out[best];
+    ++sum;
+  }
+  return FS_OK;
+}
+
+int fs_batch_query(int nruns, int precision, size_t* table_bytes) {
+  if (nruns < 1 || !table_bytes || (precision != FS_FP32 && precision != FS_FP64))
+    return FS_EINVAL;
+  *table_bytes = batch_map_offset(nruns, precision) + sizeof(int2) * (size_t)kBatchMaxCtas;
+  return FS_OK;
+}
+
+int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t table_bytes,
+                  fs_batch** out) {
+  if (!runs || nruns < 1 || !table_dev || !out) return FS_EINVAL;
+  *out = nullptr;
+  for (int r = 0; r < nruns; ++r) {
+    if (!runs[r]) return FS_EINVAL;
+    if (runs[r]->sim.sticky) return runs[r]->sim.sticky;
+  }
+  const Sim& s0 = runs[0]->sim;
+  for (int r = 1; r < nruns; ++r) {
+    const Sim& s = runs[r]->sim;
+    if (s.p.precision != s0.p.precision || s.g.dim != s0.g.dim || s.stream != s0.stream)
+      return FS_EINVAL;
+  }
+  size_t need = 0;
+  fs_batch_query(nruns, s0.p.precision, &need);
+  if (table_bytes < need || ((uintptr_t)table_dev % kAlign) != 0) return FS_EINVAL;
+  const Ops* ops = s0.ops;
+  size_t smem = 0;
+  for (int r = 0; r < nruns; ++r)
+    smem = std::max(smem, ops->batch_smem(s0.g.dim, runs[r]->sim.g.TX, runs[r]->sim.g.TY));
+  if (smem > 227 * 1024 - 2048) return FS_EINVAL;
+  int dev = 0, nsm = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      ops->batch_setup(s0.g.dim, smem, &occ) != cudaSuccess || occ < 1)
+    return FS_ECUDA;
+  const int ncta_max = std::min(nsm * occ, kBatchMaxCtas);
+  std::vector<long long> np(nruns);
+  std::vector<int> nt(nruns), ncta(nruns);
+  for (int r = 0; r < nruns; ++r) {
+    const int rc = fs_num_particles(runs[r], &np[r]);  // synchronises
+    if (rc) return rc;
+    nt[r] = runs[r]->sim.g.ntiles;
+  }
+  int rc = fs_batch_plan(nruns, np.data(), nt.data(), ncta_max, ncta.data());
+  if (rc) return rc;
+  fs_batch* b = new fs_batch();
+  b->runs.assign(runs, runs + nruns);
+  b->stream = s0.stream;
+  b->ops = ops;
+  b->dim = s0.g.dim;
+  b->smem = smem;
+  b->rec = batch_rec_bytes(s0.p.precision);
+  b->table = (char*)table_dev;
+  b->map = (int2*)(b->table + batch_map_offset(nruns, s0.p.precision));
+  std::vector<char> host(need, 0);
+  std::vector<int2> map;
+  for (int r = 0; r < nruns; ++r) {
+    const Sim& s = runs[r]->sim;
+    b->cur0.push_back(s.cur);
+    for (int p = 0; p < 2; ++p)
+      ops->fill_batch_run(&s, (s.cur + p) & 1, ncta[r],
+                          host.data() + ((size_t)p * nruns + r) * b->rec);
+    for (int k = 0; k < ncta[r]; ++k) map.push_back(make_int2(r, k));
+  }
+  b->ncta = (int)map.size();
+  memcpy(host.data() + batch_map_offset(nruns, s0.p.precision), map.data(),
+         sizeof(int2) * map.size());
+  bool ok = cudaMemcpyAsync(table_dev, host.data(), need, cudaMemcpyHostToDevice, b->stream) ==
+                cudaSuccess &&
+            cudaStreamSynchronize(b->stream) == cudaSuccess;
+  const int K = std::min(nruns, kBatchBranches);
+  ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < K; ++k) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (st) b->branch.push_back(st);
+    if (ev) b->join.push_back(ev);
+  }
+  if (!ok) {
+    fs_batch_destroy(b);
+    return FS_ECUDA;
+  }
+  *out = b;
+  return FS_OK;
+}
+
+int fs_batch_step(fs_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return FS_EINVAL;
+  for (fs_handle* h : b->runs)
+    if (h->sim.sticky) return h->sim.sticky;
+  bool use_graph = true;
+  for (fs_handle* h : b->runs) use_graph = use_graph && h->sim.p.use_graph;
+  for (int k = 0; k < nsteps; ++k) {
+    if (use_graph && b->steps_direct > 0 && !b->graphs_ready) {
+      const int rc = batch_build_graphs(b);
+      if (rc) {
+        batch_fail(b, rc);
+        return rc;
+      }
+    }
+    cudaError_t e;
+    if (b->graphs_ready) {
+      e = cudaGraphLaunch(b->graph[b->parity], b->stream);
+    } else {
+      e = batch_enqueue(b, b->parity, b->stream);
+      b->steps_direct++;
+    }
+    if (e != cudaSuccess) {
+      batch_fail(b, FS_ECUDA);
+      return FS_ECUDA;
+    }
+    b->parity ^= 1;
+    for (fs_handle* h : b->runs) {
+      Sim* s = &h->sim;
+      s->cur = 1 - s->cur;
+      s->step++;
+      s->launches += launches_per_step(s);  // the shared push counted in each run
+    }
+  }
+  return FS_OK;
+}
+
+int fs_batch_destroy(fs_batch* b) {
+  if (!b) return FS_EINVAL;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int p = 0; p < 2; ++p)
+    if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+  for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaGetLastError();
+  delete b;
+  return FS_OK;
+}
+
+extern "C" {
 
 const char* fs_strerror(int status) {
   switch (status) {

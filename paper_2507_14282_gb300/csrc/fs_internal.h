@@ -100,6 +100,21 @@ struct DevPtrs {
   double* prof;
 };
 
+// One run of a batched ensemble as the batched push reads it (device table,
+// records sizeof(BatchRun) apart: 16-byte aligned, so host and device agree
+// on the stride).
+template <typename T>
+struct alignas(16) BatchRun {
+  DevPtrs<T> d;
+  Geo g;
+  Phys ph;
+  int in, out;  // particle buffers read and written this step
+  int ncta;     // CTAs of the run's group
+  int pad;
+};
+static_assert(sizeof(BatchRun<float>) % 16 == 0 && sizeof(BatchRun<double>) % 16 == 0,
+              "batch records must tile the table at their own size");
+
 struct Sim;
 
 // Per-precision kernel launchers. Each returns cudaSuccess or the launch
@@ -111,6 +126,14 @@ struct Ops {
   cudaError_t (*ohm_final)(Sim*);
   // ev: NULL, or FS_NPHASES + 1 events recorded at the phase boundaries
   cudaError_t (*step)(Sim*, int in_buf, long long step, cudaEvent_t* ev);
+  cudaError_t (*step_rest)(Sim*, int in_buf, cudaEvent_t* ev);  // all but the push
+  // batched ensembles (k_push_batch)
+  size_t (*batch_run_bytes)();
+  void (*fill_batch_run)(const Sim*, int in_buf, int ncta, void* dst);
+  size_t (*batch_smem)(int dim, int tx, int ty);
+  cudaError_t (*batch_setup)(int dim, size_t smem, int* occ);
+  cudaError_t (*push_batch)(int dim, const void* runs, const int2* cta_map, int ncta,
+                            size_t smem, cudaStream_t st);
   cudaError_t (*fields)(Sim*);
   cudaError_t (*insert_staged)(Sim*, int buf, int n, bool from_movers);
   cudaError_t (*diag)(Sim*, int buf);

@@ -3,6 +3,7 @@
 // fs_f64.cu (the latter compiled with -fmad=false).
 #pragma once
 #include <algorithm>
+#include <cstring>
 
 #include "fs_push.cuh"
 
@@ -161,17 +162,14 @@ struct OpsImpl {
     return cudaGetLastError();
   }
 
-  static cudaError_t step(Sim* s, int in, long long step, cudaEvent_t* ev) {
+  // Everything of a step after the push (movers, injection, moments, field
+  // advance, step counter); ev as in step().
+  static cudaError_t step_rest(Sim* s, int in, cudaEvent_t* ev) {
     DevPtrs<T> d = P(s);
     const int out = 1 - in;
     auto mark = [&](int k) {
       if (ev) cudaEventRecord(ev[k], s->stream);
     };
-    mark(0);
-    cudaError_t e;
-    e = (s->g.dim == 1) ? push_dispatch<T, 1>(s, in, step) : push_dispatch<T, 2>(s, in, step);
-    if (e != cudaSuccess) return e;
-    mark(1);
     const int mg = std::min((s->g.ntiles + 7) / 8, 152 * 16);
     if (s->g.dim == 1)
       k_movers<T, 1><<<mg, kBlock, 0, s->stream>>>(d, s->g, out);
@@ -193,13 +191,65 @@ struct OpsImpl {
       k_inject_commit<<<1, 32, 0, s->stream>>>(d.ctr, rowoff, s->g.ny);
     }
     mark(3);
-    e = moments(s);
+    cudaError_t e = moments(s);
     if (e != cudaSuccess) return e;
     mark(4);
     e = fields(s);
     k_step_end<<<1, 32, 0, s->stream>>>(d.ctr);
     mark(5);
     return e;
+  }
+
+  static cudaError_t step(Sim* s, int in, long long step, cudaEvent_t* ev) {
+    if (ev) cudaEventRecord(ev[0], s->stream);
+    const cudaError_t e =
+        (s->g.dim == 1) ? push_dispatch<T, 1>(s, in, step) : push_dispatch<T, 2>(s, in, step);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s->stream);
+    return step_rest(s, in, ev);
+  }
+
+  // ---- batched ensembles: one push launch over every run's CTA group
+  static size_t batch_run_bytes() { return sizeof(BatchRun<T>); }
+  static void fill_batch_run(const Sim* s, int in, int ncta, void* dst) {
+    BatchRun<T> r;
+    r.d = const_cast<Sim*>(s)->ptrs<T>();
+    r.g = s->g;
+    r.ph = s->ph;
+    r.in = in;
+    r.out = 1 - in;
+    r.ncta = ncta;
+    r.pad = 0;
+    memcpy(dst, &r, sizeof r);
+  }
+  static size_t batch_smem(int dim, int tx, int ty) {
+    using S = PushShape<T>;
+    return dim == 1 ? PushLayout<T, 1>(tx, ty, S::kChunkLarge, S::kStagesLarge).bytes
+                    : PushLayout<T, 2>(tx, ty, S::kChunkLarge, S::kStagesLarge).bytes;
+  }
+  template <int DIM>
+  static cudaError_t batch_kernel_setup(size_t smem, int* occ) {
+    using S = PushShape<T>;
+    auto kern = k_push_batch<T, DIM, S::kChunkLarge, S::kStagesLarge>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess && occ)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, kBlock, smem);
+    return e;
+  }
+  // sets the shared-memory attribute; occ (optional): CTAs per SM
+  static cudaError_t batch_setup(int dim, size_t smem, int* occ) {
+    return dim == 1 ? batch_kernel_setup<1>(smem, occ) : batch_kernel_setup<2>(smem, occ);
+  }
+  static cudaError_t push_batch(int dim, const void* runs, const int2* cta_map, int ncta,
+                                size_t smem, cudaStream_t st) {
+    using S = PushShape<T>;
+    const BatchRun<T>* r = (const BatchRun<T>*)runs;
+    if (dim == 1)
+      k_push_batch<T, 1, S::kChunkLarge, S::kStagesLarge><<<ncta, kBlock, smem, st>>>(r, cta_map);
+    else
+      k_push_batch<T, 2, S::kChunkLarge, S::kStagesLarge><<<ncta, kBlock, smem, st>>>(r, cta_map);
+    return cudaGetLastError();
   }
 
   static cudaError_t insert_staged(Sim* s, int buf, int n, bool from_movers) {
@@ -289,6 +339,12 @@ struct OpsImpl {
     o.profiles = profiles;
     o.export_grid = export_grid;
     o.import_B = import_B;
+    o.step_rest = step_rest;
+    o.batch_run_bytes = batch_run_bytes;
+    o.fill_batch_run = fill_batch_run;
+    o.batch_smem = batch_smem;
+    o.batch_setup = batch_setup;
+    o.push_batch = push_batch;
     o.export_particles = export_particles;
     return o;
   }

@@ -184,7 +184,7 @@ __device__ __forceinline__ void warp_scan_excl(const int* in, int* out, int n,
 }
 
 // The chunk after c = {tile, first particle, count, tile count} for a CTA
-// that owns tiles blockIdx.x, blockIdx.x + G, ...; tile >= ntiles: done.
+// that owns tiles cta, cta + G, ...; tile >= ntiles: done.
 // pf[0] holds the count of tile c.x + G, copied asynchronously into shared
 // memory one tile transition earlier; the count of the tile after it is
 // requested now.
@@ -534,13 +534,14 @@ __device__ __forceinline__ void drain_stages(unsigned char* sm, const PushLayout
     if (desc[2 * o].x < ntiles && desc[2 * o].z > 0) mbar_wait(&bar[o], (parity >> o) & 1u);
 }
 
+// The push of one run by one CTA of a group of G CTAs (rank cta in the
+// group): tiles cta, cta + G, ... of the run; sm is the dynamic shared memory.
 template <typename T, int DIM, int CH, int NS>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPtrs<T> d, StepArgs a) {
+__device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, const Phys& ph,
+                                         int in, int out, int cta, int G,
+                                         unsigned char* sm) {
   using A = typename Num<T>::acc;
   constexpr int PPT = (CH + kBlock - 1) / kBlock;
-  extern __shared__ __align__(128) unsigned char sm[];
-  const Geo g = a.g;
-  const Phys ph = a.ph;
   const PushLayout<T, DIM> L(g.TX, g.TY, CH, NS);
   const int TX = L.TX, TY = L.TY, EX = L.EX, EY = L.EY, NE = L.NE, NINT = L.NINT,
             NK = L.NK, NA = L.NA, AX = L.AX;
@@ -554,10 +555,9 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
   PushTally* tl = (PushTally*)(sm + L.tally);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int* wk = (int*)(sm + L.wk) + warp * (NK + 1);
-  const int G = gridDim.x;
-  const int* cnt_in = d.cnt[a.in];
-  const Parts<T> PI = d.P[a.in];
-  const Parts<T> PO = d.P[a.out];
+  const int* cnt_in = d.cnt[in];
+  const Parts<T> PI = d.P[in];
+  const Parts<T> PO = d.P[out];
   const T dtdx = (T)ph.dtdx, dtdy = (T)ph.dtdy, hdt = (T)ph.hdt;
   const T wth = (T)(ph.w_th * (double)deposit_weight_scale<T>());
   const T wcr = (T)(ph.w_cr * (double)deposit_weight_scale<T>());
@@ -592,13 +592,13 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
   if (tid == 0) {
     // prologue: the CTA's first NS chunks, one per stage
     int4 c;
-    if ((int)blockIdx.x < g.ntiles) {
-      const int n = min(cnt_in[blockIdx.x], g.tile_cap);
-      c = make_int4(blockIdx.x, 0, min(CH, n), n);
+    if (cta < g.ntiles) {
+      const int n = min(cnt_in[cta], g.tile_cap);
+      c = make_int4(cta, 0, min(CH, n), n);
     } else {
       c = make_int4(g.ntiles, 0, 0, 0);
     }
-    if ((int)blockIdx.x + G < g.ntiles) cp_async4(pf, cnt_in + blockIdx.x + G);
+    if (cta + G < g.ntiles) cp_async4(pf, cnt_in + cta + G);
     for (int b = 0; b < NS; ++b) {
       issue_chunk<T, DIM>(sm, L, b, c, d, PI, g);
       if (b + 1 < NS) c = next_chunk(c, G, g.ntiles, CH, cnt_in, g.tile_cap, pf);
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
     if (c.y + m >= c.w) {
       // last chunk of tile t: output and mover counts now, partial next chunk
       if (tid == 0) {
-        d.cnt[a.out][t] = outRun;
+        d.cnt[out][t] = outRun;
         d.mcnt[t] = min(movRun, g.mover_per_tile);
       }
       pend = t;
@@ -826,6 +826,31 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPt
     if (tl->fse != 0.0) atomicAdd(&d.ctr->fs_energy, tl->fse);
     if (tl->rem != 0.0) atomicAdd(&d.ctr->removed_energy, tl->rem);
   }
+}
+
+
+template <typename T, int DIM, int CH, int NS>
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPtrs<T> d, StepArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  push_run<T, DIM, CH, NS>(d, a.g, a.ph, a.in, a.out, blockIdx.x, gridDim.x, sm);
+}
+
+// Batched push of an ensemble of independent runs in one persistent launch:
+// CTA b works on run cta_map[b].x as rank cta_map[b].y of that run's group of
+// runs[run].ncta CTAs; the run's pointers, geometry and physics come from the
+// device table, copied once into shared memory.
+template <typename T, int DIM, int CH, int NS>
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
+    k_push_batch(const BatchRun<T>* __restrict__ runs, const int2* __restrict__ cta_map) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(16) BatchRun<T> R;
+  const int2 cm = cta_map[blockIdx.x];
+  static_assert(sizeof(BatchRun<T>) % 4 == 0, "run record copied as words");
+  const int* src = reinterpret_cast<const int*>(runs + cm.x);
+  int* dst = reinterpret_cast<int*>(&R);
+  for (int k = threadIdx.x; k < (int)(sizeof(BatchRun<T>) / 4); k += kBlock) dst[k] = src[k];
+  __syncthreads();
+  push_run<T, DIM, CH, NS>(R.d, R.g, R.ph, R.in, R.out, cm.y, R.ncta, sm);
 }
 
 }  // namespace fsx

@@ -105,6 +105,11 @@ def lib():
         L.fs_profile_read.argtypes = [V, V, V, C.c_int]
         L.fs_strerror.argtypes = [C.c_int]
         L.fs_strerror.restype = C.c_char_p
+        L.fs_batch_plan.argtypes = [C.c_int, V, V, C.c_int, V]
+        L.fs_batch_query.argtypes = [C.c_int, C.c_int, P(C.c_size_t)]
+        L.fs_batch_init.argtypes = [V, C.c_int, V, C.c_size_t, P(V)]
+        L.fs_batch_step.argtypes = [V, C.c_int]
+        L.fs_batch_destroy.argtypes = [V]
         _lib = L
     return _lib
 
@@ -267,3 +272,54 @@ class FauxShock:
     def load_fields(self, B: np.ndarray):
         b = np.ascontiguousarray(B, dtype=np.float64).reshape(self.ny, self.nx, 3)
         _check(lib().fs_load_fields(self._h, _ptr(b)), "fs_load_fields")
+
+
+def batch_plan(n_particles, ntiles, ncta_max: int) -> list:
+    """CTA groups of a batch (fs_batch_plan; host-only, no GPU needed)."""
+    n = np.ascontiguousarray(n_particles, dtype=np.int64)
+    t = np.ascontiguousarray(ntiles, dtype=np.int32)
+    out = np.zeros(len(n), dtype=np.int32)
+    _check(lib().fs_batch_plan(len(n), _ptr(n), _ptr(t), int(ncta_max), _ptr(out)),
+           "fs_batch_plan")
+    return out.tolist()
+
+
+class FsBatch:
+    """Independent FauxShock runs stepped together (fs_batch_*): one push
+    launch over every run's CTA group per step, the rest of each run's step in
+    parallel branches of one CUDA graph. The runs must share precision,
+    dimension and stream; they are not stepped on their own while the batch
+    lives."""
+
+    def __init__(self, sims):
+        import torch
+        if not sims:
+            raise ValueError("a batch needs at least one run")
+        self.sims = list(sims)
+        prec = self.sims[0].params["precision"]
+        nb = C.c_size_t()
+        _check(lib().fs_batch_query(len(self.sims), prec, C.byref(nb)), "fs_batch_query")
+        align = 256
+        dev = self.sims[0].device
+        self._mem = torch.empty(int(nb.value) + align, dtype=torch.uint8, device=dev)
+        base = self._mem.data_ptr()
+        base += (-base) % align
+        hs = (C.c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
+        h = C.c_void_p()
+        _check(lib().fs_batch_init(hs, len(self.sims), C.c_void_p(base), nb, C.byref(h)),
+               "fs_batch_init")
+        self._h = h
+
+    def step(self, n: int = 1):
+        _check(lib().fs_batch_step(self._h, n), "fs_batch_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -52,3 +52,23 @@ def random_particles(rng, n, nx, ny, vscale=1.0, drift=0.0):
     v = rng.normal(0, vscale, (3, n))
     v[0] += drift
     return ci, cj, fx, fy, v[0], v[1], v[2]
+
+
+# Batched ensemble (config 4): 64 independent 1D FP32 runs; run r draws its
+# parameters from Philox(key = 100 + r): N_x log-uniform in 512..8192
+# (rounded to a multiple of 32 so that tiles divide the box), ppc from
+# {32, 64, 128, 256}, M_A uniform in 5..100, theta_Bn uniform in 0..60 deg,
+# beta_i = beta_e from {0.5, 1, 2}; dt = min(0.005, 0.1 dx / M_A).
+def config4_runs(n_runs: int = 64, first_seed: int = 100, precision: int = 1):
+    runs = []
+    for r in range(n_runs):
+        g = np.random.Generator(np.random.Philox(key=first_seed + r))
+        nx = int(round(float(np.exp(g.uniform(np.log(512.0), np.log(8192.0)))) / 32.0)) * 32
+        ppc = int(g.choice([32, 64, 128, 256]))
+        mach = float(g.uniform(5.0, 100.0))
+        theta = float(g.uniform(0.0, 60.0))
+        beta = float(g.choice([0.5, 1.0, 2.0]))
+        runs.append(dict(dim=1, nx=nx, ny=1, dx=0.5, dy=0.5, dt=min(0.005, 0.1 * 0.5 / mach),
+                         mach_a=mach, theta_bn_deg=theta, beta_i=beta, beta_e=beta, ppc=ppc,
+                         seed=first_seed + r, precision=precision))
+    return runs
