@@ -5,7 +5,9 @@ FP64 (4096 x 256 cells, dx = 0.5 d_i, 16 ppc = 16.8 M particles, M_A = 20,
 theta_Bn = 0, beta_i = beta_e = 1, dt = 0.0025, seed 2). The same run also
 times the FP32 precision form (8192 x 512 cells, 64 ppc = 268 M particles,
 M_A = 30, theta_Bn = 30 deg, dt = 0.002, seed 3) and reports it under "fp32"
-(the metric compares FP32 with FP64).
+(the metric compares FP32 with FP64), and the batched ensemble of 64 uneven
+1D FP32 runs stepped together (reported under "ensemble", with the same runs
+stepped one after another beside it).
 
 A step is one full hybrid step: gather, Boris push, faux-shock pass/return,
 cell binning, moment deposition, moment finish, Ohm's law + Faraday RK4
@@ -43,6 +45,11 @@ WORKLOAD_NAME = ("2D faux-shock hybrid PIC, 4096x256 cells, dx=0.5 d_i, 16 ppc "
                  "FP64 plain method, seed 2")
 FP32_NAME = ("2D faux-shock hybrid PIC precision form, 8192x512 cells, 64 ppc "
              "(268M protons), M_A=30, theta_Bn=30 deg, beta=1, dt=0.002, FP32, seed 3")
+
+ENSEMBLE_NAME = ("batched ensemble: 64 independent 1D faux-shock runs in FP32, N_x "
+                 "log-uniform in 512..8192, ppc in {32,64,128,256}, M_A 5..100, theta_Bn "
+                 "0..60 deg, beta in {0.5,1,2}, dt = min(0.005, 0.1 dx/M_A), seeds 100..163 "
+                 "(Philox), autotuned tiles; one graph-captured batched step")
 
 # Algorithmic bytes of the particle push per particle-step: the particle state
 # (int32 cell, offsets, velocity, uint32 id) read once and written once.
@@ -279,6 +286,10 @@ def ours(args):
         del res32["sim"]
         torch.cuda.empty_cache()
 
+    ens = None
+    if not args.skip_ensemble:
+        ens = ensemble(fs, torch, args, hbm, peak_src)
+
     e2e = end_to_end(fs, torch, device, args, dist, world)
 
     cpu = None
@@ -298,6 +309,7 @@ def ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "fp32": fp32,
+            "ensemble": ens,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": gpu_launches,
@@ -306,6 +318,62 @@ def ours(args):
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def ensemble(fs, torch, args, hbm, peak_src):
+    """The batched ensemble: 64 uneven 1D FP32 runs stepped together (one
+    push launch over every run's CTA group per step, graph-captured), timed
+    with CUDA events, next to the same runs stepped one after another."""
+    from paper_2507_14282_gb300 import tune
+    from tests.workloads import config4_runs
+    tuner = tune.Autotuner()
+    t0 = time.perf_counter()
+    runs = [tuner.tile(r) for r in config4_runs(64)]
+    tune_s = time.perf_counter() - t0
+    sims = [fs.FauxShock(**r) for r in runs]
+    st = sims[0].stream
+    K = args.ens_steps
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for s in sims:
+        s.step(args.warmup)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for s in sims:
+        s.step(K)
+    e1.record(st)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / K
+    n0 = sum(s.num_particles() for s in sims)
+    b = fs.FsBatch(sims)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    e0.record(st)
+    b.step(K)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    n1 = sum(s.num_particles() for s in sims)
+    status = [s.diag()["status"] for s in sims]
+    b.close()
+    n = 0.5 * (n0 + n1)
+    pb = particle_bytes(4, 1)
+    grid_b = sum(GRID_WORDS_PER_CELL * 4 * (r["nx"] + 1) for r in runs)
+    step_bytes = n * pb + grid_b
+    for s in sims:
+        s.close()
+    torch.cuda.empty_cache()
+    return {"workload": ENSEMBLE_NAME, "value": n / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "steps": K, "n_runs": len(runs), "n_particles": n,
+            "sequential_value": n / (seq_ms * 1e-3), "sequential_ms_per_step": seq_ms,
+            "speedup_vs_sequential": seq_ms / ms,
+            "bytes_per_particle_step": step_bytes / n,
+            "step_roofline": {"bound": "hbm", "achieved": step_bytes / (ms * 1e-3) / 1e9,
+                              "peak": hbm, "unit": "GB/s",
+                              "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm,
+                              "peak_source": peak_src},
+            "tiles": {k: v for k, v in sorted(tuner.cache.items())},
+            "tune_s": tune_s, "status_ok": all(x == 0 for x in status)}
 
 
 def end_to_end(fs, torch, device, args, dist, world):
@@ -444,6 +512,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=300)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ens-steps", type=int, default=50)
+    ap.add_argument("--skip-ensemble", action="store_true")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args)

@@ -861,7 +861,10 @@ int fs_destroy(fs_handle* h) {
 
 namespace {
 constexpr int kBatchMaxCtas = 4096;  // CTA map entries the table holds
-constexpr int kBatchBranches = 8;    // parallel graph branches for the per-run work
+#ifndef FS_BATCH_BRANCHES
+#define FS_BATCH_BRANCHES 32
+#endif
+constexpr int kBatchBranches = FS_BATCH_BRANCHES;  // parallel graph branches, per-run work
 
 // the kernel indexes the table by record, so the stride is the record size
 size_t batch_rec_bytes(int precision) {

@@ -2,7 +2,8 @@
 sweeps on the GPU and caches the choice per (dimension, ppc, precision).
 
 A tile's particle count sets the push's chunk fill, the halo overhead of the
-deposit and the number of persistent-CTA work items. The best count depends
+deposit and the number of persistent-CTA work items; the tuner times the two
+phases it affects (push and movers). The best count depends
 on ppc and precision more than on the box length, so the tuner times a few
 candidate counts on a representative box of each class and applies the
 winner to any box of that class (tile width = the divisor of nx whose mean
@@ -16,6 +17,7 @@ import os
 from . import fs
 
 TARGETS = (128, 256, 512, 1024)  # mean particles per tile tried
+MAX_NX = 65535                    # longest box the library accepts
 
 
 def divisors(n: int, lo: int = 2, hi: int = 256) -> list:
@@ -31,10 +33,10 @@ def tile_for(nx: int, ppc: int, target: int) -> int:
 
 
 class Autotuner:
-    def __init__(self, cache_path: str | None = None, probe_nx: int = 2048,
+    def __init__(self, cache_path: str | None = None, probe_particles: int = 1 << 22,
                  warm: int = 3, steps: int = 8):
         self.cache_path = cache_path
-        self.probe_nx = probe_nx
+        self.probe_particles = probe_particles
         self.warm, self.steps = warm, steps
         self.cache = {}
         if cache_path and os.path.exists(cache_path):
@@ -47,18 +49,17 @@ class Autotuner:
         return f"dim{dim}-ppc{ppc}-{'fp64' if precision == fs.FS_FP64 else 'fp32'}"
 
     def _time(self, params: dict) -> float:
-        """ms per step of a short run (CUDA events on the run's stream)."""
-        import torch
+        """ms per step of the phases the tile shape sets (push and movers),
+        from the library's own CUDA-event phase timing."""
         sim = fs.FauxShock(**params)
         try:
             sim.step(self.warm)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(sim.stream)
+            sim.profile(True)
+            sim.profile_read()
             sim.step(self.steps)
-            e1.record(sim.stream)
-            e1.synchronize()
-            return e0.elapsed_time(e1) / self.steps
+            ph = sim.profile_read()
+            sim.profile(False)
+            return sum(ph[k][0] / max(ph[k][1], 1) for k in ("push", "movers"))
         finally:
             sim.close()
 
@@ -69,7 +70,10 @@ class Autotuner:
         if k in self.cache:
             return self.cache[k]
         probe = dict(base)
-        probe["nx"] = self.probe_nx
+        # a box of about probe_particles particles (large enough that the
+        # kernels, not launch latency, set the time), nx a multiple of 1024
+        probe["nx"] = min(max(1024, (self.probe_particles // base["ppc"]) // 1024 * 1024),
+                          MAX_NX // 1024 * 1024)
         best, best_ms = None, None
         for target in TARGETS:
             tx = tile_for(probe["nx"], probe["ppc"], target)

@@ -107,7 +107,7 @@ def test_fp32_batch_matches_runs_alone(fs):
 def test_config4_ensemble_steps_with_autotuned_tiles(fs):
     from paper_2507_14282_gb300 import tune
     runs = W.config4_runs(8)
-    tuner = tune.Autotuner(probe_nx=1024, warm=2, steps=3)
+    tuner = tune.Autotuner(probe_particles=1 << 16, warm=2, steps=3)
     tuned = [tuner.tile(r) for r in runs]
     assert all(t["nx"] % t["tile_x"] == 0 for t in tuned)
     assert len(tuner.cache) == len({r["ppc"] for r in runs})
