@@ -137,6 +137,13 @@ typedef struct fs_diag_t {
 #define FS_PROFILE_DB2 7  /* y-averaged |B - B0|^2 / B0^2: [nx] */
 #define FS_HIST_XPX 8     /* x - p_x histogram, all species: [hist_nx][hist_np] int64 */
 #define FS_HIST_XPX_CR 9  /* the same for the cosmic-ray species only */
+#define FS_PROFILE_B 10   /* y-averaged B (lineouts of Bx, By, Bz, Sec. 3.1): [nx][3] */
+/* Perpendicular magnetic power spectrum averaged over y (Sec. 3.1, Fig. 3
+   caption): P[k] = (1/ny) sum_y (|F[By](k, y)|^2 + |F[Bz](k, y)|^2) with
+   F[f](k, y) = (1/nx) sum_x f(x, y) exp(-2 pi i k x / nx), for
+   k = 0 .. nx/2 (wavenumber 2 pi k / (nx dx)): [nx/2 + 1] doubles. Computed
+   in FP64 in every precision. */
+#define FS_SPECTRUM_BPERP 11
 
 typedef struct fs_handle fs_handle;
 typedef struct fs_batch fs_batch;   /* ensemble of handles stepped together */

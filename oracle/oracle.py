@@ -163,6 +163,26 @@ def sincos2pi(u: float):
     return c.value, s.value
 
 
+def profile_B(B: np.ndarray) -> np.ndarray:
+    """Transversely averaged lineouts of Bx, By, Bz (Sec. 3.1, Fig. 2(b)):
+    B given as [ny][nx][3] at cell centres; returns [nx][3]."""
+    return np.asarray(B, dtype=np.float64).mean(axis=0)
+
+
+def bperp_spectrum(B: np.ndarray) -> np.ndarray:
+    """Perpendicular magnetic power spectrum averaged over the transverse
+    direction (Sec. 3.1, Fig. 3 caption): |F[By](k, y)|^2 + |F[Bz](k, y)|^2
+    averaged over y, F the discrete Fourier transform along x divided by nx,
+    for k = 0 .. nx/2 (wavenumber 2 pi k / (nx dx)). B as [ny][nx][3]. The
+    transforms are numpy's FFT of each component separately."""
+    B = np.asarray(B, dtype=np.float64)
+    nx = B.shape[1]
+    Fy = np.fft.fft(B[:, :, 1], axis=1) / nx
+    Fz = np.fft.fft(B[:, :, 2], axis=1) / nx
+    P = (np.abs(Fy) ** 2 + np.abs(Fz) ** 2).mean(axis=0)
+    return P[: nx // 2 + 1]
+
+
 def boris(v, E, B, dt) -> np.ndarray:
     vv = np.array(v, dtype=np.float64)
     e = np.ascontiguousarray(E, dtype=np.float64)

@@ -25,8 +25,17 @@ size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool divides(int a, int b) { return a > 0 && b % a == 0; }
 
-// Tile shape: cells per tile close to 1024 / ppc particles... chosen so that
-// the mean tile holds about half a shared-memory chunk of particles.
+// The push's shared memory for a tx x ty tile fits one CTA.
+bool push_tile_fits(const fs_params* p, int tx, int ty) {
+  const int chunk = (p->precision == FS_FP32 && (long long)tx * ty * p->ppc > 256) ? 640 : 512;
+  const size_t smem = (p->precision == FS_FP64) ? push_smem_bytes_f64(p->dim, tx, ty, chunk)
+                                                : push_smem_bytes_f32(p->dim, tx, ty, chunk);
+  return smem <= 227 * 1024 - 1024;
+}
+
+// Tile shape: the most cells (then the squarest tile) whose mean particle
+// count stays within 512 and whose push fits shared memory; tile sides
+// divide the box.
 void choose_tile(const fs_params* p, int* tx, int* ty) {
   if (p->dim == 1) {
     if (p->tile_x > 0) { *tx = p->tile_x; *ty = 1; return; }
@@ -48,6 +57,7 @@ void choose_tile(const fs_params* p, int* tx, int* ty) {
       if (!divides(cx, p->nx)) continue;
       const long long cells = (long long)cx * cy;
       if (cells * p->ppc > 512) continue;
+      if (!push_tile_fits(p, cx, cy)) continue;  // node block + accumulators in smem
       // prefer more cells, then squarer tiles
       const long long score = cells * 1000 - (long long)abs(cx - 2 * cy);
       if (score > bestc) { bestc = score; bx = cx; by = cy; }
@@ -221,7 +231,8 @@ int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
   L->inj = take(4 * (2 * (size_t)p->ny + 2));
   L->ctr = take(sizeof(Counters));
   L->hist = take(8 * (size_t)p->hist_nx * p->hist_np);
-  L->prof = take(8 * ((size_t)g->nxn + p->nx));
+  // profiles: n [nxn], dB^2 [nx], B [nx][3], B-perp spectrum [nx/2 + 1]
+  L->prof = take(8 * ((size_t)g->nxn + p->nx + 3 * (size_t)p->nx + (size_t)p->nx / 2 + 1));
   L->total = up(o, kAlign);
   return FS_OK;
 }
@@ -664,6 +675,19 @@ int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes, int dst_on_d
     if (dst_bytes < 8 * cnt) return FS_EINVAL;
     if (s->ops->profiles(s) != cudaSuccess) return s->sticky = FS_ECUDA;
     const size_t off = s->L.prof + (what == FS_PROFILE_N ? 0 : 8 * (size_t)g.nxn);
+    if (cudaMemcpyAsync(dst, s->base + off, 8 * cnt,
+                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess)
+      return s->sticky = FS_ECUDA;
+    return sync_and_check(s);
+  }
+  if (what == FS_PROFILE_B || what == FS_SPECTRUM_BPERP) {
+    const bool spec = (what == FS_SPECTRUM_BPERP);
+    const size_t cnt = spec ? (size_t)g.nx / 2 + 1 : 3 * (size_t)g.nx;
+    if (dst_bytes < 8 * cnt) return FS_EINVAL;
+    const cudaError_t e = spec ? s->ops->spectrum_bperp(s) : s->ops->profile_B(s);
+    if (e != cudaSuccess) return s->sticky = FS_ECUDA;
+    const size_t off = s->L.prof + 8 * ((size_t)g.nxn + g.nx + (spec ? 3 * (size_t)g.nx : 0));
     if (cudaMemcpyAsync(dst, s->base + off, 8 * cnt,
                         dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         s->stream) != cudaSuccess)

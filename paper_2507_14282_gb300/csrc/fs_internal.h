@@ -139,6 +139,8 @@ struct Ops {
   cudaError_t (*diag)(Sim*, int buf);
   cudaError_t (*hist)(Sim*, int buf, int species);
   cudaError_t (*profiles)(Sim*);
+  cudaError_t (*profile_B)(Sim*);       // y-averaged B into the profile region
+  cudaError_t (*spectrum_bperp)(Sim*);  // B-perp power spectrum into the profile region
   cudaError_t (*export_grid)(Sim*, int what, double* dst_dev);
   cudaError_t (*import_B)(Sim*, const double* src_dev);
   cudaError_t (*export_particles)(Sim*, int buf, double* dst_dev, int* cell_dev,

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "fs_push.cuh"
+#include "fs_spectra.cuh"
 
 namespace fsx {
 
@@ -287,6 +288,36 @@ struct OpsImpl {
     return cudaGetLastError();
   }
 
+  static double* profile_region(Sim* s) { return (double*)(s->base + s->L.prof); }
+
+  static cudaError_t profile_B(Sim* s) {
+    const int nx = s->g.nx;
+    double* out = profile_region(s) + s->g.nxn + nx;
+    k_profile_B<T><<<grid_for(nx), kBlock, 0, s->stream>>>(P(s).B, nx, s->g.ny, out);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t spectrum_bperp(Sim* s) {
+    const int nx = s->g.nx, ny = s->g.ny;
+    double* out = profile_region(s) + s->g.nxn + 4 * (size_t)nx;
+    cudaError_t e = cudaMemsetAsync(out, 0, 8 * ((size_t)nx / 2 + 1), s->stream);
+    if (e != cudaSuccess) return e;
+    const bool pow2 = (nx & (nx - 1)) == 0;
+    if (pow2 && nx <= kFftMax) {
+      int logn = 0;
+      while ((1 << logn) < nx) ++logn;
+      const size_t smem = sizeof(double2) * (size_t)nx;
+      e = cudaFuncSetAttribute(k_bperp_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      k_bperp_fft<T><<<ny, kFftThreads, smem, s->stream>>>(P(s).B, nx, ny, logn, out);
+    } else {
+      const long long work = (long long)(nx / 2 + 1) * ny;
+      k_bperp_dft<T><<<grid_for(work), kBlock, 0, s->stream>>>(P(s).B, nx, ny, out);
+    }
+    return cudaGetLastError();
+  }
+
   static cudaError_t profiles(Sim* s) {
     k_profiles<T><<<grid_for(s->g.nxn), kBlock, 0, s->stream>>>(P(s), s->g, s->ph);
     return cudaGetLastError();
@@ -345,6 +376,8 @@ struct OpsImpl {
     o.batch_smem = batch_smem;
     o.batch_setup = batch_setup;
     o.push_batch = push_batch;
+    o.profile_B = profile_B;
+    o.spectrum_bperp = spectrum_bperp;
     o.export_particles = export_particles;
     return o;
   }

@@ -21,6 +21,7 @@ FS_OPEN, FS_SHOCK = 0, 1
 FS_FRAME_SHOCK, FS_FRAME_DOWNSTREAM = 0, 1
 FS_B, FS_E, FS_BBAR, FS_N, FS_J, FS_U = 0, 1, 2, 3, 4, 5
 FS_PROFILE_N, FS_PROFILE_DB2, FS_HIST_XPX, FS_HIST_XPX_CR = 6, 7, 8, 9
+FS_PROFILE_B, FS_SPECTRUM_BPERP = 10, 11
 ID_MASK, ID_CR, ID_RETURNED = 0x3FFFFFFF, 0x40000000, 0x80000000
 
 
@@ -226,7 +227,8 @@ class FauxShock:
         nx, ny, nxn = self.nx, self.ny, self.nxn
         shape = {FS_B: (ny, nx, 3), FS_E: (ny, nxn, 3), FS_BBAR: (ny, nxn, 3),
                  FS_N: (ny, nxn), FS_J: (ny, nxn, 3), FS_U: (ny, nxn, 3),
-                 FS_PROFILE_N: (nxn,), FS_PROFILE_DB2: (nx,)}[what]
+                 FS_PROFILE_N: (nxn,), FS_PROFILE_DB2: (nx,), FS_PROFILE_B: (nx, 3),
+                 FS_SPECTRUM_BPERP: (nx // 2 + 1,)}[what]
         out = np.zeros(shape)
         _check(lib().fs_moments(self._h, what, _ptr(out), out.nbytes, 0), "fs_moments")
         return out
