@@ -102,6 +102,15 @@ typedef struct fs_params {
   int use_graph;           /* replay fs_step as a captured CUDA graph (default 1;
                               the first step runs directly, later ones replay;
                               steps with fs_profile enabled run directly) */
+  double c_light;          /* c / v_A; 0 (default): non-relativistic ions. With
+                              c > 0 (the relativistic code of Sec. 2) particles
+                              carry u = gamma v (momentum per mass, in the vx,
+                              vy, vz slots and in fs_inject / fs_get_particles),
+                              the Boris rotation uses B dt / (2 gamma), moves and
+                              currents use v = u / gamma, the faux shock acts on
+                              v, and p_iso is the CRs' momentum */
+  int spec_np;             /* momentum spectrum n(p) (FS_SPECTRUM_P_*): bins of */
+  double spec_pmin, spec_pmax; /* |u| between log-spaced edges pmin..pmax */
 } fs_params;
 
 /* sizes reported by fs_query */
@@ -144,6 +153,11 @@ typedef struct fs_diag_t {
    k = 0 .. nx/2 (wavenumber 2 pi k / (nx dx)): [nx/2 + 1] doubles. Computed
    in FP64 in every precision. */
 #define FS_SPECTRUM_BPERP 11
+/* Momentum spectra n(p): counts of particles with e_k <= |u| < e_{k+1},
+   e_k = spec_pmin exp((k / spec_np) ln(spec_pmax / spec_pmin)) (edges
+   computed once on the host), k = 0 .. spec_np - 1: [spec_np] int64. */
+#define FS_SPECTRUM_P_CR 12   /* cosmic-ray species */
+#define FS_SPECTRUM_P_ALL 13  /* all particles */
 
 typedef struct fs_handle fs_handle;
 typedef struct fs_batch fs_batch;   /* ensemble of handles stepped together */

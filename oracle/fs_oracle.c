@@ -174,10 +174,18 @@ static void gauss2(double u1, double u2, double* g0, double* g1) {
 /* half electric kick, magnetic rotation with t = B dt/2, s = 2t/(1+t.t),   */
 /* second half kick.                                                         */
 /* ------------------------------------------------------------------------ */
-static void boris(double* v, const double* E, const double* B, double hdt) {
+static void boris(double* v, const double* E, const double* B, double hdt,
+                  double c2inv) {
   double emx = hdt * E[0], emy = hdt * E[1], emz = hdt * E[2];
   double vmx = v[0] + emx, vmy = v[1] + emy, vmz = v[2] + emz;
-  double tx = hdt * B[0], ty = hdt * B[1], tz = hdt * B[2];
+  /* relativistic ions (v holds u = gamma v): the rotation uses
+     t = B dt / (2 gamma-), gamma- from the half-kicked u */
+  double hg = hdt;
+  if (c2inv > 0.0) {
+    double uu = fma(vmz, vmz, fma(vmy, vmy, vmx * vmx));
+    hg = hdt / sqrt(1.0 + uu * c2inv);
+  }
+  double tx = hg * B[0], ty = hg * B[1], tz = hg * B[2];
   double tt = fma(tz, tz, fma(ty, ty, tx * tx));
   double f = 2.0 / (1.0 + tt);
   double sx = f * tx, sy = f * ty, sz = f * tz;
@@ -194,7 +202,12 @@ static void boris(double* v, const double* E, const double* B, double hdt) {
 }
 
 void or_boris(double* v, const double* E, const double* B, double dt) {
-  boris(v, E, B, 0.5 * dt);
+  boris(v, E, B, 0.5 * dt, 0.0);
+}
+
+void or_boris_rel(double* u, const double* E, const double* B, double dt,
+                  double c_light) {
+  boris(u, E, B, 0.5 * dt, c_light > 0.0 ? 1.0 / (c_light * c_light) : 0.0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -255,6 +268,9 @@ struct or_sim {
   int nxn;            /* node columns: nx + 1 (faux-shock box) or nx */
   double dtdx, dtdy, hdt, hdx, hdy, idx, h, hh, h6, te, vth, w_th, w_cr;
   double u2, u_cr, b0x, b0y, b0z, cellvol, rate;
+  double c2inv;      /* 1 / c^2, 0 for non-relativistic ions */
+  double p_iso_v;    /* CR injection speed: p_iso / gamma(p_iso) */
+  double* spec_e;    /* momentum-spectrum bin edges [spec_np + 1] */
   /* particles (SoA) */
   long long np, cap;
   int32_t *ci, *cj;
@@ -301,6 +317,20 @@ static void push_particle(or_sim* s, int32_t i, int32_t j, double fx,
 
 static double weight_of(const or_sim* s, uint32_t id) {
   return (id & ID_CR) ? s->w_cr : s->w_th;
+}
+
+/* 1/gamma of a stored u (momentum per mass): 1/sqrt(1 + u.u/c^2); 1 for
+   non-relativistic ions */
+static double inv_gamma_u(const or_sim* s, double ux, double uy, double uz) {
+  if (s->c2inv == 0.0) return 1.0;
+  double uu = fma(uz, uz, fma(uy, uy, ux * ux));
+  return 1.0 / sqrt(1.0 + uu * s->c2inv);
+}
+/* gamma of a velocity: 1/sqrt(1 - v.v/c^2) */
+static double gamma_v(const or_sim* s, double vx, double vy, double vz) {
+  if (s->c2inv == 0.0) return 1.0;
+  double vv = fma(vz, vz, fma(vy, vy, vx * vx));
+  return 1.0 / sqrt(1.0 - vv * s->c2inv);
 }
 
 static int wrapj(const or_sim* s, int j) {
@@ -422,6 +452,10 @@ static void deposit_and_finish(or_sim* s) {
     int i1 = node_col(s, i + 1);
     double fx = s->fx[k];
     double vx = s->vx[k], vy = s->vy[k], vz = s->vz[k];
+    if (s->c2inv > 0.0) {  /* the current of relativistic ions uses v = u / gamma */
+      double ig = inv_gamma_u(s, vx, vy, vz);
+      vx = vx * ig; vy = vy * ig; vz = vz * ig;
+    }
     if (s->p.dim == 1) {
       double g0 = 1.0 - fx;
       dep1(s, nidx(s, i, 0), wp * g0, vx, vy, vz);
@@ -644,8 +678,15 @@ static void sort_by_cell(or_sim* s) {
   free(id); free(start);
 }
 
+/* kinetic energy of a macroparticle: w v^2 / 2, or w (gamma - 1) c^2 =
+   w u.u / (gamma + 1) for relativistic ions (u stored) */
 static double kin(const or_sim* s, double wp, double vx, double vy,
                   double vz) {
+  if (s->c2inv > 0.0) {
+    double uu = fma(vz, vz, fma(vy, vy, vx * vx));
+    double gamma = sqrt(1.0 + uu * s->c2inv);
+    return (wp * (uu / (gamma + 1.0))) * s->cellvol;
+  }
   return ((wp * 0.5) * ((vx * vx + vy * vy) + vz * vz)) * s->cellvol;
 }
 
@@ -684,6 +725,8 @@ static void inject(or_sim* s, long long step) {
         if (i < 0) { i = 0; fx = 0.0; }
         if (fx >= 1.0) fx = OFFMAX;
         double fy = (s->p.dim == 2) ? or_u01(rb[1]) : 0.0;
+        double gv = gamma_v(s, vx, vy, vz);
+        vx = vx * gv; vy = vy * gv; vz = vz * gv;  /* stored as u */
         push_particle(s, i, j, fx, fy, vx, vy, vz, pid);
         s->injected++;
         s->injected_energy += kin(s, s->w_th, vx, vy, vz);
@@ -694,13 +737,14 @@ static void inject(or_sim* s, long long step) {
         uint32_t pid = (uint32_t)s->next_id++;
         uint32_t rc[4];
         draw4(s->p.seed, pid, step, PURPOSE_INJ_CR, rc);
-        double a = s->u_cr / s->p.p_iso;
+        /* speed p_iso / gamma(p_iso) in the downstream frame (p_iso without c) */
+        double a = s->u_cr / s->p_iso_v;
         double mu = a + (1.0 - a) * sqrt(or_u01(rc[0]));
         double sn = sqrt(1.0 - mu * mu);
         double c, sv;
         or_sincos2pi(or_u01(rc[1]), &c, &sv);
-        double ws = s->p.p_iso * sn;
-        double vx = s->p.p_iso * mu - s->u_cr;
+        double ws = s->p_iso_v * sn;
+        double vx = s->p_iso_v * mu - s->u_cr;
         double vy = ws * c;
         double vz = ws * sv;
         double X = (or_u01(rc[2]) * vx) * dtdx;
@@ -711,6 +755,8 @@ static void inject(or_sim* s, long long step) {
         if (i < 0) { i = 0; fx = 0.0; }
         if (fx >= 1.0) fx = OFFMAX;
         double fy = (s->p.dim == 2) ? or_u01(rc[3]) : 0.0;
+        double gv = gamma_v(s, vx, vy, vz);
+        vx = vx * gv; vy = vy * gv; vz = vz * gv;  /* stored as u */
         push_particle(s, i, j, fx, fy, vx, vy, vz, pid | ID_CR);
         s->injected++;
         s->injected_energy += kin(s, s->w_cr, vx, vy, vz);
@@ -733,9 +779,13 @@ static void push_all(or_sim* s, long long step) {
     uint32_t id = s->id[k];
     double Ep[3], Bp[3];
     gather(s, i, j, fx, fy, Ep, Bp);
-    boris(v, Ep, Bp, s->hdt);
+    boris(v, Ep, Bp, s->hdt, s->c2inv);
+    /* the move uses the velocity (v = u / gamma for relativistic ions) */
+    double ig = inv_gamma_u(s, v[0], v[1], v[2]);
+    double vxm = (s->c2inv > 0.0) ? v[0] * ig : v[0];
+    double vym = (s->c2inv > 0.0) ? v[1] * ig : v[1];
     /* move in x */
-    double fxr = fma(v[0], s->dtdx, fx);
+    double fxr = fma(vxm, s->dtdx, fx);
     double kx = floor(fxr);
     if (!(fabs(kx) < 1.0e9)) { s->err = 1; continue; }
     int inew = i + (int)kx;
@@ -745,7 +795,7 @@ static void push_all(or_sim* s, long long step) {
     int jnew = j;
     double fyn = fy;
     if (s->p.dim == 2) {
-      double fyr = fma(v[1], s->dtdy, fy);
+      double fyr = fma(vym, s->dtdy, fy);
       double ky = floor(fyr);
       if (!(fabs(ky) < 1.0e9)) { s->err = 1; continue; }
       jnew = wrapj(s, j + (int)ky);
@@ -766,9 +816,19 @@ static void push_all(or_sim* s, long long step) {
       int mode = (id & ID_CR) ? OR_FS_SHOCK : s->p.fs_mode_thermal;
       s->incident++;
       double e0 = kin(s, wp, v[0], v[1], v[2]);
+      /* the rule acts on the velocity; a relativistic ion's u is
+         converted to v and back */
+      double vel[3] = {v[0], v[1], v[2]};
+      if (s->c2inv > 0.0) { vel[0] = v[0] * ig; vel[1] = v[1] * ig; vel[2] = v[2] * ig; }
       if (mode == OR_FS_SHOCK &&
-          fs_rule_impl(s->u2, s->p.fs_speed_frame, s->p.seed, v,
+          fs_rule_impl(s->u2, s->p.fs_speed_frame, s->p.seed, vel,
                        id & ID_MASK, step, NULL)) {
+        if (s->c2inv > 0.0) {
+          double gv = gamma_v(s, vel[0], vel[1], vel[2]);
+          v[0] = vel[0] * gv; v[1] = vel[1] * gv; v[2] = vel[2] * gv;
+        } else {
+          v[0] = vel[0]; v[1] = vel[1]; v[2] = vel[2];
+        }
         s->reflected++;
         s->fs_energy += kin(s, wp, v[0], v[1], v[2]) - e0;
         /* re-place: the fraction g of the step spent beyond x = 0 is
@@ -776,7 +836,7 @@ static void push_all(or_sim* s, long long step) {
         double Xo = (double)i + fx;
         double Xn = (double)i + fxr;
         double g = Xn / (Xn - Xo);
-        double f = g * (v[0] * s->dtdx);
+        double f = g * (vel[0] * s->dtdx);
         if (f < 0.0) f = 0.0;
         if (f >= 1.0) f = OFFMAX;
         inew = 0;
@@ -841,6 +901,15 @@ or_sim* or_create(const or_params* p) {
   s->b0y = sin(th);
   s->b0z = 0.0;
   s->cellvol = (p->dim == 2) ? p->dx * p->dy : p->dx;
+  s->c2inv = (p->c_light > 0.0) ? 1.0 / (p->c_light * p->c_light) : 0.0;
+  s->p_iso_v = (s->c2inv > 0.0) ? p->p_iso / sqrt(1.0 + (p->p_iso * p->p_iso) * s->c2inv)
+                                : p->p_iso;
+  if (p->spec_np > 0 && p->spec_pmin > 0.0 && p->spec_pmax > p->spec_pmin) {
+    s->spec_e = (double*)malloc((size_t)(p->spec_np + 1) * sizeof(double));
+    double lr = log(p->spec_pmax / p->spec_pmin);
+    for (int k = 0; k <= p->spec_np; ++k)
+      s->spec_e[k] = p->spec_pmin * exp(((double)k / (double)p->spec_np) * lr);
+  }
   s->rate = (((double)p->ppc * p->mach_a) * p->dt) / p->dx;
   long long nc = (long long)nx * ny, nn = (long long)s->nxn * ny;
   s->B = (double*)calloc(3 * nc, sizeof(double));
@@ -878,6 +947,8 @@ or_sim* or_create(const or_params* p) {
           double vx = s->vth * g0 - p->mach_a;
           double vy = s->vth * g1;
           double vz = s->vth * g2;
+          double gv = gamma_v(s, vx, vy, vz);
+          vx = vx * gv; vy = vy * gv; vz = vz * gv;  /* stored as u */
           push_particle(s, i, j, fx, fy, vx, vy, vz, pid);
         }
       }
@@ -894,7 +965,7 @@ void or_destroy(or_sim* s) {
   free(s->vx); free(s->vy); free(s->vz); free(s->id);
   free(s->B); free(s->Bs); free(s->Bsum); free(s->K);
   free(s->E); free(s->Es); free(s->Bb); free(s->n); free(s->J); free(s->u);
-  free(s->qn); free(s->qj); free(s->acc);
+  free(s->qn); free(s->qj); free(s->acc); free(s->spec_e);
   free(s);
 }
 
@@ -1026,6 +1097,26 @@ int or_diag(const or_sim* s, or_diag_t* o) {
 /* x - p_x histogram of macroparticle counts; species 0 thermal, 1 cosmic
    rays, -1 all. Bin index bx = floor(X nbx / nx) with X = i + fx in cells,
    bp = floor((vx - pmin) nbp / (pmax - pmin)); out-of-range p_x not counted */
+int or_spectrum_p(const or_sim* s, int species, long long* out) {
+  int nb = s->p.spec_np;
+  if (nb < 1 || !s->spec_e) return -1;
+  memset(out, 0, (size_t)nb * sizeof(long long));
+  for (long long k = 0; k < s->np; ++k) {
+    int cr = (s->id[k] & ID_CR) ? 1 : 0;
+    if (species >= 0 && cr != species) continue;
+    double ux = s->vx[k], uy = s->vy[k], uz = s->vz[k];
+    double p = sqrt(fma(uz, uz, fma(uy, uy, ux * ux)));
+    if (!(p >= s->spec_e[0]) || !(p < s->spec_e[nb])) continue;
+    int lo = 0, hi = nb;  /* e[lo] <= p < e[hi] */
+    while (hi - lo > 1) {
+      int mid = (lo + hi) / 2;
+      if (p >= s->spec_e[mid]) lo = mid; else hi = mid;
+    }
+    out[lo]++;
+  }
+  return 0;
+}
+
 int or_histogram(const or_sim* s, int species, long long* out) {
   int nbx = s->p.hist_nx, nbp = s->p.hist_np;
   if (nbx < 1 || nbp < 1) return -1;

@@ -47,6 +47,11 @@ typedef struct {
   uint64_t seed;
   int hist_nx, hist_np;       /* x-p_x histogram shape */
   double hist_pmin, hist_pmax;
+  double c_light;             /* c / v_A; 0: non-relativistic ions. With c > 0
+                                 the stored velocity is u = gamma v (momentum
+                                 per mass), as in the relativistic dHybridR */
+  int spec_np;                /* momentum spectrum n(p): log bins of |u| */
+  double spec_pmin, spec_pmax;
 } or_params;
 
 typedef struct {
@@ -87,6 +92,11 @@ int or_inject(or_sim* s, long long n, const int32_t* ci, const int32_t* cj,
               const double* vy, const double* vz, const uint32_t* ids);
 int or_diag(const or_sim* s, or_diag_t* out);
 int or_histogram(const or_sim* s, int species, long long* out);
+/* Momentum spectrum of one species (-1: all, 0: thermal, 1: cosmic rays):
+   counts of |u| in spec_np bins between log-spaced edges
+   e_k = spec_pmin exp((k / spec_np) ln(spec_pmax / spec_pmin)), bin k for
+   e_k <= |u| < e_{k+1}; out [spec_np]. */
+int or_spectrum_p(const or_sim* s, int species, long long* out);
 void or_gather(const or_sim* s, int i, int j, double fx, double fy,
                double* out6);
 
@@ -97,6 +107,9 @@ double or_u01(uint32_t k);
 double or_log(double x);
 void or_sincos2pi(double u, double* c, double* s);
 void or_boris(double* v, const double* E, const double* B, double dt);
+/* relativistic Boris step of u = gamma v (c_light = c / v_A) */
+void or_boris_rel(double* u, const double* E, const double* B, double dt,
+                  double c_light);
 int or_fs_rule(const or_params* p, double* v, uint32_t pid, long long step,
                double* mu_out);
 

@@ -47,6 +47,8 @@ class OrParams(C.Structure):
         ("seed", C.c_uint64),
         ("hist_nx", C.c_int), ("hist_np", C.c_int),
         ("hist_pmin", C.c_double), ("hist_pmax", C.c_double),
+        ("c_light", C.c_double),
+        ("spec_np", C.c_int), ("spec_pmin", C.c_double), ("spec_pmax", C.c_double),
     ]
 
 
@@ -71,6 +73,7 @@ DEFAULTS = dict(
     inject_thermal=1, cr_enable=0, n_cr_ratio=0.01, p_iso=100.0, u_cr=0.0,
     n_sub=2, n_floor=0.05, eta=0.0, j_cr_ext=0.0, init_plasma=1, seed=1,
     hist_nx=64, hist_np=64, hist_pmin=-40.0, hist_pmax=40.0,
+    c_light=0.0, spec_np=64, spec_pmin=1.0, spec_pmax=1.0e4,
 )
 
 
@@ -109,6 +112,9 @@ def lib():
         L.or_inject.argtypes = [C.c_void_p, C.c_longlong] + [C.c_void_p] * 8
         L.or_diag.argtypes = [C.c_void_p, P(OrDiag)]
         L.or_histogram.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.or_spectrum_p.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.or_boris_rel.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                   C.c_double]
         L.or_gather.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double,
                                 C.c_double, C.c_void_p]
         L.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -181,6 +187,14 @@ def bperp_spectrum(B: np.ndarray) -> np.ndarray:
     Fz = np.fft.fft(B[:, :, 2], axis=1) / nx
     P = (np.abs(Fy) ** 2 + np.abs(Fz) ** 2).mean(axis=0)
     return P[: nx // 2 + 1]
+
+
+def boris_rel(u, E, B, dt, c_light) -> np.ndarray:
+    """One relativistic Boris step of u = gamma v (c_light = c / v_A)."""
+    uu = np.ascontiguousarray(u, dtype=np.float64).copy()
+    lib().or_boris_rel(_ptr(uu), _ptr(np.ascontiguousarray(E, np.float64)),
+                       _ptr(np.ascontiguousarray(B, np.float64)), dt, c_light)
+    return uu
 
 
 def boris(v, E, B, dt) -> np.ndarray:
@@ -281,6 +295,14 @@ class Oracle:
         d = OrDiag()
         lib().or_diag(self._h, C.byref(d))
         return {name: getattr(d, name) for name, _ in OrDiag._fields_}
+
+    def spectrum_p(self, species: int = 1) -> np.ndarray:
+        """Counts of |u| in the log-spaced momentum bins (species -1 all,
+        0 thermal, 1 cosmic rays)."""
+        out = np.zeros(self._p.spec_np, dtype=np.int64)
+        if lib().or_spectrum_p(self._h, species, _ptr(out)) != 0:
+            raise ValueError("momentum spectrum needs spec_np >= 1 and 0 < pmin < pmax")
+        return out
 
     def histogram(self, species: int = -1) -> np.ndarray:
         out = np.zeros((self._p.hist_nx, self._p.hist_np), dtype=np.int64)

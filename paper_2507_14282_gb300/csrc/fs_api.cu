@@ -95,6 +95,9 @@ int validate(const fs_params* p) {
     if (!(p->p_iso > ucr)) return FS_EINVAL;
   }
   if (p->hist_nx < 1 || p->hist_np < 1 || !(p->hist_pmax > p->hist_pmin)) return FS_EINVAL;
+  if (!(p->c_light >= 0)) return FS_EINVAL;
+  if (p->c_light > 0 && !(p->mach_a < p->c_light)) return FS_EINVAL;
+  if (p->spec_np < 1 || !(p->spec_pmin > 0) || !(p->spec_pmax > p->spec_pmin)) return FS_EINVAL;
   if (p->mach_a < 0) return FS_EINVAL;
   return FS_OK;
 }
@@ -184,6 +187,10 @@ int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
   ph->hist_np = p->hist_np;
   ph->hist_pmin = p->hist_pmin;
   ph->hist_pmax = p->hist_pmax;
+  ph->c2inv = (p->c_light > 0.0) ? 1.0 / (p->c_light * p->c_light) : 0.0;
+  ph->p_iso_v = (ph->c2inv > 0.0) ? p->p_iso / sqrt(1.0 + (p->p_iso * p->p_iso) * ph->c2inv)
+                                  : p->p_iso;
+  ph->spec_np = p->spec_np;
 
   // device buffer layout
   const size_t T = (p->precision == FS_FP64) ? 8 : 4;
@@ -231,6 +238,7 @@ int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
   L->inj = take(4 * (2 * (size_t)p->ny + 2));
   L->ctr = take(sizeof(Counters));
   L->hist = take(8 * (size_t)p->hist_nx * p->hist_np);
+  L->spec = take(8 * (2 * (size_t)p->spec_np + 1));  // edges [np + 1], counts [np]
   // profiles: n [nxn], dB^2 [nx], B [nx][3], B-perp spectrum [nx/2 + 1]
   L->prof = take(8 * ((size_t)g->nxn + p->nx + 3 * (size_t)p->nx + (size_t)p->nx / 2 + 1));
   L->total = up(o, kAlign);
@@ -421,6 +429,10 @@ int fs_params_default(int dim, fs_params* out) {
   out->hist_np = 64;
   out->hist_pmin = -40.0;
   out->hist_pmax = 40.0;
+  out->c_light = 0.0;
+  out->spec_np = 64;
+  out->spec_pmin = 1.0;
+  out->spec_pmax = 1.0e4;
   return FS_OK;
 }
 
@@ -503,6 +515,19 @@ int fs_init(const fs_params* p, void* device_mem, size_t device_bytes,
     }
     // the copy reads a host stack value: wait for it before returning
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) { delete h; return FS_ECUDA; }
+  }
+  {
+    // momentum-spectrum bin edges, computed once on the host
+    std::vector<double> edges(p->spec_np + 1);
+    const double lr = log(p->spec_pmax / p->spec_pmin);
+    for (int k = 0; k <= p->spec_np; ++k)
+      edges[k] = p->spec_pmin * exp(((double)k / (double)p->spec_np) * lr);
+    if (cudaMemcpyAsync(s->base + s->L.spec, edges.data(), 8 * edges.size(),
+                        cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess) {
+      delete h;
+      return FS_ECUDA;
+    }
   }
   r = redeposit(s);
   if (r) { delete h; return r; }
@@ -676,6 +701,17 @@ int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes, int dst_on_d
     if (s->ops->profiles(s) != cudaSuccess) return s->sticky = FS_ECUDA;
     const size_t off = s->L.prof + (what == FS_PROFILE_N ? 0 : 8 * (size_t)g.nxn);
     if (cudaMemcpyAsync(dst, s->base + off, 8 * cnt,
+                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess)
+      return s->sticky = FS_ECUDA;
+    return sync_and_check(s);
+  }
+  if (what == FS_SPECTRUM_P_CR || what == FS_SPECTRUM_P_ALL) {
+    const size_t np = (size_t)s->p.spec_np;
+    if (dst_bytes < 8 * np) return FS_EINVAL;
+    if (s->ops->spectrum_p(s, s->cur, what == FS_SPECTRUM_P_CR ? 1 : -1) != cudaSuccess)
+      return s->sticky = FS_ECUDA;
+    if (cudaMemcpyAsync(dst, s->base + s->L.spec + 8 * (np + 1), 8 * np,
                         dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         s->stream) != cudaSuccess)
       return s->sticky = FS_ECUDA;

@@ -70,6 +70,8 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float rcpT(float a) { return __frcp_rn(a); }
 __device__ __forceinline__ double rcpT(double a) { return __drcp_rn(a); }
+__device__ __forceinline__ float sqrtT(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double sqrtT(double a) { return __dsqrt_rn(a); }
 __device__ __forceinline__ double acc_to_double(float a) { return (double)a; }
 __device__ __forceinline__ double acc_to_double(unsigned long long a) {
   return (double)(long long)a * 0x1p-40;
@@ -109,13 +111,47 @@ __device__ __forceinline__ int wrap(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
+// Kinetic energy of a macroparticle of weight wp: wp v^2 / 2 (v stored), or
+// for relativistic ions (u = gamma v stored, c2inv = 1/c^2 > 0)
+// wp (gamma - 1) c^2 = wp u.u / (gamma + 1).
 __device__ __forceinline__ double kinetic(double wp, double vx, double vy,
-                                          double vz, double vol) {
+                                          double vz, double vol, double c2inv = 0.0) {
+  if (c2inv > 0.0) {
+    const double uu = __fma_rn(vz, vz, __fma_rn(vy, vy, __dmul_rn(vx, vx)));
+    const double gamma = __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(uu, c2inv)));
+    return __dmul_rn(__dmul_rn(wp, __ddiv_rn(uu, __dadd_rn(gamma, 1.0))), vol);
+  }
   return __dmul_rn(
       __dmul_rn(__dmul_rn(wp, 0.5),
                 __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)),
                           __dmul_rn(vz, vz))),
       vol);
+}
+
+// 1/gamma of a stored u = gamma v: 1 / sqrt(1 + u.u / c^2)
+template <typename T>
+__device__ __forceinline__ T inv_gamma_u(T ux, T uy, T uz, T c2inv) {
+  const T uu = fmaT(uz, uz, fmaT(uy, uy, ux * ux));
+  return (T)1 / sqrtT((T)1 + uu * c2inv);
+}
+// gamma of a velocity: 1 / sqrt(1 - v.v / c^2)
+__device__ __forceinline__ double gamma_v(double vx, double vy, double vz, double c2inv) {
+  const double vv = __fma_rn(vz, vz, __fma_rn(vy, vy, __dmul_rn(vx, vx)));
+  return __ddiv_rn(1.0, __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(vv, c2inv))));
+}
+// the velocity of a stored state (u for relativistic ions, v otherwise)
+template <typename T>
+__device__ __forceinline__ void velocity_of(T ux, T uy, T uz, T c2inv, T& vx, T& vy, T& vz) {
+  if (c2inv > (T)0) {
+    const T ig = inv_gamma_u(ux, uy, uz, c2inv);
+    vx = ux * ig;
+    vy = uy * ig;
+    vz = uz * ig;
+  } else {
+    vx = ux;
+    vy = uy;
+    vz = uz;
+  }
 }
 
 // ------------------------------------------------------------------------
@@ -125,10 +161,17 @@ __device__ __forceinline__ double kinetic(double wp, double vx, double vy,
 // ------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void boris(T& vx, T& vy, T& vz, const T E[3],
-                                      const T B[3], T hdt) {
+                                      const T B[3], T hdt, T c2inv = (T)0) {
   const T emx = hdt * E[0], emy = hdt * E[1], emz = hdt * E[2];
   const T vmx = vx + emx, vmy = vy + emy, vmz = vz + emz;
-  const T tx = hdt * B[0], ty = hdt * B[1], tz = hdt * B[2];
+  // relativistic ions (u = gamma v stored): t = B dt / (2 gamma-), gamma-
+  // from the half-kicked u
+  T hg = hdt;
+  if (c2inv > (T)0) {
+    const T uu = fmaT(vmz, vmz, fmaT(vmy, vmy, vmx * vmx));
+    hg = hdt / sqrtT((T)1 + uu * c2inv);
+  }
+  const T tx = hg * B[0], ty = hg * B[1], tz = hg * B[2];
   const T tt = fmaT(tz, tz, fmaT(ty, ty, tx * tx));
   // 2 / (1 + t.t) as 2 * (correctly rounded reciprocal): doubling is exact,
   // so this is the same number as the rounded quotient
@@ -279,7 +322,9 @@ __device__ __forceinline__ void place_new(const DevPtrs<T>& d, const Geo& g,
   P.id[gi] = id;
   const double ws = deposit_weight_scale<T>();
   const T wp = (T)(((id & kIdCR) ? ph.w_cr : ph.w_th) * ws);
-  deposit_far<T, DIM>(d, g, i, j, fx, fy, wp, vx, vy, vz);
+  T dvx, dvy, dvz;  // the current uses the velocity
+  velocity_of<T>(vx, vy, vz, (T)ph.c2inv, dvx, dvy, dvz);
+  deposit_far<T, DIM>(d, g, i, j, fx, fy, wp, dvx, dvy, dvz);
 }
 
 // ------------------------------------------------------------------------
@@ -375,9 +420,14 @@ __global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
           if (ft >= (T)1) ft = Num<T>::offmax;
           T fyt = (T)fy;
           if (fyt >= (T)1) fyt = Num<T>::offmax;
-          place_new<T, DIM>(d, g, ph, buf, i, j, ft, fyt, (T)vx, (T)vy, (T)vz, pid);
+          double ux = vx, uy = vy, uz = vz;  // stored as u = gamma v
+          if (ph.c2inv > 0.0) {
+            const double gv = gamma_v(vx, vy, vz, ph.c2inv);
+            ux = __dmul_rn(vx, gv); uy = __dmul_rn(vy, gv); uz = __dmul_rn(vz, gv);
+          }
+          place_new<T, DIM>(d, g, ph, buf, i, j, ft, fyt, (T)ux, (T)uy, (T)uz, pid);
           ++l_inj;
-          l_e = __dadd_rn(l_e, kinetic(ph.w_th, vx, vy, vz, ph.cellvol));
+          l_e = __dadd_rn(l_e, kinetic(ph.w_th, ux, uy, uz, ph.cellvol, ph.c2inv));
         }
       }
       if (ph.cr_enable) {
@@ -388,14 +438,15 @@ __global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
         } else {
           const uint32_t pid = (uint32_t)num;
           const Philox4 rc = draw4(ph.seed, pid, step, kPurposeInjCR);
-          const double a = __ddiv_rn(ph.u_cr, ph.p_iso);
+          // speed p_iso / gamma(p_iso) in the downstream frame (p_iso without c)
+          const double a = __ddiv_rn(ph.u_cr, ph.p_iso_v);
           const double mu =
               __dadd_rn(a, __dmul_rn(__dsub_rn(1.0, a), __dsqrt_rn(u01(rc.x[0]))));
           const double sn = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(mu, mu)));
           double c, s;
           fs_sincos2pi(u01(rc.x[1]), &c, &s);
-          const double ws = __dmul_rn(ph.p_iso, sn);
-          const double vx = __dsub_rn(__dmul_rn(ph.p_iso, mu), ph.u_cr);
+          const double ws = __dmul_rn(ph.p_iso_v, sn);
+          const double vx = __dsub_rn(__dmul_rn(ph.p_iso_v, mu), ph.u_cr);
           const double vy = __dmul_rn(ws, c);
           const double vz = __dmul_rn(ws, s);
           const double X = __dmul_rn(__dmul_rn(u01(rc.x[2]), vx), ph.dtdx);
@@ -410,10 +461,15 @@ __global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
           if (ft >= (T)1) ft = Num<T>::offmax;
           T fyt = (T)fy;
           if (fyt >= (T)1) fyt = Num<T>::offmax;
-          place_new<T, DIM>(d, g, ph, buf, i, j, ft, fyt, (T)vx, (T)vy, (T)vz,
+          double ux = vx, uy = vy, uz = vz;  // stored as u = gamma v
+          if (ph.c2inv > 0.0) {
+            const double gv = gamma_v(vx, vy, vz, ph.c2inv);
+            ux = __dmul_rn(vx, gv); uy = __dmul_rn(vy, gv); uz = __dmul_rn(vz, gv);
+          }
+          place_new<T, DIM>(d, g, ph, buf, i, j, ft, fyt, (T)ux, (T)uy, (T)uz,
                             pid | kIdCR);
           ++l_inj;
-          l_e = __dadd_rn(l_e, kinetic(ph.w_cr, vx, vy, vz, ph.cellvol));
+          l_e = __dadd_rn(l_e, kinetic(ph.w_cr, ux, uy, uz, ph.cellvol, ph.c2inv));
         }
       }
     }
@@ -778,9 +834,13 @@ __global__ void k_init_particles(DevPtrs<T> d, Geo g, Phys ph, int buf, int ppc)
     double g0, g1, g2, g3;
     gauss2(u01(ra.x[2]), u01(ra.x[3]), &g0, &g1);
     gauss2(u01(rb.x[0]), u01(rb.x[1]), &g2, &g3);
-    const double vx = __dsub_rn(__dmul_rn(ph.vth, g0), ph.mach_a);
-    const double vy = __dmul_rn(ph.vth, g1);
-    const double vz = __dmul_rn(ph.vth, g2);
+    double vx = __dsub_rn(__dmul_rn(ph.vth, g0), ph.mach_a);
+    double vy = __dmul_rn(ph.vth, g1);
+    double vz = __dmul_rn(ph.vth, g2);
+    if (ph.c2inv > 0.0) {  // stored as u = gamma v
+      const double gv = gamma_v(vx, vy, vz, ph.c2inv);
+      vx = __dmul_rn(vx, gv); vy = __dmul_rn(vy, gv); vz = __dmul_rn(vz, gv);
+    }
     T ft = (T)fx, fyt = (T)fy;
     if (ft >= (T)1) ft = Num<T>::offmax;
     if (fyt >= (T)1) fyt = Num<T>::offmax;
@@ -808,9 +868,10 @@ __global__ void k_deposit_all(DevPtrs<T> d, Geo g, Phys ph, int buf) {
     const int gi = base + p;
     const int cell = P.cell[gi];
     const uint32_t id = P.id[gi];
+    T vx, vy, vz;  // the current uses the velocity
+    velocity_of<T>(P.vx[gi], P.vy[gi], P.vz[gi], (T)ph.c2inv, vx, vy, vz);
     deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, P.ox[gi],
-                        DIM == 2 ? P.oy[gi] : (T)0, (id & kIdCR) ? wcr : wth,
-                        P.vx[gi], P.vy[gi], P.vz[gi]);
+                        DIM == 2 ? P.oy[gi] : (T)0, (id & kIdCR) ? wcr : wth, vx, vy, vz);
   }
 }
 
@@ -859,7 +920,7 @@ __global__ void k_diag_particles(DevPtrs<T> d, Geo g, Phys ph, int buf) {
     const int gi = base + p;
     const double wp = (P.id[gi] & kIdCR) ? ph.w_cr : ph.w_th;
     const double vx = P.vx[gi], vy = P.vy[gi], vz = P.vz[gi];
-    s[0] += kinetic(wp, vx, vy, vz, ph.cellvol);
+    s[0] += kinetic(wp, vx, vy, vz, ph.cellvol, ph.c2inv);
     s[1] += (wp * vx) * ph.cellvol;
     s[2] += (wp * vy) * ph.cellvol;
     s[3] += (wp * vz) * ph.cellvol;

@@ -71,6 +71,9 @@ struct Phys {
   unsigned long long seed;
   int hist_nx, hist_np;
   double hist_pmin, hist_pmax;
+  double c2inv;    // 1 / c^2 (0: non-relativistic ions)
+  double p_iso_v;  // CR injection speed p_iso / gamma(p_iso)
+  int spec_np;     // momentum-spectrum bins
 };
 
 // Byte offsets of every region inside the caller's device buffer.
@@ -78,7 +81,7 @@ struct Layout {
   size_t part[2][7], mov[7], stg[7];
   size_t tile_base, cnt[2], mcnt;
   size_t B, Bs, Bsum, E, Es, Bb, G, n, u, J, pre;
-  size_t partial, far, acc, inj, ctr, hist, prof;
+  size_t partial, far, acc, inj, ctr, hist, prof, spec;
   size_t total;
 };
 
@@ -141,6 +144,7 @@ struct Ops {
   cudaError_t (*profiles)(Sim*);
   cudaError_t (*profile_B)(Sim*);       // y-averaged B into the profile region
   cudaError_t (*spectrum_bperp)(Sim*);  // B-perp power spectrum into the profile region
+  cudaError_t (*spectrum_p)(Sim*, int buf, int species);  // n(p) counts
   cudaError_t (*export_grid)(Sim*, int what, double* dst_dev);
   cudaError_t (*import_B)(Sim*, const double* src_dev);
   cudaError_t (*export_particles)(Sim*, int buf, double* dst_dev, int* cell_dev,

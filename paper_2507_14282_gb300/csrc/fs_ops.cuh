@@ -318,6 +318,16 @@ struct OpsImpl {
     return cudaGetLastError();
   }
 
+  static cudaError_t spectrum_p(Sim* s, int buf, int species) {
+    const int np = s->p.spec_np;
+    const double* e = (const double*)(s->base + s->L.spec);
+    unsigned long long* out = (unsigned long long*)(s->base + s->L.spec + 8 * ((size_t)np + 1));
+    cudaError_t err = cudaMemsetAsync(out, 0, 8 * (size_t)np, s->stream);
+    if (err != cudaSuccess) return err;
+    k_spectrum_p<T><<<s->g.ntiles, kBlock, 0, s->stream>>>(P(s), s->g, buf, species, np, e, out);
+    return cudaGetLastError();
+  }
+
   static cudaError_t profiles(Sim* s) {
     k_profiles<T><<<grid_for(s->g.nxn), kBlock, 0, s->stream>>>(P(s), s->g, s->ph);
     return cudaGetLastError();
@@ -378,6 +388,7 @@ struct OpsImpl {
     o.push_batch = push_batch;
     o.profile_B = profile_B;
     o.spectrum_bperp = spectrum_bperp;
+    o.spectrum_p = spectrum_p;
     o.export_particles = export_particles;
     return o;
   }

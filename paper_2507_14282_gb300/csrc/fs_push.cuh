@@ -139,7 +139,7 @@ struct PushLayout {
     bstride = o - F[0];
     o += (size_t)(NS - 1) * bstride;
     // the key-sorted copy of the chunk being finished: the four CIC corner
-    // weights, {vx, vy, vz, 0}, {fx, fy}, cell and id per particle
+    // weights, {vx, vy, vz, 1/gamma}, {fx, fy}, cell and id per particle
     sW = take(o, sizeof(T) * 4 * CH);
     sV = take(o, sizeof(T) * 4 * CH);
     sF = take(o, sizeof(T) * 2 * CH);
@@ -313,10 +313,18 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
       Bp[q] = fmaT(w11, v[3 + q], Bp[q]);
     }
   }
-  boris<T>(vx, vy, vz, Ep, Bp, hdt);
-  const T fxr = fmaT(vx, dtdx, fx);
+  const T c2inv = (T)ph.c2inv;
+  boris<T>(vx, vy, vz, Ep, Bp, hdt, c2inv);
+  // the move uses the velocity (v = u / gamma for relativistic ions)
+  T mvx = vx, mvy = vy, ig = (T)1;
+  if (c2inv > (T)0) {
+    ig = inv_gamma_u(vx, vy, vz, c2inv);
+    mvx = vx * ig;
+    mvy = vy * ig;
+  }
+  const T fxr = fmaT(mvx, dtdx, fx);
   T fyr = fy;
-  if (DIM == 2) fyr = fmaT(vy, dtdy, fy);
+  if (DIM == 2) fyr = fmaT(mvy, dtdy, fy);
   // Common case: a tile away from every box edge and a shift of at most one
   // cell: no wall, wrap or far-mover handling can apply. Same values as the
   // general path below (shift in {-1, 0, 1}, subtracted exactly).
@@ -384,18 +392,24 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
   } else if (inew >= g.nx) {
     atomicAdd(&tl->esc, 1ull);
     atomicAdd(&tl->rem, kinetic(cr ? ph.w_cr : ph.w_th, (double)vx, (double)vy, (double)vz,
-                                ph.cellvol));
+                                ph.cellvol, ph.c2inv));
     return NE + 1;
   } else if (inew < 0) {
     const int mode = cr ? FS_SHOCK : ph.fs_mode_thermal;
     const double wpd = cr ? ph.w_cr : ph.w_th;
     atomicAdd(&tl->inc, 1ull);
-    double dvx = vx, dvy = vy, dvz = vz;
-    const double e0 = kinetic(wpd, dvx, dvy, dvz, ph.cellvol);
+    const double e0 = kinetic(wpd, (double)vx, (double)vy, (double)vz, ph.cellvol, ph.c2inv);
+    // the rule acts on the velocity: a relativistic ion's u -> v -> u
+    double dvx = mvx, dvy = (c2inv > (T)0) ? vy * ig : vy, dvz = (c2inv > (T)0) ? vz * ig : vz;
     if (mode == FS_SHOCK &&
         fs_return(dvx, dvy, dvz, ph.u2, ph.fs_frame, ph.seed, id & kIdMask, step)) {
+      double ux = dvx, uy = dvy, uz = dvz;
+      if (ph.c2inv > 0.0) {
+        const double gv = gamma_v(dvx, dvy, dvz, ph.c2inv);
+        ux = __dmul_rn(dvx, gv); uy = __dmul_rn(dvy, gv); uz = __dmul_rn(dvz, gv);
+      }
       atomicAdd(&tl->ref, 1ull);
-      atomicAdd(&tl->fse, __dsub_rn(kinetic(wpd, dvx, dvy, dvz, ph.cellvol), e0));
+      atomicAdd(&tl->fse, __dsub_rn(kinetic(wpd, ux, uy, uz, ph.cellvol, ph.c2inv), e0));
       const double Xo = __dadd_rn((double)i, (double)fx);
       const double Xn = __dadd_rn((double)i, (double)fxr);
       const double gfr = __ddiv_rn(Xn, __dsub_rn(Xn, Xo));
@@ -407,9 +421,9 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
       fxn = ft;
       inew = 0;
       iunw = 0;
-      vx = (T)dvx;
-      vy = (T)dvy;
-      vz = (T)dvz;
+      vx = (T)ux;
+      vy = (T)uy;
+      vz = (T)uz;
       id |= kIdReturned;
     } else {
       atomicAdd(&tl->tr, 1ull);
@@ -464,7 +478,7 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
 
 
 // CIC deposit of one key's particles, which sit contiguously in [b0, b1) of
-// the key-sorted chunk (W: corner weights, V: {vx, vy, vz, 0}). The warp
+// the key-sorted chunk (W: corner weights, V: {vx, vy, vz, 1/gamma}). The warp
 // works as NC corners x SPL splits: lane (corner c, split s) sums corner c's
 // four quantities (weight, weight * v) over particles b0 + s, b0 + s + SPL,
 // ...; a transpose reduction over the splits then leaves each quantity's
@@ -473,10 +487,15 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
 // the sums do not depend on the order.
 template <typename T>
 __device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T* W,
-                                         const T* V, int i, int c) {
+                                         const T* V, int i, int c, bool rel) {
   const T cw = W[4 * i + c];
   T v[4];
   ld4(V + 4 * i, v);
+  if (rel) {  // relativistic ions: V holds u and 1/gamma
+    v[0] = v[0] * v[3];
+    v[1] = v[1] * v[3];
+    v[2] = v[2] * v[3];
+  }
   acc[0] = acc[0] + to_acc(cw);
   acc[1] = acc[1] + to_acc_prod(cw, v[0]);
   acc[2] = acc[2] + to_acc_prod(cw, v[1]);
@@ -486,7 +505,7 @@ __device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T
 template <typename T, int DIM>
 __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, int AX,
                                              int le, int b0, int b1, const T* W, const T* V,
-                                             int lane) {
+                                             int lane, bool rel) {
   using A_t = typename Num<T>::acc;
   constexpr int NC = (DIM == 2) ? 4 : 2;
   constexpr int SPL = 32 / NC;
@@ -494,10 +513,10 @@ __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, 
   A_t acc[4] = {(A_t)0, (A_t)0, (A_t)0, (A_t)0};
   int i = b0 + s;
   for (; i + SPL < b1; i += 2 * SPL) {  // two particles in flight per lane
-    team_add<T>(acc, W, V, i, c);
-    team_add<T>(acc, W, V, i + SPL, c);
+    team_add<T>(acc, W, V, i, c, rel);
+    team_add<T>(acc, W, V, i + SPL, c, rel);
   }
-  if (i < b1) team_add<T>(acc, W, V, i, c);
+  if (i < b1) team_add<T>(acc, W, V, i, c, rel);
   // two halving levels leave one quantity per lane, the rest add pairs
   {
     const bool up = (s & (SPL / 2)) != 0;
@@ -562,6 +581,7 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
   const T wth = (T)(ph.w_th * (double)deposit_weight_scale<T>());
   const T wcr = (T)(ph.w_cr * (double)deposit_weight_scale<T>());
   const long long step = d.ctr->step;  // device step counter (graph-replayable)
+  const bool rel = ph.c2inv > 0.0;     // relativistic ions: states hold u = gamma v
 
   // ---- per-CTA tables: extended cell <-> sort key; zero accumulators
   for (int e = tid; e < NE; e += kBlock) {
@@ -657,9 +677,12 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
         key = push_one<T, DIM>(F, L.NFX, cell, fx, fy, vx, vy, vz, id, i0, j0, TX, TY, EX,
                                EY, NE, e2k, g, ph, dtdx, dtdy, hdt, step, tl,
                                status, inner);
-        if (key == NE)  // far mover: straight to the global far sums
+        if (key == NE) {  // far mover: straight to the global far sums
+          T dvx, dvy, dvz;  // the current uses the velocity
+          velocity_of<T>(vx, vy, vz, (T)ph.c2inv, dvx, dvy, dvz);
           deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, fx, fy,
-                              (id & kIdCR) ? wcr : wth, vx, vy, vz);
+                              (id & kIdCR) ? wcr : wth, dvx, dvy, dvz);
+        }
         sc[p] = cell;
         sx[p] = fx;
         if (DIM == 2) sy[p] = fy;
@@ -717,7 +740,9 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       oc[pos] = sc[p];
       oid[pos] = id;
       st2(oF + 2 * pos, fx, fy);
-      st4(oV + 4 * pos, svx[p], svy[p], svz[p], (T)0);
+      // {u} of the state, and 1/gamma (the current uses v = u / gamma)
+      st4(oV + 4 * pos, svx[p], svy[p], svz[p],
+          rel ? inv_gamma_u(svx[p], svy[p], svz[p], (T)ph.c2inv) : (T)1);
       // corner weights: wp * (gx * gy), corners (0,0) (1,0) (0,1) (1,1)
       const T gx0 = (T)1 - fx;
       if (DIM == 2) {
@@ -793,7 +818,7 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       }
       for (; k < NE && wk[k] < r1; ++k) {
         const int b0 = max(wk[k], r0), b1 = min(wk[k + 1], r1);
-        if (b0 < b1) team_deposit<T, DIM>(ACC, NA, AX, k2e[k], b0, b1, oW, oV, lane);
+        if (b0 < b1) team_deposit<T, DIM>(ACC, NA, AX, k2e[k], b0, b1, oW, oV, lane, rel);
       }
     }
     outRun += S;

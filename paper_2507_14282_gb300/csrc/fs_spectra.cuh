@@ -1,7 +1,8 @@
-// fs_spectra.cuh -- magnetic-field diagnostics of the paper's Sec. 3.1:
-// transversely averaged lineouts of Bx, By, Bz and the perpendicular power
-// spectrum < |F_perp(k_x, y)|^2 > = |F[By]|^2 + |F[Bz]|^2 averaged over y
-// (Fig. 3 caption), F the DFT along x normalised by 1/nx. FP64 in every
+// fs_spectra.cuh -- diagnostics of the paper's Sec. 3: transversely averaged
+// lineouts of Bx, By, Bz and the perpendicular power spectrum
+// < |F_perp(k_x, y)|^2 > = |F[By]|^2 + |F[Bz]|^2 averaged over y (Sec. 3.1,
+// Fig. 3 caption), F the DFT along x normalised by 1/nx; and the momentum
+// spectrum n(p) of the particles (the CR spectra of Sec. 3). FP64 in every
 // precision; not on the per-step path.
 //
 // The spectrum packs each row into one complex sequence z = By + i Bz: for
@@ -104,6 +105,31 @@ __global__ void k_bperp_dft(const T* __restrict__ B, int nx, int ny, double* __r
       w = cmul(w, step);
     }
     add_power(P, k, zk, zm, nx, ny);
+  }
+}
+
+// Momentum spectrum n(p): counts of |u| between the log-spaced edges
+// e[0..np] (e[k] <= |u| < e[k+1]); species -1 all, 1 cosmic rays only.
+// Integer counts, bins chosen by exact comparisons with |u| = sqrt(u.u).
+template <typename T>
+__global__ void k_spectrum_p(DevPtrs<T> d, Geo g, int buf, int species, int np,
+                             const double* __restrict__ e,
+                             unsigned long long* __restrict__ out) {
+  const int t = blockIdx.x;
+  const int cnt = min(d.cnt[buf][t], g.tile_cap), base = d.tile_base[t];
+  const Parts<T> P = d.P[buf];
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const int gi = base + q;
+    if (species == 1 && !(P.id[gi] & kIdCR)) continue;
+    const double ux = P.vx[gi], uy = P.vy[gi], uz = P.vz[gi];
+    const double p = __dsqrt_rn(__fma_rn(uz, uz, __fma_rn(uy, uy, __dmul_rn(ux, ux))));
+    if (!(p >= e[0]) || !(p < e[np])) continue;
+    int lo = 0, hi = np;  // e[lo] <= p < e[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (p >= e[mid]) lo = mid; else hi = mid;
+    }
+    atomicAdd(&out[lo], 1ull);
   }
 }
 

@@ -22,6 +22,7 @@ FS_FRAME_SHOCK, FS_FRAME_DOWNSTREAM = 0, 1
 FS_B, FS_E, FS_BBAR, FS_N, FS_J, FS_U = 0, 1, 2, 3, 4, 5
 FS_PROFILE_N, FS_PROFILE_DB2, FS_HIST_XPX, FS_HIST_XPX_CR = 6, 7, 8, 9
 FS_PROFILE_B, FS_SPECTRUM_BPERP = 10, 11
+FS_SPECTRUM_P_CR, FS_SPECTRUM_P_ALL = 12, 13
 ID_MASK, ID_CR, ID_RETURNED = 0x3FFFFFFF, 0x40000000, 0x80000000
 
 
@@ -46,6 +47,8 @@ class FsParams(C.Structure):
         ("hist_nx", C.c_int), ("hist_np", C.c_int),
         ("hist_pmin", C.c_double), ("hist_pmax", C.c_double),
         ("use_graph", C.c_int),
+        ("c_light", C.c_double),
+        ("spec_np", C.c_int), ("spec_pmin", C.c_double), ("spec_pmax", C.c_double),
     ]
 
 
@@ -237,6 +240,13 @@ class FauxShock:
         """Writes a grid quantity as FP64 into a CUDA tensor (no host copy)."""
         _check(lib().fs_moments(self._h, what, C.c_void_p(out.data_ptr()),
                                 out.numel() * out.element_size(), 1), "fs_moments")
+
+    def spectrum_p(self, cr_only: bool = True) -> np.ndarray:
+        """Momentum spectrum n(p): counts of |u| in spec_np log-spaced bins."""
+        out = np.zeros(self._p.spec_np, dtype=np.int64)
+        what = FS_SPECTRUM_P_CR if cr_only else FS_SPECTRUM_P_ALL
+        _check(lib().fs_moments(self._h, what, _ptr(out), out.nbytes, 0), "fs_moments")
+        return out
 
     def histogram(self, cr_only: bool = False) -> np.ndarray:
         out = np.zeros((self._p.hist_nx, self._p.hist_np), dtype=np.int64)
