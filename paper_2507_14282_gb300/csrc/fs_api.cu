@@ -950,6 +950,7 @@ struct fs_batch {
   int ncta = 0;
   size_t smem = 0;
   int dim = 1;
+  int rel = 0;  // some run has relativistic ions (c > 0)
   const Ops* ops = nullptr;
   int parity = 0;  // steps taken, mod 2
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -962,7 +963,7 @@ namespace {
 // one launch, then each run's remaining kernels on its branch.
 cudaError_t batch_enqueue(fs_batch* b, int p, cudaStream_t st) {
   const int nr = (int)b->runs.size();
-  cudaError_t e = b->ops->push_batch(b->dim, b->table + (size_t)p * nr * b->rec, b->map,
+  cudaError_t e = b->ops->push_batch(b->dim, b->rel, b->table + (size_t)p * nr * b->rec, b->map,
                                      b->ncta, b->smem, st);
   if (e != cudaSuccess) return e;
   if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
@@ -1081,13 +1082,16 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
   if (table_bytes < need || ((uintptr_t)table_dev % kAlign) != 0) return FS_EINVAL;
   const Ops* ops = s0.ops;
   size_t smem = 0;
-  for (int r = 0; r < nruns; ++r)
+  int rel = 0;
+  for (int r = 0; r < nruns; ++r) {
     smem = std::max(smem, ops->batch_smem(s0.g.dim, runs[r]->sim.g.TX, runs[r]->sim.g.TY));
+    if (runs[r]->sim.ph.c2inv > 0.0) rel = 1;
+  }
   if (smem > 227 * 1024 - 2048) return FS_EINVAL;
   int dev = 0, nsm = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      ops->batch_setup(s0.g.dim, smem, &occ) != cudaSuccess || occ < 1)
+      ops->batch_setup(s0.g.dim, rel, smem, &occ) != cudaSuccess || occ < 1)
     return FS_ECUDA;
   const int ncta_max = std::min(nsm * occ, kBatchMaxCtas);
   std::vector<long long> np(nruns);
@@ -1104,6 +1108,7 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
   b->stream = s0.stream;
   b->ops = ops;
   b->dim = s0.g.dim;
+  b->rel = rel;
   b->smem = smem;
   b->rec = batch_rec_bytes(s0.p.precision);
   b->table = (char*)table_dev;

@@ -134,9 +134,10 @@ struct Ops {
   size_t (*batch_run_bytes)();
   void (*fill_batch_run)(const Sim*, int in_buf, int ncta, void* dst);
   size_t (*batch_smem)(int dim, int tx, int ty);
-  cudaError_t (*batch_setup)(int dim, size_t smem, int* occ);
-  cudaError_t (*push_batch)(int dim, const void* runs, const int2* cta_map, int ncta,
-                            size_t smem, cudaStream_t st);
+  // rel: the push variant with the relativistic terms (some run has c > 0)
+  cudaError_t (*batch_setup)(int dim, int rel, size_t smem, int* occ);
+  cudaError_t (*push_batch)(int dim, int rel, const void* runs, const int2* cta_map,
+                            int ncta, size_t smem, cudaStream_t st);
   cudaError_t (*fields)(Sim*);
   cudaError_t (*insert_staged)(Sim*, int buf, int n, bool from_movers);
   cudaError_t (*diag)(Sim*, int buf);

@@ -17,14 +17,14 @@ inline int grid_for(long long n, int block = kBlock) {
   return (int)g;
 }
 
-template <typename T, int DIM, int CH, int NS>
+template <typename T, int DIM, int CH, int NS, bool REL>
 cudaError_t launch_push(Sim* s, int in, long long step) {
   const PushLayout<T, DIM> L(s->g.TX, s->g.TY, CH, NS);
   static size_t attr_bytes = 0;  // largest dynamic shared memory enabled so far
   static size_t occ_bytes = 0;
   static int occ_blocks = 1, n_sm = 0;
   if (L.bytes > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_push<T, DIM, CH, NS>,
+    cudaError_t e = cudaFuncSetAttribute(k_push<T, DIM, CH, NS, REL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L.bytes);
     if (e != cudaSuccess) return e;
@@ -35,7 +35,7 @@ cudaError_t launch_push(Sim* s, int in, long long step) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, k_push<T, DIM, CH, NS>,
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, k_push<T, DIM, CH, NS, REL>,
                                                         kBlock, L.bytes);
     if (e != cudaSuccess) return e;
     if (occ_blocks < 1) return cudaErrorInvalidConfiguration;
@@ -49,7 +49,7 @@ cudaError_t launch_push(Sim* s, int in, long long step) {
   a.step = step;
   const long long want = (long long)n_sm * occ_blocks;
   const int grid = (int)std::min<long long>(want, s->g.ntiles);
-  k_push<T, DIM, CH, NS><<<grid, kBlock, L.bytes, s->stream>>>(s->ptrs<T>(), a);
+  k_push<T, DIM, CH, NS, REL><<<grid, kBlock, L.bytes, s->stream>>>(s->ptrs<T>(), a);
   return cudaGetLastError();
 }
 
@@ -70,9 +70,15 @@ struct PushShape<double> {
 template <typename T, int DIM>
 cudaError_t push_dispatch(Sim* s, int in, long long step) {
   using S = PushShape<T>;
+  // the relativistic terms are compiled in only for runs with a finite c
+  if (s->ph.c2inv > 0.0) {
+    if (s->g.chunk == S::kChunkSmall)
+      return launch_push<T, DIM, S::kChunkSmall, S::kStagesSmall, true>(s, in, step);
+    return launch_push<T, DIM, S::kChunkLarge, S::kStagesLarge, true>(s, in, step);
+  }
   if (s->g.chunk == S::kChunkSmall)
-    return launch_push<T, DIM, S::kChunkSmall, S::kStagesSmall>(s, in, step);
-  return launch_push<T, DIM, S::kChunkLarge, S::kStagesLarge>(s, in, step);
+    return launch_push<T, DIM, S::kChunkSmall, S::kStagesSmall, false>(s, in, step);
+  return launch_push<T, DIM, S::kChunkLarge, S::kStagesLarge, false>(s, in, step);
 }
 
 template <typename T>
@@ -228,28 +234,43 @@ struct OpsImpl {
     return dim == 1 ? PushLayout<T, 1>(tx, ty, S::kChunkLarge, S::kStagesLarge).bytes
                     : PushLayout<T, 2>(tx, ty, S::kChunkLarge, S::kStagesLarge).bytes;
   }
-  template <int DIM>
+  template <int DIM, bool REL>
   static cudaError_t batch_kernel_setup(size_t smem, int* occ) {
     using S = PushShape<T>;
-    auto kern = k_push_batch<T, DIM, S::kChunkLarge, S::kStagesLarge>;
+    auto kern = k_push_batch<T, DIM, S::kChunkLarge, S::kStagesLarge, REL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess && occ)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, kBlock, smem);
     return e;
   }
-  // sets the shared-memory attribute; occ (optional): CTAs per SM
-  static cudaError_t batch_setup(int dim, size_t smem, int* occ) {
-    return dim == 1 ? batch_kernel_setup<1>(smem, occ) : batch_kernel_setup<2>(smem, occ);
+  // sets the shared-memory attribute; occ (optional): CTAs per SM. rel: the
+  // variant with the relativistic terms (some run has a finite c).
+  static cudaError_t batch_setup(int dim, int rel, size_t smem, int* occ) {
+    if (rel)
+      return dim == 1 ? batch_kernel_setup<1, true>(smem, occ)
+                      : batch_kernel_setup<2, true>(smem, occ);
+    return dim == 1 ? batch_kernel_setup<1, false>(smem, occ)
+                    : batch_kernel_setup<2, false>(smem, occ);
   }
-  static cudaError_t push_batch(int dim, const void* runs, const int2* cta_map, int ncta,
+  template <bool REL>
+  static void push_batch_launch(int dim, const BatchRun<T>* r, const int2* cta_map, int ncta,
                                 size_t smem, cudaStream_t st) {
     using S = PushShape<T>;
-    const BatchRun<T>* r = (const BatchRun<T>*)runs;
     if (dim == 1)
-      k_push_batch<T, 1, S::kChunkLarge, S::kStagesLarge><<<ncta, kBlock, smem, st>>>(r, cta_map);
+      k_push_batch<T, 1, S::kChunkLarge, S::kStagesLarge, REL>
+          <<<ncta, kBlock, smem, st>>>(r, cta_map);
     else
-      k_push_batch<T, 2, S::kChunkLarge, S::kStagesLarge><<<ncta, kBlock, smem, st>>>(r, cta_map);
+      k_push_batch<T, 2, S::kChunkLarge, S::kStagesLarge, REL>
+          <<<ncta, kBlock, smem, st>>>(r, cta_map);
+  }
+  static cudaError_t push_batch(int dim, int rel, const void* runs, const int2* cta_map,
+                                int ncta, size_t smem, cudaStream_t st) {
+    const BatchRun<T>* r = (const BatchRun<T>*)runs;
+    if (rel)
+      push_batch_launch<true>(dim, r, cta_map, ncta, smem, st);
+    else
+      push_batch_launch<false>(dim, r, cta_map, ncta, smem, st);
     return cudaGetLastError();
   }
 

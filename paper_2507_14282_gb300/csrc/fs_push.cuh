@@ -257,7 +257,7 @@ struct PushTally {
   double fse, rem;
 };
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool REL>
 __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& cell,
                                         T& fx, T& fy, T& vx, T& vy, T& vz,
                                         uint32_t& id, int i0, int j0, int TX, int TY,
@@ -313,7 +313,8 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
       Bp[q] = fmaT(w11, v[3 + q], Bp[q]);
     }
   }
-  const T c2inv = (T)ph.c2inv;
+  // REL = false: the relativistic terms are compiled out (c2inv taken as 0)
+  const T c2inv = REL ? (T)ph.c2inv : (T)0;
   boris<T>(vx, vy, vz, Ep, Bp, hdt, c2inv);
   // the move uses the velocity (v = u / gamma for relativistic ions)
   T mvx = vx, mvy = vy, ig = (T)1;
@@ -404,7 +405,7 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
     if (mode == FS_SHOCK &&
         fs_return(dvx, dvy, dvz, ph.u2, ph.fs_frame, ph.seed, id & kIdMask, step)) {
       double ux = dvx, uy = dvy, uz = dvz;
-      if (ph.c2inv > 0.0) {
+      if (REL && ph.c2inv > 0.0) {
         const double gv = gamma_v(dvx, dvy, dvz, ph.c2inv);
         ux = __dmul_rn(dvx, gv); uy = __dmul_rn(dvy, gv); uz = __dmul_rn(dvz, gv);
       }
@@ -485,13 +486,13 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
 // total in one lane, which adds it to the tile's node accumulator. Each
 // contribution is formed as in the per-particle scheme, so in fixed point
 // the sums do not depend on the order.
-template <typename T>
+template <typename T, bool REL>
 __device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T* W,
-                                         const T* V, int i, int c, bool rel) {
+                                         const T* V, int i, int c) {
   const T cw = W[4 * i + c];
   T v[4];
   ld4(V + 4 * i, v);
-  if (rel) {  // relativistic ions: V holds u and 1/gamma
+  if (REL) {  // relativistic ions: V holds u and 1/gamma
     v[0] = v[0] * v[3];
     v[1] = v[1] * v[3];
     v[2] = v[2] * v[3];
@@ -502,10 +503,10 @@ __device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T
   acc[3] = acc[3] + to_acc_prod(cw, v[2]);
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool REL>
 __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, int AX,
                                              int le, int b0, int b1, const T* W, const T* V,
-                                             int lane, bool rel) {
+                                             int lane) {
   using A_t = typename Num<T>::acc;
   constexpr int NC = (DIM == 2) ? 4 : 2;
   constexpr int SPL = 32 / NC;
@@ -513,10 +514,10 @@ __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, 
   A_t acc[4] = {(A_t)0, (A_t)0, (A_t)0, (A_t)0};
   int i = b0 + s;
   for (; i + SPL < b1; i += 2 * SPL) {  // two particles in flight per lane
-    team_add<T>(acc, W, V, i, c, rel);
-    team_add<T>(acc, W, V, i + SPL, c, rel);
+    team_add<T, REL>(acc, W, V, i, c);
+    team_add<T, REL>(acc, W, V, i + SPL, c);
   }
-  if (i < b1) team_add<T>(acc, W, V, i, c, rel);
+  if (i < b1) team_add<T, REL>(acc, W, V, i, c);
   // two halving levels leave one quantity per lane, the rest add pairs
   {
     const bool up = (s & (SPL / 2)) != 0;
@@ -555,7 +556,7 @@ __device__ __forceinline__ void drain_stages(unsigned char* sm, const PushLayout
 
 // The push of one run by one CTA of a group of G CTAs (rank cta in the
 // group): tiles cta, cta + G, ... of the run; sm is the dynamic shared memory.
-template <typename T, int DIM, int CH, int NS>
+template <typename T, int DIM, int CH, int NS, bool REL>
 __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, const Phys& ph,
                                          int in, int out, int cta, int G,
                                          unsigned char* sm) {
@@ -581,7 +582,9 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
   const T wth = (T)(ph.w_th * (double)deposit_weight_scale<T>());
   const T wcr = (T)(ph.w_cr * (double)deposit_weight_scale<T>());
   const long long step = d.ctr->step;  // device step counter (graph-replayable)
-  const bool rel = ph.c2inv > 0.0;     // relativistic ions: states hold u = gamma v
+  // relativistic ions (REL and c2inv > 0): states hold u = gamma v
+  const bool rel = REL && ph.c2inv > 0.0;
+  const T c2inv = REL ? (T)ph.c2inv : (T)0;
 
   // ---- per-CTA tables: extended cell <-> sort key; zero accumulators
   for (int e = tid; e < NE; e += kBlock) {
@@ -674,12 +677,12 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
         T fy = (DIM == 2) ? sy[p] : (T)0;
         T vx = svx[p], vy = svy[p], vz = svz[p];
         uint32_t id = sid[p];
-        key = push_one<T, DIM>(F, L.NFX, cell, fx, fy, vx, vy, vz, id, i0, j0, TX, TY, EX,
+        key = push_one<T, DIM, REL>(F, L.NFX, cell, fx, fy, vx, vy, vz, id, i0, j0, TX, TY, EX,
                                EY, NE, e2k, g, ph, dtdx, dtdy, hdt, step, tl,
                                status, inner);
         if (key == NE) {  // far mover: straight to the global far sums
           T dvx, dvy, dvz;  // the current uses the velocity
-          velocity_of<T>(vx, vy, vz, (T)ph.c2inv, dvx, dvy, dvz);
+          velocity_of<T>(vx, vy, vz, c2inv, dvx, dvy, dvz);
           deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, fx, fy,
                               (id & kIdCR) ? wcr : wth, dvx, dvy, dvz);
         }
@@ -742,7 +745,7 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       st2(oF + 2 * pos, fx, fy);
       // {u} of the state, and 1/gamma (the current uses v = u / gamma)
       st4(oV + 4 * pos, svx[p], svy[p], svz[p],
-          rel ? inv_gamma_u(svx[p], svy[p], svz[p], (T)ph.c2inv) : (T)1);
+          rel ? inv_gamma_u(svx[p], svy[p], svz[p], c2inv) : (T)1);
       // corner weights: wp * (gx * gy), corners (0,0) (1,0) (0,1) (1,1)
       const T gx0 = (T)1 - fx;
       if (DIM == 2) {
@@ -818,7 +821,7 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       }
       for (; k < NE && wk[k] < r1; ++k) {
         const int b0 = max(wk[k], r0), b1 = min(wk[k + 1], r1);
-        if (b0 < b1) team_deposit<T, DIM>(ACC, NA, AX, k2e[k], b0, b1, oW, oV, lane, rel);
+        if (b0 < b1) team_deposit<T, DIM, REL>(ACC, NA, AX, k2e[k], b0, b1, oW, oV, lane);
       }
     }
     outRun += S;
@@ -854,17 +857,18 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
 }
 
 
-template <typename T, int DIM, int CH, int NS>
+// REL: compiled with the relativistic terms (used when c2inv > 0).
+template <typename T, int DIM, int CH, int NS, bool REL>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPtrs<T> d, StepArgs a) {
   extern __shared__ __align__(128) unsigned char sm[];
-  push_run<T, DIM, CH, NS>(d, a.g, a.ph, a.in, a.out, blockIdx.x, gridDim.x, sm);
+  push_run<T, DIM, CH, NS, REL>(d, a.g, a.ph, a.in, a.out, blockIdx.x, gridDim.x, sm);
 }
 
 // Batched push of an ensemble of independent runs in one persistent launch:
 // CTA b works on run cta_map[b].x as rank cta_map[b].y of that run's group of
 // runs[run].ncta CTAs; the run's pointers, geometry and physics come from the
 // device table, copied once into shared memory.
-template <typename T, int DIM, int CH, int NS>
+template <typename T, int DIM, int CH, int NS, bool REL>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
     k_push_batch(const BatchRun<T>* __restrict__ runs, const int2* __restrict__ cta_map) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -875,7 +879,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
   int* dst = reinterpret_cast<int*>(&R);
   for (int k = threadIdx.x; k < (int)(sizeof(BatchRun<T>) / 4); k += kBlock) dst[k] = src[k];
   __syncthreads();
-  push_run<T, DIM, CH, NS>(R.d, R.g, R.ph, R.in, R.out, cm.y, R.ncta, sm);
+  push_run<T, DIM, CH, NS, REL>(R.d, R.g, R.ph, R.in, R.out, cm.y, R.ncta, sm);
 }
 
 }  // namespace fsx
