@@ -45,7 +45,7 @@ extern "C" {
 #define FS_EIDOVERFLOW (-4)   /* more than 2^30 particle ids issued */
 #define FS_ECUDA (-5)         /* a CUDA call or kernel launch failed */
 #define FS_ETIMEOUT (-6)      /* reserved: a bounded device wait ran out */
-#define FS_EUNSTABLE (-7)     /* reserved: field solve beyond its stability bound */
+#define FS_EUNSTABLE (-7)     /* fs_diag: field integrator beyond its RK4 stability bound */
 
 /* precision of particle and field arithmetic */
 #define FS_FP64 0
@@ -133,7 +133,16 @@ typedef struct fs_diag_t {
   double injected_energy, removed_energy;
   int status;                     /* sticky device status bits */
   long long launches;             /* kernels this handle has launched */
+  /* Stability number of the field integrator: z = h omega_max, h = dt/n_sub
+     the RK4 substep and omega_max = max over nodes of
+     (4/dx^2 + 4/dy^2) |Bbar| / n + (2/dx + 2/dy) |u| (no dy terms in 1D), an
+     upper estimate of the fastest discrete mode (grid-scale whistler plus
+     advection). RK4 is stable on the imaginary axis for z <= FS_RK4_Z_MAX;
+     above it fs_diag returns FS_EUNSTABLE (with *out filled in). */
+  double max_z;
 } fs_diag_t;
+
+#define FS_RK4_Z_MAX 2.8284271247461903 /* 2 sqrt 2 */
 
 /* what codes for fs_moments */
 #define FS_B 0            /* B at cell centres: [ny][nx][3] doubles */

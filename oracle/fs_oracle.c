@@ -288,6 +288,7 @@ struct or_sim {
   long long step, next_id;
   long long incident, transmitted, reflected, escaped, injected;
   double fs_energy, injected_energy, removed_energy;
+  double push_work;  /* cumulative work of E on the ions in the pushes */
   int err;
 };
 
@@ -690,6 +691,24 @@ static double kin(const or_sim* s, double wp, double vx, double vy,
   return ((wp * 0.5) * ((vx * vx + vy * vy) + vz * vz)) * s->cellvol;
 }
 
+/* Work done by E on one macroparticle in a Boris step. The magnetic
+   rotation keeps |u-| (u = v, or gamma v for relativistic ions), so
+   |u_new|^2 - |u_old|^2 = dt E.(u_new + u_old) exactly, and the kinetic
+   energy w (gamma - 1) c^2 (w u^2 / 2 without c) changes by
+   w dt E.(u_new + u_old) / (gamma_new + gamma_old), gamma = 1 without c. */
+static double push_work_of(const or_sim* s, double wp, const double* E,
+                           const double* uo, const double* un) {
+  double es = E[0] * (uo[0] + un[0]) + E[1] * (uo[1] + un[1]) +
+              E[2] * (uo[2] + un[2]);
+  double gsum = 2.0;
+  if (s->c2inv > 0.0) {
+    double uuo = uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2];
+    double uun = un[0] * un[0] + un[1] * un[1] + un[2] * un[2];
+    gsum = sqrt(1.0 + uuo * s->c2inv) + sqrt(1.0 + uun * s->c2inv);
+  }
+  return ((wp * s->p.dt) * es / gsum) * s->cellvol;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Injection (Sec. 2): thermal plasma enters through x = L drifting at -u_sh*/
 /* (a drifting Maxwellian); optionally cosmic rays enter at the faux shock  */
@@ -779,7 +798,9 @@ static void push_all(or_sim* s, long long step) {
     uint32_t id = s->id[k];
     double Ep[3], Bp[3];
     gather(s, i, j, fx, fy, Ep, Bp);
+    const double vo[3] = {v[0], v[1], v[2]};
     boris(v, Ep, Bp, s->hdt, s->c2inv);
+    s->push_work += push_work_of(s, weight_of(s, id), Ep, vo, v);
     /* the move uses the velocity (v = u / gamma for relativistic ions) */
     double ig = inv_gamma_u(s, v[0], v[1], v[2]);
     double vxm = (s->c2inv > 0.0) ? v[0] * ig : v[0];
@@ -1075,6 +1096,7 @@ int or_diag(const or_sim* s, or_diag_t* o) {
   o->fs_energy = s->fs_energy;
   o->injected_energy = s->injected_energy;
   o->removed_energy = s->removed_energy;
+  o->push_work = s->push_work;
   double ke = 0.0, px = 0.0, py = 0.0, pz = 0.0, ub = 0.0;
   for (long long k = 0; k < s->np; ++k) {
     double wp = weight_of(s, s->id[k]);

@@ -60,6 +60,9 @@ typedef struct {
   double kinetic, magnetic, px, py, pz;
   double fs_energy;           /* cumulative sum of w * dE at reflections */
   double injected_energy, removed_energy;
+  double push_work;           /* cumulative work of E on the ions in the Boris
+                                 pushes: with the three energies above it
+                                 closes the kinetic-energy budget */
 } or_diag_t;
 
 typedef struct or_sim or_sim;

@@ -63,6 +63,7 @@ class OrDiag(C.Structure):
         ("px", C.c_double), ("py", C.c_double), ("pz", C.c_double),
         ("fs_energy", C.c_double),
         ("injected_energy", C.c_double), ("removed_energy", C.c_double),
+        ("push_work", C.c_double),
     ]
 
 

@@ -862,7 +862,8 @@ int fs_diag(fs_handle* h, fs_diag_t* out) {
   out->removed_energy = c.removed_energy;
   out->status = c.status;
   out->launches = s->launches;
-  return FS_OK;
+  out->max_z = c.sums[5];
+  return out->max_z > FS_RK4_Z_MAX ? FS_EUNSTABLE : FS_OK;
 }
 
 int fs_profile(fs_handle* h, int enable) {

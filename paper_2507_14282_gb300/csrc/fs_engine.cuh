@@ -950,6 +950,31 @@ __global__ void k_diag_field(DevPtrs<T> d, Geo g, Phys ph) {
   }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) atomicAdd(&d.ctr->sums[4], s);
+  // Stability number of the field integrator, z = h omega_max with h the
+  // RK4 substep: the fastest discrete mode is bounded by the grid-scale
+  // whistler, k^2 |Bbar| / n with k^2 <= 4/dx^2 + 4/dy^2 for the staggered
+  // differences, plus advection, k |u| with k <= 2/dx + 2/dy. Kept as the
+  // maximum over nodes in sums[5] (non-negative doubles order like their
+  // bit patterns).
+  const double kk = 16.0 * (ph.hdx * ph.hdx + ph.hdy * ph.hdy);
+  const double ka = 4.0 * (ph.hdx + ph.hdy);
+  const int nn = g.nxn * g.ny;
+  double zmax = 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nn;
+       c += gridDim.x * blockDim.x) {
+    const double bx = d.Bb[c], by = d.Bb[nn + c], bz = d.Bb[2 * nn + c];
+    const double ux = d.u[c], uy = d.u[nn + c], uz = d.u[2 * nn + c];
+    const double b = sqrt(bx * bx + by * by + bz * bz);
+    const double um = sqrt(ux * ux + uy * uy + uz * uz);
+    const double z = ph.h * (kk * b / (double)d.n[c] + ka * um);
+    zmax = z > zmax ? z : zmax;  // a NaN z leaves zmax; NaN is caught elsewhere
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, zmax, o);
+    zmax = w > zmax ? w : zmax;
+  }
+  if ((threadIdx.x & 31) == 0 && zmax > 0.0)
+    atomicMax((unsigned long long*)&d.ctr->sums[5], (unsigned long long)__double_as_longlong(zmax));
 }
 
 template <typename T, int DIM>

@@ -24,6 +24,8 @@ FS_PROFILE_N, FS_PROFILE_DB2, FS_HIST_XPX, FS_HIST_XPX_CR = 6, 7, 8, 9
 FS_PROFILE_B, FS_SPECTRUM_BPERP = 10, 11
 FS_SPECTRUM_P_CR, FS_SPECTRUM_P_ALL = 12, 13
 ID_MASK, ID_CR, ID_RETURNED = 0x3FFFFFFF, 0x40000000, 0x80000000
+FS_EUNSTABLE = -7
+FS_RK4_Z_MAX = 2.8284271247461903  # 2 sqrt 2: RK4 on the imaginary axis
 
 
 class FsParams(C.Structure):
@@ -72,6 +74,7 @@ class FsDiag(C.Structure):
         ("fs_energy", C.c_double),
         ("injected_energy", C.c_double), ("removed_energy", C.c_double),
         ("status", C.c_int), ("launches", C.c_longlong),
+        ("max_z", C.c_double),
     ]
 
 
@@ -222,9 +225,15 @@ class FauxShock:
         return n.value
 
     def diag(self) -> dict:
+        """fs_diag as a dict; 'unstable' is True when the field integrator's
+        stability number max_z exceeds the RK4 bound (FS_EUNSTABLE)."""
         d = FsDiag()
-        _check(lib().fs_diag(self._h, C.byref(d)), "fs_diag")
-        return {name: getattr(d, name) for name, _ in FsDiag._fields_}
+        rc = lib().fs_diag(self._h, C.byref(d))
+        if rc != FS_EUNSTABLE:
+            _check(rc, "fs_diag")
+        out = {name: getattr(d, name) for name, _ in FsDiag._fields_}
+        out["unstable"] = rc == FS_EUNSTABLE
+        return out
 
     def grid(self, what: int) -> np.ndarray:
         nx, ny, nxn = self.nx, self.ny, self.nxn

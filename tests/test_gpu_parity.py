@@ -345,3 +345,22 @@ def test_fp32_fields_within_tolerance(fs, dim):
     assert d["injected"] == dr["injected"]
     sd = 4 * np.sqrt(max(dr["reflected"], 1)) + 2
     assert abs(d["reflected"] - dr["reflected"]) <= sd
+
+
+def test_field_stability_number_and_unstable_report(fs):
+    # z = h [(4/dx^2 (+4/dy^2)) |Bbar| / n + (2/dx (+2/dy)) |u|], maximum over
+    # nodes, from the run's own node fields; FS_EUNSTABLE above 2 sqrt 2
+    for dim, dx, dt, unstable in ((1, 0.5, 0.005, False), (2, 0.5, 0.0025, False),
+                                  (1, 0.05, 0.02, True)):
+        p = W.scaled(W.CONFIG_1D if dim == 1 else W.CONFIG_2D, nx=64,
+                     ny=1 if dim == 1 else 16, dx=dx, dy=dx, dt=dt, ppc=8)
+        sim = fs.FauxShock(precision=fs.FS_FP64, **p)
+        d = sim.diag()
+        bb, n, u = sim.grid(fs.FS_BBAR), sim.grid(fs.FS_N), sim.grid(fs.FS_U)
+        kk = 4 / dx**2 * (2 if dim == 2 else 1)
+        ka = 2 / dx * (2 if dim == 2 else 1)
+        z = dt / 2 * (kk * np.linalg.norm(bb, axis=-1) / n + ka * np.linalg.norm(u, axis=-1))
+        assert d["max_z"] == pytest.approx(z.max(), rel=1e-12)
+        assert d["unstable"] == unstable
+        assert (d["max_z"] > fs.FS_RK4_Z_MAX) == unstable
+        sim.close()
