@@ -290,6 +290,10 @@ def ours(args):
     if not args.skip_ensemble:
         ens = ensemble(fs, torch, args, hbm, peak_src)
 
+    win = None
+    if not args.skip_window:
+        win = window(torch, args)
+
     e2e = end_to_end(fs, torch, device, args, dist, world)
 
     cpu = None
@@ -310,6 +314,7 @@ def ours(args):
             "roofline": roofline,
             "fp32": fp32,
             "ensemble": ens,
+            "window": win,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": gpu_launches,
@@ -374,6 +379,49 @@ def ensemble(fs, torch, args, hbm, peak_src):
                               "peak_source": peak_src},
             "tiles": {k: v for k, v in sorted(tuner.cache.items())},
             "tune_s": tune_s, "status_ok": all(x == 0 for x in status)}
+
+
+WINDOW_NAME = ("differentiable window, 1D faux-shock box: 2048 cells, 128 ppc (262k ions), "
+               "M_A=20, theta_Bn=0, beta=1, CR source p_iso=100 n_cr=0.01, 200 steps "
+               "checkpointed every 20, loss = upstream |dB_perp|^2 dx, gradient w.r.t. 16 "
+               "mode amplitudes, u_cr and u2; seed 4")
+
+
+def window(torch, args):
+    """The differentiable window (FP32 and FP64): forward, and forward +
+    backward (each segment recomputed from its checkpoint, then the adjoint
+    sweep), timed on the host around the synchronising calls."""
+    import numpy as np
+    from paper_2507_14282_gb300 import window as W
+    from tests import window_inputs as WI
+    X, V = WI.plasma(2048, 128)
+    amps, ph = WI.modes()
+    th = WI.theta(amps)
+    out = {"workload": WINDOW_NAME, "unit": UNIT}
+    for name, prec in (("fp32", 1), ("fp64", 0)):
+        w = W.FauxShockWindow(X, V, ph, steps=200, ckpt=20, nx=2048, ny=1, ppc=128,
+                              precision=prec, cr_enable=1, fs_mode_thermal=1, p_iso=100.0,
+                              n_cr_ratio=0.01, **WI.COMMON)
+        w.loss_and_grad(th)  # warm-up
+        K = 3
+        t0 = time.perf_counter()
+        for _ in range(K):
+            w.forward(th)
+        tf = (time.perf_counter() - t0) / K
+        t0 = time.perf_counter()
+        for _ in range(K):
+            L, g = w.loss_and_grad(th)
+        tfb = (time.perf_counter() - t0) / K
+        c = w.counts()
+        n = 2048 * 128 + c["injected"] / 2  # mean slots over the window
+        out[name] = {"forward_value": n * 200 / tf, "forward_backward_value": n * 200 / tfb,
+                     "forward_ms": tf * 1e3, "forward_backward_ms": tfb * 1e3,
+                     "loss": L, "grad_norm_modes": float(np.linalg.norm(g[:16])),
+                     "grad_u_cr": float(g[16]), "grad_u2": float(g[17]),
+                     "device_bytes": w.bytes, "counts": c}
+        w.close()
+        torch.cuda.empty_cache()
+    return out
 
 
 def end_to_end(fs, torch, device, args, dist, world):
@@ -514,6 +562,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ens-steps", type=int, default=50)
     ap.add_argument("--skip-ensemble", action="store_true")
+    ap.add_argument("--skip-window", action="store_true")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args)

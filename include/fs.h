@@ -331,6 +331,55 @@ int fs_destroy(fs_handle* h);
 /* Name of a status code. */
 const char* fs_strerror(int status);
 
+/* ------------------------------------------------------------------------
+   Differentiable window (1D faux-shock box): the gradient of a loss at the
+   end of `steps` hybrid steps with respect to
+     theta = (a_1 .. a_M, u_cr, u2),
+   the amplitudes of M seeded transverse-B modes
+     B_y = B0_y + sum_m a_m cos(2 pi m x / L + phi_m),
+     B_z = B0_z + sum_m a_m sin(2 pi m x / L + phi_m)   (x at cell centres),
+   the drift speed u_cr of the cosmic-ray source at the faux shock (Sec. 2;
+   its ions start with speed p_iso, flux-weighted in the frame drifting at
+   u_cr) and the faux shock's downstream speed u2 (the kick of the return,
+   Eq. 1). The loss is the upstream magnetic fluctuation energy at the
+   window's end, sum over cells i >= loss_i0 of |B_perp - B0_perp|^2 dx.
+   The step is fs_step's scheme (CIC gather, Boris push, faux-shock return,
+   inflow at x = L, CR source, CIC deposit, RK4 Ohm + Faraday with the
+   moments frozen), on particles kept in fixed slots. The backward is the
+   discrete adjoint along the forward's branches: crossings, returns,
+   escapes, the density floor and every random draw are frozen. Checkpoints
+   every ckpt_every steps; each segment is recomputed once in the backward
+   (deterministic int64 fixed-point deposit sums, so a recomputed segment
+   repeats the forward exactly).
+   Parameters come from fs_params with dim = 1, the faux-shock box and no
+   relativistic ions (c_light = 0); precision FS_FP32 or FS_FP64; p->u2 and
+   p->u_cr are ignored (theta holds them).
+
+   fs_window_query: device bytes for the window (no allocation).
+   fs_window_init: x_init[n_init] positions in cells (X = i + f, 0 <= X <
+   nx), v_init[n_init][3] velocities (v_A), host arrays copied before return;
+   mode_phase[n_modes] the phases phi_m; dev_buf (256-byte aligned, >= the
+   queried bytes, owned by the caller, outliving the handle). The initial
+   ions get ids 0 .. n_init - 1; injected ions continue from n_init.
+   fs_window_forward: runs the window for theta[n_modes + 2] and writes the
+   loss; synchronises. FS_EINVAL for u2 <= 0 or u_cr outside [0, p_iso).
+   fs_window_backward: d loss / d theta (times dloss) into grad[n_modes + 2];
+   needs a forward just before it (the backward reuses and overwrites the
+   forward's state; FS_EINVAL otherwise); synchronises.
+   fs_window_counts: incident, returned, transmitted, escaped, injected of
+   the last forward. */
+typedef struct fs_window fs_window;
+int fs_window_query(const fs_params* p, int steps, int ckpt_every, long long n_init,
+                    int n_modes, size_t* bytes);
+int fs_window_init(const fs_params* p, int steps, int ckpt_every, long long n_init,
+                   const double* x_init, const double* v_init, int n_modes,
+                   const double* mode_phase, int loss_i0, void* dev_buf, size_t bytes,
+                   void* cuda_stream, fs_window** out);
+int fs_window_forward(fs_window* w, const double* theta, double* loss);
+int fs_window_backward(fs_window* w, double dloss, double* grad);
+int fs_window_counts(fs_window* w, long long* out5);
+int fs_window_destroy(fs_window* w);
+
 #ifdef __cplusplus
 }
 #endif

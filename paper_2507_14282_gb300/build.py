@@ -24,6 +24,7 @@ UNITS = {
     "fs_api.cu": [],
     "fs_f32.cu": [],
     "fs_f64.cu": ["-fmad=false"],
+    "fs_window.cu": [],
 }
 
 

@@ -117,6 +117,14 @@ def lib():
         L.fs_batch_init.argtypes = [V, C.c_int, V, C.c_size_t, P(V)]
         L.fs_batch_step.argtypes = [V, C.c_int]
         L.fs_batch_destroy.argtypes = [V]
+        L.fs_window_query.argtypes = [P(FsParams), C.c_int, C.c_int, C.c_longlong, C.c_int,
+                                      P(C.c_size_t)]
+        L.fs_window_init.argtypes = [P(FsParams), C.c_int, C.c_int, C.c_longlong, V, V,
+                                     C.c_int, V, C.c_int, V, C.c_size_t, V, P(V)]
+        L.fs_window_forward.argtypes = [V, V, P(C.c_double)]
+        L.fs_window_backward.argtypes = [V, C.c_double, V]
+        L.fs_window_counts.argtypes = [V, V]
+        L.fs_window_destroy.argtypes = [V]
         _lib = L
     return _lib
 

@@ -75,3 +75,26 @@ def test_oracle_is_not_imported_by_the_package():
     code = ("import sys, paper_2507_14282_gb300; "
             "assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)")
     subprocess.run([sys.executable, "-c", code], check=True, cwd=ROOT)
+
+
+def test_window_query_sizes_and_rejections(fs):
+    import ctypes as C
+    L = fs.lib()
+
+    def q(steps=200, ckpt=20, n=262144, modes=16, **kw):
+        kw.setdefault("dim", 1)
+        kw.setdefault("ny", 1)
+        p = fs.make_params(nx=2048, ppc=128, dt=0.0025, mach_a=20.0, cr_enable=1, **kw)
+        b = C.c_size_t()
+        rc = L.fs_window_query(C.byref(p), steps, ckpt, n, modes, C.byref(b))
+        return rc, b.value
+
+    rc, b32 = q(precision=fs.FS_FP32)
+    assert rc == 0 and b32 > 262144 * 16 * 11  # state, ten checkpoints, the tape
+    rc, b64 = q(precision=fs.FS_FP64)
+    assert rc == 0 and b64 > b32
+    assert q(precision=fs.FS_FP32, steps=400)[1] > b32  # more checkpoints
+    assert q(dim=2, ny=16)[0] == -1          # 1D only
+    assert q(c_light=50.0)[0] == -1          # no relativistic ions
+    assert q(bc_x=fs.FS_BC_PERIODIC)[0] == -1
+    assert q(steps=0)[0] == -1 and q(ckpt=0)[0] == -1 and q(n=-1)[0] == -1

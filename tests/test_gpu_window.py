@@ -1,0 +1,150 @@
+"""Differentiable window on the GPU: the CUDA forward and adjoint through the
+C ABI (fs_window_*), against the FP64 PyTorch oracle (autograd) on a 64-cell,
+8-ppc copy, and against central finite differences of the CUDA forward on
+the full differentiable-window workload (2048 cells, 128 ppc, 200 steps
+checkpointed every 20).
+"""
+import numpy as np
+import pytest
+
+from tests import window_inputs as WI
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsw():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_14282_gb300 import build
+    build.build()
+    from paper_2507_14282_gb300 import window as m
+    return m
+
+
+def gpu_window(fsw, nx, ppc, steps, ckpt, precision=0, loss_i0=0):
+    X, V = WI.plasma(nx, ppc)
+    amps, ph = WI.modes()
+    w = fsw.FauxShockWindow(X, V, ph, steps=steps, ckpt=ckpt, loss_i0=loss_i0, nx=nx, ny=1,
+                            ppc=ppc, precision=precision, cr_enable=1, fs_mode_thermal=1,
+                            p_iso=100.0, n_cr_ratio=0.01, **WI.COMMON)
+    return w, WI.theta(amps)
+
+
+@pytest.fixture(scope="module")
+def oracle_small():
+    from oracle import window as wo
+    X, V = WI.plasma(64, 8)
+    amps, ph = WI.modes()
+    spec = wo.WindowSpec(nx=64, ppc=8, X0=X, V0=V, phases=ph, **WI.COMMON)
+    L, g, win = wo.loss_and_grad(spec, WI.theta(amps), 200)
+    return L, g, win.counts
+
+
+def test_fp64_forward_and_gradient_match_the_oracle_adjoint(fsw, oracle_small):
+    L0, g0, counts0 = oracle_small
+    w, th = gpu_window(fsw, 64, 8, 200, 20)
+    L, g = w.loss_and_grad(th)
+    c = w.counts()
+    for k in ("incident", "reflected", "transmitted", "escaped", "injected"):
+        assert c[k] == counts0[k], (k, c[k], counts0[k])
+    assert c["reflected"] > 0 and c["injected"] > 0
+    # every kind of parameter has a gradient well above round-off
+    assert np.abs(g0[:16]).min() > 1e-3 and abs(g0[16]) > 1e-5 and abs(g0[17]) > 1e-3
+    assert L == pytest.approx(L0, rel=1e-9)
+    # modes (scale: their largest gradient), then u_cr and u2 each on its own
+    gm = np.abs(g0[:16]).max()
+    np.testing.assert_allclose(g[:16], g0[:16], rtol=0, atol=1e-6 * gm)
+    assert g[16] == pytest.approx(g0[16], rel=1e-5)
+    assert g[17] == pytest.approx(g0[17], rel=1e-6)
+    w.close()
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(fsw):
+    w1, th = gpu_window(fsw, 64, 8, 60, 20)
+    w2, _ = gpu_window(fsw, 64, 8, 60, 60)
+    w3, _ = gpu_window(fsw, 64, 8, 60, 7)
+    L1, g1 = w1.loss_and_grad(th)
+    L2, g2 = w2.loss_and_grad(th)
+    L3, g3 = w3.loss_and_grad(th)
+    assert L1 == L2 == L3
+    np.testing.assert_allclose(g2, g1, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(g3, g1, rtol=1e-12, atol=1e-15)
+    # a second forward gives the same loss (the window keeps its inputs)
+    assert w1.forward(th) == L1
+
+
+def test_autograd_function_runs_the_cuda_adjoint(fsw):
+    import torch
+    w, th = gpu_window(fsw, 64, 8, 40, 20)
+    t = torch.tensor(th, dtype=torch.float64, requires_grad=True)
+    loss = fsw.window_loss(w, t)
+    (3.0 * loss).backward()
+    L, g = w.loss_and_grad(th)
+    assert float(loss.detach()) == L
+    np.testing.assert_allclose(t.grad.numpy(), 3.0 * g, rtol=1e-12, atol=1e-18)
+
+
+@pytest.fixture(scope="module")
+def full_fp64(fsw):
+    w, th = gpu_window(fsw, 2048, 128, 200, 20)
+    L, g = w.loss_and_grad(th)
+    return w, th, L, g
+
+
+@pytest.fixture(scope="module")
+def full_fp64_100(fsw):
+    w, th = gpu_window(fsw, 2048, 128, 100, 20)
+    L, g = w.loss_and_grad(th)
+    return w, th, L, g
+
+
+def central_difference(w, th, k, L, rel_h):
+    h = rel_h * max(abs(th[k]), 1e-2)
+    tp, tm = th.copy(), th.copy()
+    tp[k] += h
+    tm[k] -= h
+    fd = (w.forward(tp) - w.forward(tm)) / (2 * h)
+    # far above what FP64 rounding of the loss can give over 2 h
+    assert abs(fd) > 1e-12 * abs(L) / h
+    return fd
+
+
+# The loss is piecewise differentiable: CIC weights have kinks where a
+# particle crosses a cell face, and a returned ion's re-placement and path
+# move with u2 and u_cr. A difference interval must be narrower than the
+# spacing of the kinks it crosses and wider than rounding: for the kick u2
+# that is h = 1e-6 u2 (1e-5 already straddles kinks and moves the quotient
+# by 0.4 %, 1e-8 is rounding-limited); the modes take h = 1e-5 |a_m|.
+@pytest.mark.parametrize("k,rel_h", [(0, 1e-5), (7, 1e-5), (15, 1e-5), (17, 1e-6)])
+def test_full_window_gradient_matches_central_differences(full_fp64, k, rel_h):
+    w, th, L, g = full_fp64
+    fd = central_difference(w, th, k, L, rel_h)
+    atol = 1e-6 * np.abs(g[:16]).max() if k < 16 else 0.0
+    assert g[k] == pytest.approx(fd, rel=1e-3, abs=atol), (k, g[k], fd)
+
+
+def test_cosmic_ray_drift_gradient_matches_central_differences(full_fp64_100, full_fp64):
+    # d L / d u_cr is 1e7 times smaller than the mode gradients; over 100
+    # steps the difference quotient converges and agrees with the adjoint to
+    # 1e-3. Over 200 steps the kinks of thousands of cosmic-ray crossings make
+    # the quotient wander by about 1 % across a decade of h around the
+    # adjoint's value.
+    w, th, L, g = full_fp64_100
+    fd = central_difference(w, th, 16, L, 1e-6)
+    assert g[16] == pytest.approx(fd, rel=1e-3), (g[16], fd)
+    w, th, L, g = full_fp64
+    fd = central_difference(w, th, 16, L, 1e-6)
+    assert g[16] == pytest.approx(fd, rel=2e-2), (g[16], fd)
+
+
+def test_fp32_window_gradient_tracks_fp64(fsw, full_fp64):
+    _, th, L64, g64 = full_fp64
+    w, _ = gpu_window(fsw, 2048, 128, 200, 20, precision=1)
+    L32, g32 = w.loss_and_grad(th)
+    assert L32 == pytest.approx(L64, rel=1e-3)
+    gm = np.abs(g64[:16]).max()
+    assert np.abs(g32[:16] - g64[:16]).max() <= 2e-2 * gm
+    assert g32[17] == pytest.approx(g64[17], rel=5e-2)
+    w.close()
