@@ -282,6 +282,40 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
       Ep[q] = fmaT(fx, b[q], g0 * a[q]);
       Bp[q] = fmaT(fx, b[3 + q], g0 * a[3 + q]);
     }
+  } else if constexpr (sizeof(T) == 4) {
+    // FP32: the same products and fused multiply-adds, two components per
+    // paired instruction (Ex Ey | Ez Bx | By Bz, the node's 16-byte halves)
+    const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
+    const T w00 = gx0 * gy0, w10 = fx * gy0, w01 = gx0 * fy, w11 = fx * fy;
+    const float* n00 = reinterpret_cast<const float*>(F) + (ly * NFX + lx) * 8;
+    const float4 a0 = reinterpret_cast<const float4*>(n00)[0];
+    const float2 b0 = reinterpret_cast<const float2*>(n00)[2];
+    const float4 a1 = reinterpret_cast<const float4*>(n00 + 8)[0];
+    const float2 b1 = reinterpret_cast<const float2*>(n00 + 8)[2];
+    const float4 a2 = reinterpret_cast<const float4*>(n00 + NFX * 8)[0];
+    const float2 b2 = reinterpret_cast<const float2*>(n00 + NFX * 8)[2];
+    const float4 a3 = reinterpret_cast<const float4*>(n00 + NFX * 8 + 8)[0];
+    const float2 b3 = reinterpret_cast<const float2*>(n00 + NFX * 8 + 8)[2];
+    const float2 W00 = make_float2(w00, w00), W10 = make_float2(w10, w10);
+    const float2 W01 = make_float2(w01, w01), W11 = make_float2(w11, w11);
+    float2 p0 = __fmul2_rn(W00, make_float2(a0.x, a0.y));
+    float2 p1 = __fmul2_rn(W00, make_float2(a0.z, a0.w));
+    float2 p2 = __fmul2_rn(W00, b0);
+    p0 = __ffma2_rn(W10, make_float2(a1.x, a1.y), p0);
+    p1 = __ffma2_rn(W10, make_float2(a1.z, a1.w), p1);
+    p2 = __ffma2_rn(W10, b1, p2);
+    p0 = __ffma2_rn(W01, make_float2(a2.x, a2.y), p0);
+    p1 = __ffma2_rn(W01, make_float2(a2.z, a2.w), p1);
+    p2 = __ffma2_rn(W01, b2, p2);
+    p0 = __ffma2_rn(W11, make_float2(a3.x, a3.y), p0);
+    p1 = __ffma2_rn(W11, make_float2(a3.z, a3.w), p1);
+    p2 = __ffma2_rn(W11, b3, p2);
+    Ep[0] = p0.x;
+    Ep[1] = p0.y;
+    Ep[2] = p1.x;
+    Bp[0] = p1.y;
+    Bp[1] = p2.x;
+    Bp[2] = p2.y;
   } else {
     const T gx0 = (T)1 - fx, gy0 = (T)1 - fy;
     const T w00 = gx0 * gy0, w10 = fx * gy0, w01 = gx0 * fy, w11 = fx * fy;

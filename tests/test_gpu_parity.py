@@ -364,3 +364,60 @@ def test_field_stability_number_and_unstable_report(fs):
         assert d["unstable"] == unstable
         assert (d["max_z"] > fs.FS_RK4_Z_MAX) == unstable
         sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_tile_buckets_stay_cell_sorted(fs, prec):
+    # Each tile's bucket (exported contiguously, in bucket order) is sorted by
+    # cell up to a tail of particles appended since the push: those moved in
+    # from other tiles and the injected ones (a few per cent per step).
+    p = W.scaled(W.CONFIG_2D_FP32, nx=256, ny=64, seed=5)
+    sim = fs.FauxShock(precision=fs.FS_FP64 if prec == "fp64" else fs.FS_FP32, **p)
+    tx, ty = sim.sizes.tile_x, sim.sizes.tile_y
+    for steps in (1, 4):
+        sim.step(steps)
+        q = sim.particles()
+        i, j = q["ci"], q["cj"]
+        tile = (j // ty) * (p["nx"] // tx) + i // tx
+        local = (j % ty) * tx + i % tx
+        sorted_n, k, n = 0, 0, len(tile)
+        while k < n:
+            e = k + 1
+            while e < n and tile[e] == tile[k]:
+                e += 1
+            run = local[k:e]
+            desc = np.nonzero(np.diff(run) < 0)[0]
+            sorted_n += (desc[0] + 1) if desc.size else (e - k)
+            k = e
+        assert sorted_n >= 0.9 * n, (steps, sorted_n / n)
+    assert sim.diag()["status"] == 0
+    sim.close()
+
+
+@pytest.mark.parametrize("mode", ["shock", "open+cr"])
+def test_fp32_2d_precision_form_tiles_within_tolerance(fs, mode):
+    # the precision form's shape: 64 ppc in 4 x 2-cell tiles (512 particles,
+    # the tile push's FP32 chunk), returning or open faux shock
+    cfg = W.scaled(W.CONFIG_2D_FP32, nx=64, ny=16)
+    if mode == "open+cr":
+        cfg.update(fs_mode_thermal=O.FS_OPEN, cr_enable=1)
+    gpu = fs.FauxShock(precision=fs.FS_FP32, **cfg)
+    assert (gpu.sizes.tile_x, gpu.sizes.tile_y) == (4, 2)
+    ref = O.Oracle(**cfg)
+    gpu.step(1)
+    ref.step(1)
+    for gw, ow in GRIDS:
+        assert rel_l2(gpu.grid(gw), ref.grid(ow)) <= 1e-5, (gw, mode)
+    gpu.step(99)
+    ref.step(99)
+    errs = {gw: rel_l2(gpu.grid(gw), ref.grid(ow)) for gw, ow in GRIDS}
+    assert max(errs.values()) <= 1e-3, errs
+    d, dr = gpu.diag(), ref.diag()
+    assert d["status"] == 0
+    assert d["injected"] == dr["injected"]
+    assert d["incident"] == d["transmitted"] + d["reflected"]
+    n0 = cfg["nx"] * cfg["ny"] * cfg["ppc"]
+    assert d["n_particles"] == n0 + d["injected"] - d["transmitted"] - d["escaped"]
+    sd = 4 * np.sqrt(max(dr["reflected"], 1)) + 2
+    assert abs(d["reflected"] - dr["reflected"]) <= sd
+    gpu.close()
