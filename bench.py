@@ -158,13 +158,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(n_gpus: int):
+def dist_setup(n_gpus: int, backend: str = "nccl"):
     if n_gpus <= 1 or "RANK" not in os.environ:
         return 0, 1, 0, None
     import torch.distributed as dist
-    dist.init_process_group("nccl")
+    dist.init_process_group(backend)
     return (dist.get_rank(), dist.get_world_size(), int(os.environ.get("LOCAL_RANK", 0)),
             dist)
+
+
+def replica_value(n_mean: float, steps: int, ms_local: float, dist, device="cpu"):
+    """Whole-job throughput of independent replicas (one box per rank): the
+    particles every rank pushed per step, summed, times the steps, over the
+    slowest rank's time. Returns (value, ms of the slowest rank)."""
+    import torch
+    if not dist:
+        return n_mean * steps / (ms_local * 1e-3), ms_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    n = torch.tensor([n_mean], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(n.item()) * steps / (float(t.item()) * 1e-3), float(t.item())
 
 
 def timed_run(fs, torch, params: dict, prec, steps: int, warmup: int, dist, device,
@@ -226,12 +240,7 @@ def ours(args):
 
     res64 = timed_run(fs, torch, FP64_WORKLOAD, fs.FS_FP64, args.steps, args.warmup, dist,
                       device, True, local_rank)
-    t64 = res64["ms_total"]
-    if dist:
-        tt = torch.tensor([t64], device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t64 = float(tt.item())
-    value = res64["n_mean"] * args.steps * world / (t64 * 1e-3)
+    value, t64 = replica_value(res64["n_mean"], args.steps, res64["ms_total"], dist, device)
     ms_step = t64 / args.steps
     pb64 = particle_bytes(8, 2)
     grid_b64 = GRID_WORDS_PER_CELL * 8 / FP64_WORKLOAD["ppc"]
@@ -259,13 +268,8 @@ def ours(args):
     if not args.skip_fp32:
         res32 = timed_run(fs, torch, FP32_WORKLOAD, fs.FS_FP32, args.steps32, args.warmup,
                           dist, device, False, local_rank)
-        t32 = res32["ms_total"]
-        if dist:
-            tt = torch.tensor([t32], device=device)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t32 = float(tt.item())
+        v32, t32 = replica_value(res32["n_mean"], args.steps32, res32["ms_total"], dist, device)
         ms32 = t32 / args.steps32
-        v32 = res32["n_mean"] * args.steps32 * world / (t32 * 1e-3)
         pb32 = particle_bytes(4, 2)
         gb32 = GRID_WORDS_PER_CELL * 4 / FP32_WORKLOAD["ppc"]
         kern32 = res32["phases"]["push"]
