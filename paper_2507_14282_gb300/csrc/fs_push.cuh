@@ -250,6 +250,19 @@ __device__ __forceinline__ void ld2(const double* p, double (&v)[2]) {
   v[0] = a.x; v[1] = a.y;
 }
 
+// Ordered integer key of a double: monotone in its value, with -0 and +0
+// equal and a NaN beyond every finite key, so that x >= c (c finite) is the
+// same test as ordered_key(x) >= ordered_key(c).
+__device__ __forceinline__ long long ordered_key(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long m = b & 0x7FFFFFFFFFFFFFFFLL;
+  return b < 0 ? -m : m;
+}
+constexpr long long kKeyOne = 0x3FF0000000000000LL;  // ordered_key(1.0)
+constexpr long long kKeyTwo = 0x4000000000000000LL;  // ordered_key(2.0)
+__device__ __forceinline__ bool ge_one(double x) { return ordered_key(x) >= kKeyOne; }
+__device__ __forceinline__ bool ge_one(float x) { return x >= 1.0f; }
+
 // Faux-shock and open-wall bookkeeping of one CTA (rare events): shared
 // memory, added to the global counters once at the end.
 struct PushTally {
@@ -362,18 +375,39 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
   if (DIM == 2) fyr = fmaT(mvy, dtdy, fy);
   // Common case: a tile away from every box edge and a shift of at most one
   // cell: no wall, wrap or far-mover handling can apply. Same values as the
-  // general path below (shift in {-1, 0, 1}, subtracted exactly).
-  if (inner && fxr >= (T)-1 && fxr < (T)2 && (DIM == 1 || (fyr >= (T)-1 && fyr < (T)2))) {
-    const bool xp = fxr >= (T)1, xm = fxr < (T)0;
+  // general path below (shift in {-1, 0, 1}, subtracted exactly). The
+  // comparisons with -1, 0, 1 and 2 are exact either way; in FP64 they run
+  // on the ordered integer key of the value, off GB300's narrow FP64 pipe.
+  bool inr, xp, xm, yp = false, ym = false;
+  if constexpr (sizeof(T) == 8) {
+    const long long kx = ordered_key(fxr);
+    inr = kx >= -kKeyOne && kx < kKeyTwo;
+    xp = kx >= kKeyOne;
+    xm = kx < 0;
+    if (DIM == 2) {
+      const long long ky = ordered_key(fyr);
+      inr = inr && ky >= -kKeyOne && ky < kKeyTwo;
+      yp = ky >= kKeyOne;
+      ym = ky < 0;
+    }
+  } else {
+    inr = fxr >= (T)-1 && fxr < (T)2 && (DIM == 1 || (fyr >= (T)-1 && fyr < (T)2));
+    xp = fxr >= (T)1;
+    xm = fxr < (T)0;
+    if (DIM == 2) {
+      yp = fyr >= (T)1;
+      ym = fyr < (T)0;
+    }
+  }
+  if (inner && inr) {
     const int ikx = xp ? 1 : (xm ? -1 : 0);
     T fxn = fxr - (xp ? (T)1 : (xm ? (T)-1 : (T)0));
-    if (fxn >= (T)1) fxn = Num<T>::offmax;
+    if (ge_one(fxn)) fxn = Num<T>::offmax;
     int iky = 0;
     if (DIM == 2) {
-      const bool yp = fyr >= (T)1, ym = fyr < (T)0;
       iky = yp ? 1 : (ym ? -1 : 0);
       T fyn = fyr - (yp ? (T)1 : (ym ? (T)-1 : (T)0));
-      if (fyn >= (T)1) fyn = Num<T>::offmax;
+      if (ge_one(fyn)) fyn = Num<T>::offmax;
       fy = fyn;
     }
     cell = ((j + iky) << 16) | (i + ikx);
