@@ -663,18 +663,63 @@ __global__ void k_ohm_pre(const T* __restrict__ nN, T* __restrict__ pre, Geo g, 
   }
 }
 
+// The node value of Ohm's law from curl B (cxv, cyv, czv), Bbar, 1/n, the
+// pressure terms and u.
+template <typename T>
+__device__ __forceinline__ void ohm_e(T cxv, T cyv, T czv, T bbx, T bby, T bbz, T inv_n, T pgx,
+                                      T pgy, T ux, T uy, T uz, T jcr, T eta, bool resist,
+                                      T& ex, T& ey, T& ez) {
+  const T ax = cxv - jcr, ay = cyv, az = czv;
+  const T cax = fmaT(ay, bbz, -(az * bby));
+  const T cay = fmaT(az, bbx, -(ax * bbz));
+  const T caz = fmaT(ax, bby, -(ay * bbx));
+  const T cux = fmaT(uy, bbz, -(uz * bby));
+  const T cuy = fmaT(uz, bbx, -(ux * bbz));
+  const T cuz = fmaT(ux, bby, -(uy * bbx));
+  ex = fmaT(pgx, inv_n, fmaT(cax, inv_n, -cux));
+  ey = fmaT(pgy, inv_n, fmaT(cay, inv_n, -cuy));
+  ez = fmaT(caz, inv_n, -cuz);
+  if (resist) {
+    ex = ex + eta * cxv;
+    ey = ey + eta * cyv;
+    ez = ez + eta * czv;
+  }
+}
+
+// The RK4 stage update of one B component from K = -curl E:
+//   stage 1: Bsum = K;            Bs = B + (h/2) K
+//   stage 2: Bsum = Bsum + 2 K;   Bs = B + (h/2) K
+//   stage 3: Bsum = Bsum + 2 K;   Bs = B + h K
+//   stage 4: Bsum = Bsum + K;     B  = B + (h/6) Bsum
+template <typename T>
+__device__ __forceinline__ void rk4_stage(int stage, T K, T& bsum, T& bs, T& b, T h, T hh,
+                                          T h6) {
+  if (stage == 1) {
+    bsum = K;
+    bs = fmaT(hh, K, b);
+  } else if (stage == 2) {
+    bsum = fmaT((T)2, K, bsum);
+    bs = fmaT(hh, K, b);
+  } else if (stage == 3) {
+    bsum = fmaT((T)2, K, bsum);
+    bs = fmaT(h, K, b);
+  } else {
+    const T sum = bsum + K;
+    b = fmaT(h6, sum, b);
+  }
+}
+
+// Ohm's law at node q = j * nxn + i (the body of k_ohm).
 template <typename T, int DIM>
-__global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
-                      const T* __restrict__ uN, const T* __restrict__ pre,
-                      T* __restrict__ Eo, T* __restrict__ Bbo, T* __restrict__ G, Geo g,
-                      Phys ph) {
+__device__ __forceinline__ void ohm_node(int q, const T* Bc, const T* nN, const T* uN,
+                                         const T* pre, T* Eo, T* Bbo, T* G, const Geo& g,
+                                         const Phys& ph) {
   const int nx = g.nx, ny = g.ny, nxn = g.nxn;
   const int nc = nx * ny, nn = nxn * ny;
   const T hdx = (T)ph.hdx, hdy = (T)ph.hdy, idx = (T)ph.idx;
   const T jcr = (T)ph.jcr, eta = (T)ph.eta;
   const bool per = (g.bc_x == FS_BC_PERIODIC);
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nn;
-       q += gridDim.x * blockDim.x) {
+  {
     const int i = q % nxn, j = q / nxn;
     auto cxo = [&](int c) { return per ? wrap(c, nx) : min(max(c, 0), nx - 1); };
     T bbx, bby, bbz, cxv, cyv, czv;
@@ -723,22 +768,9 @@ __global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
     } else {
       density_terms<T, DIM>(nN, i, j, g, ph, inv_n, pgx, pgy);
     }
-    const T ux = uN[q], uy = uN[nn + q], uz = uN[2 * nn + q];
-    const T ax = cxv - jcr, ay = cyv, az = czv;
-    const T cax = fmaT(ay, bbz, -(az * bby));
-    const T cay = fmaT(az, bbx, -(ax * bbz));
-    const T caz = fmaT(ax, bby, -(ay * bbx));
-    const T cux = fmaT(uy, bbz, -(uz * bby));
-    const T cuy = fmaT(uz, bbx, -(ux * bbz));
-    const T cuz = fmaT(ux, bby, -(uy * bbx));
-    T ex = fmaT(pgx, inv_n, fmaT(cax, inv_n, -cux));
-    T ey = fmaT(pgy, inv_n, fmaT(cay, inv_n, -cuy));
-    T ez = fmaT(caz, inv_n, -cuz);
-    if (ph.eta != 0.0) {
-      ex = ex + eta * cxv;
-      ey = ey + eta * cyv;
-      ez = ez + eta * czv;
-    }
+    T ex, ey, ez;
+    ohm_e<T>(cxv, cyv, czv, bbx, bby, bbz, inv_n, pgx, pgy, uN[q], uN[nn + q], uN[2 * nn + q],
+             jcr, eta, ph.eta != 0.0, ex, ey, ez);
     Eo[q] = ex;
     Eo[nn + q] = ey;
     Eo[2 * nn + q] = ez;
@@ -765,23 +797,27 @@ __global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
   }
 }
 
-// Faraday at the centres, K = -curl E from the four corner nodes, and the
-// RK4 stage update:
-//   stage 1: Bsum = K;            Bs = B + (h/2) K
-//   stage 2: Bsum = Bsum + 2 K;   Bs = B + (h/2) K
-//   stage 3: Bsum = Bsum + 2 K;   Bs = B + h K
-//   stage 4: Bsum = Bsum + K;     B  = B + (h/6) Bsum
 template <typename T, int DIM>
-__global__ void k_faraday(const T* __restrict__ En, T* __restrict__ B,
-                          T* __restrict__ Bs, T* __restrict__ Bsum, int stage,
-                          Geo g, Phys ph) {
+__global__ void k_ohm(const T* __restrict__ Bc, const T* __restrict__ nN,
+                      const T* __restrict__ uN, const T* __restrict__ pre,
+                      T* __restrict__ Eo, T* __restrict__ Bbo, T* __restrict__ G, Geo g,
+                      Phys ph) {
+  const int nn = g.nxn * g.ny;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += gridDim.x * blockDim.x)
+    ohm_node<T, DIM>(q, Bc, nN, uN, pre, Eo, Bbo, G, g, ph);
+}
+
+// Faraday at centre c = j * nx + i, K = -curl E from the four corner nodes
+// (two in 1D), and the RK4 stage update (rk4_stage): the body of k_faraday.
+template <typename T, int DIM>
+__device__ __forceinline__ void faraday_cell(int c, const T* En, T* B, T* Bs, T* Bsum,
+                                             int stage, const Geo& g, const Phys& ph) {
   const int nx = g.nx, ny = g.ny, nxn = g.nxn;
   const int nc = nx * ny, nn = nxn * ny;
   const T hdx = (T)ph.hdx, hdy = (T)ph.hdy, idx = (T)ph.idx;
   const T h = (T)ph.h, hh = (T)ph.hh, h6 = (T)ph.h6;
   const bool per = (g.bc_x == FS_BC_PERIODIC);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
-       c += gridDim.x * blockDim.x) {
+  {
     const int i = c % nx, j = c / nx;
     const int i1 = (per && i + 1 == nx) ? 0 : i + 1;
     T K[3];
@@ -808,21 +844,18 @@ __global__ void k_faraday(const T* __restrict__ En, T* __restrict__ B,
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const size_t k = (size_t)q * nc + c;
-      if (stage == 1) {
-        Bsum[k] = K[q];
-        Bs[k] = fmaT(hh, K[q], B[k]);
-      } else if (stage == 2) {
-        Bsum[k] = fmaT((T)2, K[q], Bsum[k]);
-        Bs[k] = fmaT(hh, K[q], B[k]);
-      } else if (stage == 3) {
-        Bsum[k] = fmaT((T)2, K[q], Bsum[k]);
-        Bs[k] = fmaT(h, K[q], B[k]);
-      } else {
-        const T sum = Bsum[k] + K[q];
-        B[k] = fmaT(h6, sum, B[k]);
-      }
+      rk4_stage<T>(stage, K[q], Bsum[k], Bs[k], B[k], h, hh, h6);
     }
   }
+}
+
+template <typename T, int DIM>
+__global__ void k_faraday(const T* __restrict__ En, T* __restrict__ B,
+                          T* __restrict__ Bs, T* __restrict__ Bsum, int stage,
+                          Geo g, Phys ph) {
+  const int nc = g.nx * g.ny;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+    faraday_cell<T, DIM>(c, En, B, Bs, Bsum, stage, g, ph);
 }
 
 // ------------------------------------------------------------------------

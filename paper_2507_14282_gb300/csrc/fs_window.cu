@@ -39,29 +39,29 @@ template <typename T>
 struct Win {
   int cap;  // particle slots
   Slots<T> s;
-  // fields: B at centres [3][nx]; E, Bbar at nodes [3][nxn]; RK4 stages
-  T *B, *Bs, *Bsum, *E, *Es, *Bb;
+  // fields: B at centres [3][nx] (and the buffer the next B is written to);
+  // E, Bbar at nodes [3][nxn]
+  T *B, *Bx, *E, *Bb;
   T *n, *u, *nraw;             // moments in use [nxn], [3][nxn], [nxn]
   unsigned long long* q;       // fixed-point deposit sums [4][nxn]
   unsigned long long* ctr;     // incident, returned, transmitted, escaped, injected
   // adjoint
   T *lf, *lv;                  // particle adjoints: offset, velocity [3][cap]
-  double *lB, *lE, *lBb;       // [3][nx], [3][nxn], [3][nxn]
-  double *lN, *lU;             // adjoint of the moments of the step being reversed
-  double *lNm, *lUm;           // adjoint of the moments that E^n used
-  double *lNr, *lJ;            // deposit adjoints (raw density, current)
-  double *P;                   // node partials [4][nxn]
-  double *Y;                   // RK4 stage inputs [n_sub][4][3][nx]
-  double *g, *lY, *lsum, *lend;  // RK4 adjoint work [3][nx]
+  double *lB, *lBx;            // of B [3][nx] (and the buffer the next one goes to)
+  double *lE, *lBb;            // of E, Bbar [3][nxn]
+  double *lNm, *lUm;           // of the moments that E^n used [nxn], [3][nxn]
+  double *lNr, *lJ;            // of the deposit sums (raw density, current)
   double* grad;                // d loss / d theta [M + 2]
 };
 
 // ---------------------------------------------------------------- forward
+// Gather, Boris push, move, far wall and faux-shock crossing of slot p.
 template <typename T>
-__global__ void k_win_push(Win<T> w, Slots<T> tape, uint8_t* ev, Geo g, Phys ph,
-                           long long step, int np) {
+__device__ __forceinline__ void push_slot(int p, const Win<T>& w, const Slots<T>& tape,
+                                          uint8_t* ev, const Geo& g, const Phys& ph,
+                                          long long step) {
   const int nxn = g.nxn;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+  {
     int ci = w.s.ci[p];
     T f = w.s.f[p];
     T vx = w.s.v[p], vy = w.s.v[w.cap + p], vz = w.s.v[2 * w.cap + p];
@@ -75,7 +75,7 @@ __global__ void k_win_push(Win<T> w, Slots<T> tape, uint8_t* ev, Geo g, Phys ph,
     }
     if (ci < 0) {
       if (ev) ev[p] = kEvRemoved;
-      continue;
+      return;
     }
     uint8_t e = kEvNone;
     const T g0 = (T)1 - f;
@@ -124,7 +124,7 @@ __global__ void k_win_push(Win<T> w, Slots<T> tape, uint8_t* ev, Geo g, Phys ph,
     if (ev) ev[p] = e;
     if (e == kEvRemoved) {
       w.s.ci[p] = -1;
-      continue;
+      return;
     }
     w.s.ci[p] = inew;
     w.s.f[p] = fn;
@@ -163,11 +163,11 @@ __device__ __forceinline__ double cr_draw(const Phys& ph, uint32_t pid, long lon
 // n_new thermal ions at x = L, then n_new cosmic rays at x = 0, into slots
 // np .. np + 2 n_new (ids first, first + 1, ...), as the engine draws them.
 template <typename T>
-__global__ void k_win_inject(Win<T> w, Geo g, Phys ph, long long step, int np, int n_new,
-                             unsigned long long first) {
+__device__ __forceinline__ void inject_one(int k, const Win<T>& w, const Geo& g,
+                                           const Phys& ph, long long step, int np, int n_new,
+                                           unsigned long long first) {
   const int nth = ph.inject_thermal ? n_new : 0;
   const int ncr = ph.cr_enable ? n_new : 0;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nth + ncr) return;
   const uint32_t pid = (uint32_t)(first + k);
   const int nx = g.nx;
@@ -209,61 +209,118 @@ __global__ void k_win_inject(Win<T> w, Geo g, Phys ph, long long step, int np, i
   if (k == 0) atomicAdd(&w.ctr[4], (unsigned long long)(nth + ncr));
 }
 
+// One launch for the push of slots 0 .. np - 1 and the injection into
+// slots np .. (the two touch disjoint slots): the first `ib` blocks inject,
+// so that their long FP64 draw chains start first, the rest push. Also
+// clears the fixed-point sums for the step's deposit.
+template <typename T>
+__global__ void k_win_push_inject(Win<T> w, Slots<T> tape, uint8_t* ev, Geo g, Phys ph,
+                                  long long step, int np, int n_new, unsigned long long first,
+                                  int ib) {
+  // the deposit sums, read by the previous step's field kernel, start over
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 4 * g.nxn; k += gridDim.x * blockDim.x)
+    w.q[k] = 0ull;
+  if ((int)blockIdx.x < ib) {
+    inject_one<T>(blockIdx.x * blockDim.x + threadIdx.x, w, g, ph, step, np, n_new, first);
+    return;
+  }
+  const int stride = (gridDim.x - ib) * blockDim.x;
+  for (int p = (blockIdx.x - ib) * blockDim.x + threadIdx.x; p < np; p += stride)
+    push_slot<T>(p, w, tape, ev, g, ph, step);
+}
+
 __device__ __forceinline__ unsigned long long fix(double c) {
   return (unsigned long long)__double2ll_rn(c * kFix);
 }
 
-// CIC deposit of every live slot into the fixed-point sums (order free).
+// Sum of v over the lanes of `mask` (all of which call it with that mask),
+// exact for |v| < 2^57: the 16-bit low parts and the 32-bit high part are
+// added as 32-bit integers and recombined.
+__device__ __forceinline__ long long group_sum(unsigned mask, long long v) {
+  const unsigned l0 = __reduce_add_sync(mask, (unsigned)(v & 0xFFFF));
+  const unsigned l1 = __reduce_add_sync(mask, (unsigned)((v >> 16) & 0xFFFF));
+  const int hi = __reduce_add_sync(mask, (int)(v >> 32));
+  return ((long long)hi << 32) + ((long long)l1 << 16) + (long long)l0;
+}
+
+// CIC deposit of every live slot into the fixed-point sums. The slots of a
+// warp sit mostly in a few cells (birth order), so the lanes of each cell
+// first add their contributions (integer sums: the result does not depend on
+// the grouping) and one lane per cell issues the atomics.
 template <typename T>
 __global__ void k_win_deposit(Win<T> w, Geo g, Phys ph, int np) {
   const int nxn = g.nxn;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    const int ci = w.s.ci[p];
-    if (ci < 0) continue;
-    const double wp = (w.s.id[p] & kIdCR) ? ph.w_cr : ph.w_th;
-    const double f = (double)w.s.f[p];
-    const double c0 = wp * (1.0 - f), c1 = wp * f;
-    const double v[3] = {(double)w.s.v[p], (double)w.s.v[w.cap + p],
-                         (double)w.s.v[2 * w.cap + p]};
-    atomicAdd(&w.q[ci], fix(c0));
-    atomicAdd(&w.q[ci + 1], fix(c1));
+  const int lane = threadIdx.x & 31;
+  constexpr long long kBig = 1LL << 57;
+  for (int base = blockIdx.x * blockDim.x + threadIdx.x - lane; base < np;
+       base += gridDim.x * blockDim.x) {
+    const int p = base + lane;
+    const int ci = (p < np) ? w.s.ci[p] : -1;
+    long long a[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // n at ci, ci + 1; J_c at ci, ci + 1
+    if (ci >= 0) {
+      const double wp = (w.s.id[p] & kIdCR) ? ph.w_cr : ph.w_th;
+      const double f = (double)w.s.f[p];
+      const double c0 = wp * (1.0 - f), c1 = wp * f;
+      const double v[3] = {(double)w.s.v[p], (double)w.s.v[w.cap + p],
+                           (double)w.s.v[2 * w.cap + p]};
+      a[0] = (long long)fix(c0);
+      a[1] = (long long)fix(c1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a[2 + 2 * c] = (long long)fix(c0 * v[c]);
+        a[3 + 2 * c] = (long long)fix(c1 * v[c]);
+      }
+    }
+    bool big = false;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) big |= (a[k] >= kBig || a[k] <= -kBig);
+    const unsigned grp = __match_any_sync(0xffffffffu, ci);
+    const bool lead = !__any_sync(0xffffffffu, big);
+    if (lead) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = group_sum(grp, a[k]);
+    }
+    if (ci < 0 || (lead && lane != __ffs(grp) - 1)) continue;
+    atomicAdd(&w.q[ci], (unsigned long long)a[0]);
+    atomicAdd(&w.q[ci + 1], (unsigned long long)a[1]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      atomicAdd(&w.q[(c + 1) * nxn + ci], fix(c0 * v[c]));
-      atomicAdd(&w.q[(c + 1) * nxn + ci + 1], fix(c1 * v[c]));
+      atomicAdd(&w.q[(c + 1) * nxn + ci], (unsigned long long)a[2 + 2 * c]);
+      atomicAdd(&w.q[(c + 1) * nxn + ci + 1], (unsigned long long)a[3 + 2 * c]);
     }
   }
 }
 
-// Moments from the sums: wall nodes x2, density floor, u = J / n; clears the
-// sums. Also writes a copy (the tape of these moments) when given.
+// Moments at node i from the fixed-point sums: wall nodes x2, the density
+// floor, u = J / n; nraw is the density before the floor.
 template <typename T>
-__global__ void k_win_moments(Win<T> w, Geo g, Phys ph, T* tn, T* tu, T* tr) {
+__device__ __forceinline__ void moment_values(int i, const unsigned long long* q, const Geo& g,
+                                              const Phys& ph, T& n, T& nraw, T u[3]) {
+  const int nxn = g.nxn;
+  const double sc = (i == 0 || i == g.nx) ? 2.0 : 1.0;
+  const double nr = (double)(long long)q[i] * kUnfix * sc;
+  n = (T)nr;
+  nraw = (T)nr;
+  const T nf = (T)ph.n_floor;
+  if (n < nf) n = nf;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) u[c] = (T)((double)(long long)q[(c + 1) * nxn + i] * kUnfix * sc) / n;
+}
+
+// The moments at the start of the window; clears the sums.
+template <typename T>
+__global__ void k_win_moments(Win<T> w, Geo g, Phys ph) {
   const int nxn = g.nxn;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nxn) return;
-  const double sc = (i == 0 || i == g.nx) ? 2.0 : 1.0;
-  const double nr = (double)(long long)w.q[i] * kUnfix * sc;
-  double J[3];
+  T n, nr, u[3];
+  moment_values<T>(i, w.q, g, ph, n, nr, u);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    J[c] = (double)(long long)w.q[(c + 1) * nxn + i] * kUnfix * sc;
-    w.q[(c + 1) * nxn + i] = 0ull;
-  }
-  w.q[i] = 0ull;
-  T n = (T)nr;
-  const T nf = (T)ph.n_floor;
-  if (n < nf) n = nf;
-  w.nraw[i] = (T)nr;
+  for (int k = 0; k < 4; ++k) w.q[k * nxn + i] = 0ull;
+  w.nraw[i] = nr;
   w.n[i] = n;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) w.u[c * nxn + i] = (T)J[c] / n;
-  if (tn) {
-    tn[i] = n;
-    tr[i] = (T)nr;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) tu[c * nxn + i] = w.u[c * nxn + i];
-  }
+  for (int c = 0; c < 3; ++c) w.u[c * nxn + i] = u[c];
 }
 
 // B = B0 + sum_m a_m (cos, sin)(2 pi m x / L + phi_m) at the centres
@@ -288,10 +345,10 @@ __global__ void k_win_seed_B(T* B, Geo g, Phys ph, double dx, const double* amps
 }
 
 // loss = sum_{i >= i0} |B_perp - B0_perp|^2 dx (into *out), and its
-// gradient with respect to B (into lB) when lB is given
+// gradient with respect to B times `scale` (into lB) when lB is given
 template <typename T>
 __global__ void k_win_loss(const T* B, Geo g, Phys ph, int i0, double dx, double* out,
-                           double* lB) {
+                           double* lB, double scale) {
   double s = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
     double dy = 0.0, dz = 0.0;
@@ -302,8 +359,8 @@ __global__ void k_win_loss(const T* B, Geo g, Phys ph, int i0, double dx, double
     }
     if (lB) {
       lB[i] = 0.0;
-      lB[g.nx + i] = 2.0 * dy * dx;
-      lB[2 * g.nx + i] = 2.0 * dz * dx;
+      lB[g.nx + i] = scale * (2.0 * dy * dx);
+      lB[2 * g.nx + i] = scale * (2.0 * dz * dx);
     }
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -311,145 +368,459 @@ __global__ void k_win_loss(const T* B, Geo g, Phys ph, int i0, double dx, double
 }
 
 // ---------------------------------------------------------------- adjoint
-// Node-local part of the adjoint of Ohm's law (1D, nodes i = 0..nx), for a
-// centre field Bc with n, u frozen. The adjoint of E at the node comes from
-// lE, or, with gK != nullptr, from the adjoint gK of K = -curl E at the
-// centres (Faraday: K_y(c) = (E_z(c+1) - E_z(c))/dx, K_z(c) = -(E_y(c+1) -
-// E_y(c))/dx). lBbar (optional) adds the adjoint of Bbar. Writes the
-// adjoints of the node's Bbar_y, Bbar_z, dB_y/dx, dB_z/dx into P and adds the
-// adjoints of n and u.
-template <typename T>
-__global__ void k_win_ohm_adj(const double* Bc, const T* nN, const T* uN, const double* gK,
-                              const double* lE, const double* lBbar, double* P, double* lN,
-                              double* lU, Geo g, Phys ph) {
-  const int nx = g.nx, nxn = g.nxn;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nxn) return;
+// Adjoint of Ohm's law at one node of the 1D grid with n, u frozen. In: the
+// centre fields Bm, Bp of the node's two cells (clamped at the walls), the
+// density n at the node and np, nm at its neighbours (mirrored at the walls),
+// u at the node and the adjoint (lex, ley, lez) of E there. Out: the
+// adjoints of Bbar_y, Bbar_z, dB_y/dx, dB_z/dx at the node (P), that of n at
+// the node (ln), the weight lp of n at the right neighbour (its negative at
+// the left one: the pressure term's two-point difference) and the adjoint
+// of u (lu).
+//   E = ((curl B - jcr x) x Bbar - T_e grad n)/n - u x Bbar + eta curl B,
+//   curl B = (0, -dB_z/dx, dB_y/dx)
+struct OhmAdj {
+  double P[4], ln, lp, lu[3];
+};
+__device__ __forceinline__ OhmAdj ohm_adj_point(const double Bm[3], const double Bp[3],
+                                                double n, double np, double nm,
+                                                const double u[3], double lex, double ley,
+                                                double lez, const Phys& ph) {
   const double idx = ph.idx, te = ph.te, jcr = ph.jcr, eta = ph.eta;
-  double lex, ley, lez;
-  if (gK) {
-    const double gym = (i >= 1) ? gK[nx + i - 1] : 0.0, gy = (i < nx) ? gK[nx + i] : 0.0;
-    const double gzm = (i >= 1) ? gK[2 * nx + i - 1] : 0.0, gz = (i < nx) ? gK[2 * nx + i] : 0.0;
-    lex = 0.0;
-    lez = (gym - gy) * idx;
-    ley = (gz - gzm) * idx;
-  } else {
-    lex = lE[i];
-    ley = lE[nxn + i];
-    lez = lE[2 * nxn + i];
-  }
-  const int im = min(max(i - 1, 0), nx - 1), ip = min(max(i, 0), nx - 1);
-  const double bbx = 0.5 * (Bc[im] + Bc[ip]);
-  const double bby = 0.5 * (Bc[nx + im] + Bc[nx + ip]);
-  const double bbz = 0.5 * (Bc[2 * nx + im] + Bc[2 * nx + ip]);
-  const double dby = (Bc[nx + ip] - Bc[nx + im]) * idx;
-  const double dbz = (Bc[2 * nx + ip] - Bc[2 * nx + im]) * idx;
-  const double n = (double)nN[i];
-  const double ux = (double)uN[i], uy = (double)uN[nxn + i], uz = (double)uN[2 * nxn + i];
+  const double bbx = 0.5 * (Bm[0] + Bp[0]);
+  const double bby = 0.5 * (Bm[1] + Bp[1]);
+  const double bbz = 0.5 * (Bm[2] + Bp[2]);
+  const double dby = (Bp[1] - Bm[1]) * idx;
+  const double dbz = (Bp[2] - Bm[2]) * idx;
+  const double ux = u[0], uy = u[1], uz = u[2];
   const double in = 1.0 / n;
-  // E = ((curl B - jcr x) x Bbar - T_e grad n)/n - u x Bbar + eta curl B,
-  // curl B = (0, -dbz, dby)
-  double lbby = lex * (-dby * in + uz) + lez * (-jcr * in - ux);
-  double lbbz = lex * (-dbz * in - uy) + ley * (jcr * in + ux);
-  const double ldby = lex * (-bby * in) + ley * (bbx * in) + lez * eta;
-  const double ldbz = lex * (-bbz * in) + lez * (bbx * in) - ley * eta;
-  if (lBbar) {
-    lbby += lBbar[nxn + i];
-    lbbz += lBbar[2 * nxn + i];
-  }
-  P[i] = lbby;
-  P[nxn + i] = lbbz;
-  P[2 * nxn + i] = ldby;
-  P[3 * nxn + i] = ldbz;
-  // moments: 1/n and the pressure term -T_e (n(i+1) - n(i-1)) / (2 dx)
-  // (mirrored density at the walls); neighbours add too, so atomics
+  OhmAdj r;
+  r.P[0] = lex * (-dby * in + uz) + lez * (-jcr * in - ux);
+  r.P[1] = lex * (-dbz * in - uy) + ley * (jcr * in + ux);
+  r.P[2] = lex * (-bby * in) + ley * (bbx * in) + lez * eta;
+  r.P[3] = lex * (-bbz * in) + lez * (bbx * in) - ley * eta;
   const double cax = -dbz * bbz - dby * bby;
   const double cay = dby * bbx + jcr * bbz;
   const double caz = -jcr * bby + dbz * bbx;
-  const int ipn = (i + 1 > nx) ? 2 * nx - (i + 1) : i + 1;
-  const int imn = (i - 1 < 0) ? -(i - 1) : i - 1;
-  const double pgx = -(te * (((double)nN[ipn] - (double)nN[imn]) * ph.hdx));
-  atomicAdd(&lN[i], -(lex * (pgx + cax) + ley * cay + lez * caz) * in * in);
-  const double lp = -lex * in * te * ph.hdx;  // d ex / d n(i+1); the negative for n(i-1)
-  if (lp != 0.0) {
-    atomicAdd(&lN[ipn], lp);
-    atomicAdd(&lN[imn], -lp);
-  }
-  // u x Bbar: ex = .. - (uy bbz - uz bby), ey = .. - (uz bbx - ux bbz),
-  // ez = .. - (ux bby - uy bbx); only node i touches lU(i)
-  lU[i] += ley * bbz - lez * bby;
-  lU[nxn + i] += -lex * bbz + lez * bbx;
-  lU[2 * nxn + i] += lex * bby - ley * bbx;
+  const double pgx = -(te * ((np - nm) * ph.hdx));
+  r.ln = -(lex * (pgx + cax) + ley * cay + lez * caz) * in * in;
+  r.lp = -lex * in * te * ph.hdx;
+  r.lu[0] = ley * bbz - lez * bby;
+  r.lu[1] = -lex * bbz + lez * bbx;
+  r.lu[2] = lex * bby - ley * bbx;
+  return r;
 }
 
-// Centre part: the adjoint of B(c) from its two nodes (Bbar = (Bm + Bp)/2,
-// dB = (Bp - Bm)/dx, with the wall nodes reading cell 0 or nx - 1 twice).
-// out = adjoint of B; then acc += out (if acc) and gn = a * lend + b * out
-// (if gn: the next RK4 stage's adjoint).
-__global__ void k_win_curl_adj(const double* P, double* out, double* acc, double* gn,
-                               const double* lend, double a, double b, Geo g, Phys ph) {
-  const int nx = g.nx, nxn = g.nxn;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nx) return;
-  const double idx = ph.idx;
-  double ly = 0.0, lz = 0.0;
-  // node c sees cell c as its p side, node c + 1 sees it as its m side
-  ly += 0.5 * P[c] + P[2 * nxn + c] * idx;
-  lz += 0.5 * P[nxn + c] + P[3 * nxn + c] * idx;
-  ly += 0.5 * P[c + 1] - P[2 * nxn + c + 1] * idx;
-  lz += 0.5 * P[nxn + c + 1] - P[3 * nxn + c + 1] * idx;
-  if (c == 0) {  // node 0: m side clamped to cell 0
-    ly += 0.5 * P[0] - P[2 * nxn] * idx;
-    lz += 0.5 * P[nxn] - P[3 * nxn] * idx;
+// Centre part: the adjoint (ly, lz) of B_y, B_z at cell c from the node
+// partials of its two nodes c (Pc) and c + 1 (Pc1) (Bbar = (Bm + Bp)/2,
+// dB = (Bp - Bm)/dx); the wall nodes 0 and nx read cell 0 or nx - 1 twice.
+__device__ __forceinline__ void curl_adj_point(const double Pc[4], const double Pc1[4],
+                                               bool left_wall, bool right_wall, double idx,
+                                               double& ly, double& lz) {
+  ly = 0.0;
+  lz = 0.0;
+  ly += 0.5 * Pc[0] + Pc[2] * idx;  // node c sees cell c as its p side
+  lz += 0.5 * Pc[1] + Pc[3] * idx;
+  ly += 0.5 * Pc1[0] - Pc1[2] * idx;  // node c + 1 sees it as its m side
+  lz += 0.5 * Pc1[1] - Pc1[3] * idx;
+  if (left_wall) {  // node 0: m side clamped to cell 0
+    ly += 0.5 * Pc[0] - Pc[2] * idx;
+    lz += 0.5 * Pc[1] - Pc[3] * idx;
   }
-  if (c == nx - 1) {  // node nx: p side clamped to cell nx - 1
-    ly += 0.5 * P[nx] + P[2 * nxn + nx] * idx;
-    lz += 0.5 * P[nxn + nx] + P[3 * nxn + nx] * idx;
-  }
-  out[c] = 0.0;
-  out[nx + c] = ly;
-  out[2 * nx + c] = lz;
-  if (acc) {
-    acc[nx + c] += ly;
-    acc[2 * nx + c] += lz;
-  }
-  if (gn) {
-    gn[c] = 0.0;
-    gn[nx + c] = a * lend[nx + c] + b * ly;
-    gn[2 * nx + c] = a * lend[2 * nx + c] + b * lz;
+  if (right_wall) {  // node nx: p side clamped to cell nx - 1
+    ly += 0.5 * Pc1[0] + Pc1[2] * idx;
+    lz += 0.5 * Pc1[1] + Pc1[3] * idx;
   }
 }
 
-// dst = a * x (+ b * y)
-__global__ void k_win_axpy(double* dst, const double* x, double a, const double* y, double b,
-                           int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = a * x[i] + (y ? b * y[i] : 0.0);
-}
-
+// Adjoint of the moments at node i: from the adjoints ln, lu of n (floored)
+// and u = J / n to those of the raw sums (wall nodes x2, no gradient through
+// a floored density).
 template <typename T>
-__global__ void k_win_to_double(double* dst, const T* src, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = (double)src[i];
-}
-
-// Adjoint of the moments of one step: from the adjoints of n (floored) and
-// u = J / n to those of the raw sums (wall nodes x2, no gradient through a
-// floored density).
-template <typename T>
-__global__ void k_win_moments_adj(const T* nN, const T* uN, const T* nraw, const double* lN,
-                                  const double* lU, double* lNr, double* lJ, Geo g, Phys ph) {
+__device__ __forceinline__ void moments_adj_node(int i, const T* nN, const T* uN,
+                                                 const T* nraw, double ln, const double lu[3],
+                                                 double* lNr, double* lJ, const Geo& g,
+                                                 const Phys& ph) {
   const int nxn = g.nxn;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nxn) return;
   const double sc = (i == 0 || i == g.nx) ? 2.0 : 1.0;
   const double n = (double)nN[i];
-  double ln = lN[i];
   for (int c = 0; c < 3; ++c) {
-    lJ[c * nxn + i] = lU[c * nxn + i] / n * sc;
-    ln -= lU[c * nxn + i] * (double)uN[c * nxn + i] / n;
+    lJ[c * nxn + i] = lu[c] / n * sc;
+    ln -= lu[c] * (double)uN[c * nxn + i] / n;
   }
   lNr[i] = ((double)nraw[i] < ph.n_floor) ? 0.0 : ln * sc;
+}
+
+// ------------------------------------------------ blocked field kernels
+// A step's field work is tens of dependent phases over a small 1D grid. Each
+// CTA owns kTbCells cells (and their left nodes; the last CTA also node nx)
+// and runs all phases of the step in shared memory over its cells plus a
+// halo, recomputing the halo: the stencils reach one cell per phase, so
+// wrong values enter from a tile's inner edges (read there with clamped
+// indices) at one cell per phase and never reach the owned cells while the
+// halo is at least the number of phases. At the domain walls the tile edge is
+// the wall and the clamped and mirrored indices are the walls' own. No
+// synchronisation between CTAs, and the FP64 work spreads over the SMs.
+constexpr int kTbCells = 16;
+constexpr int kTbThreads = 64;
+
+// halos: the forward's 4 n_sub stages and final Ohm; the adjoint's stage
+// recompute, its 4 n_sub reverse stages and the moment adjoints
+__host__ __device__ inline int halo_fields(int n_sub) { return 4 * n_sub + 2; }
+__host__ __device__ inline int halo_rk4_adj(int n_sub) { return 8 * n_sub + 3; }
+
+struct Tile {
+  int c0, c1;  // owned cells [c0, c1)
+  int lo, L;   // local cells lo .. lo + L - 1, local nodes lo .. lo + L
+  int nx;
+  __device__ __forceinline__ Tile(int b, int nx_, int halo) : nx(nx_) {
+    c0 = b * kTbCells;
+    c1 = min(nx, c0 + kTbCells);
+    lo = max(0, c0 - halo);
+    L = min(nx, c1 + halo) - lo;
+  }
+  // global cell (clamped at the walls) -> local cell (clamped to the tile)
+  __device__ __forceinline__ int cell(int c) const {
+    c = min(max(c, 0), nx - 1);
+    return min(max(c - lo, 0), L - 1);
+  }
+  // global node (mirrored at the walls) -> local node (clamped to the tile)
+  __device__ __forceinline__ int node(int i) const {
+    i = (i < 0) ? -i : ((i > nx) ? 2 * nx - i : i);
+    return min(max(i - lo, 0), L);
+  }
+  __device__ __forceinline__ bool owns_cell(int c) const { return c >= c0 && c < c1; }
+  __device__ __forceinline__ bool owns_node(int i) const {
+    return (i >= c0 && i < c1) || (i == nx && c1 == nx);
+  }
+};
+
+// Ohm's law at global node gi of a tile, from the tile's centre field B
+// [3][L], density n [L + 1] and velocity u [3][L + 1] (the 1D form of
+// ohm_node).
+template <typename T>
+__device__ __forceinline__ void tile_ohm(const Tile& t, int gi, const T* B, const T* n,
+                                         const T* u, const Phys& ph, T E[3], T Bb[3]) {
+  const int L = t.L, Ln = L + 1, i = gi - t.lo;
+  const int im = t.cell(gi - 1), ip = t.cell(gi);
+  const T idx = (T)ph.idx;
+  const T bmy = B[L + im], bpy = B[L + ip], bmz = B[2 * L + im], bpz = B[2 * L + ip];
+  Bb[0] = (T)0.5 * (B[im] + B[ip]);
+  Bb[1] = (T)0.5 * (bmy + bpy);
+  Bb[2] = (T)0.5 * (bmz + bpz);
+  const T dby = (bpy - bmy) * idx;
+  const T dbz = (bpz - bmz) * idx;
+  const T te = (T)ph.te;
+  const T dnx = (n[t.node(gi + 1)] - n[t.node(gi - 1)]) * (T)ph.hdx;
+  const T inv_n = (T)1 / n[i];
+  ohm_e<T>((T)0, -dbz, dby, Bb[0], Bb[1], Bb[2], inv_n, -(te * dnx), -(te * (T)0), u[i],
+           u[Ln + i], u[2 * Ln + i], (T)ph.jcr, (T)ph.eta, ph.eta != 0.0, E[0], E[1], E[2]);
+}
+
+// Faraday + RK4 stage update at local cell c of a tile (1D: K = (0, dEz/dx,
+// -dEy/dx) from the nodes c, c + 1).
+template <typename T>
+__device__ __forceinline__ void tile_faraday(const Tile& t, int c, const T* E, T* B, T* Bs,
+                                             T* K, int stage, const Phys& ph) {
+  const int L = t.L, Ln = L + 1;
+  const T idx = (T)ph.idx;
+  const T dxey = (E[Ln + c + 1] - E[Ln + c]) * idx;
+  const T dxez = (E[2 * Ln + c + 1] - E[2 * Ln + c]) * idx;
+  const T Kc[3] = {(T)0, dxez, -dxey};
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    rk4_stage<T>(stage, Kc[q], K[q * L + c], Bs[q * L + c], B[q * L + c], (T)ph.h, (T)ph.hh,
+                 (T)ph.h6);
+}
+
+constexpr size_t kMaxSmem = 227 * 1024;  // shared memory a CTA may opt in to
+
+inline size_t fields_smem(int n_sub, size_t tsz) {
+  const size_t L = kTbCells + 2 * halo_fields(n_sub);
+  return tsz * (9 * L + 7 * (L + 1));
+}
+inline size_t rk4_adj_smem(int n_sub, size_t tsz) {
+  const size_t L = kTbCells + 2 * halo_rk4_adj(n_sub), Ln = L + 1;
+  return tsz * (9 * L + 7 * Ln) + 8 * ((12 * (size_t)n_sub + 12) * L + 11 * Ln);
+}
+
+// One step's moments (and their tape) from the deposit sums, B's tape, the
+// n_sub RK4 substeps of Ohm + Faraday with n, u frozen, then E, Bbar for the
+// next gather and the new B (into Bout; B is read by neighbouring tiles).
+template <typename T>
+__global__ void __launch_bounds__(kTbThreads) k_win_fields(Win<T> w, Geo g, Phys ph, int n_sub,
+                                                           T* Bout, T* tn, T* tu, T* tr,
+                                                           T* tapeB) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nx = g.nx, nxn = g.nxn, t0 = threadIdx.x, nt = blockDim.x;
+  const Tile t(blockIdx.x, nx, halo_fields(n_sub));
+  const int L = t.L, Ln = L + 1;
+  T* sB = (T*)smem;
+  T* sBs = sB + 3 * L;
+  T* sK = sBs + 3 * L;
+  T* sE = sK + 3 * L;
+  T* sn = sE + 3 * Ln;
+  T* su = sn + Ln;
+  for (int k = t0; k < 3 * L; k += nt) {
+    const int q = k / L, gc = t.lo + k - q * L;
+    const T v = w.B[q * nx + gc];
+    sB[k] = v;
+    if (tapeB && t.owns_cell(gc)) tapeB[q * nx + gc] = v;
+  }
+  for (int i = t0; i < Ln; i += nt) {
+    const int gi = t.lo + i;
+    T n, nr, u[3];
+    moment_values<T>(gi, w.q, g, ph, n, nr, u);
+    sn[i] = n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) su[c * Ln + i] = u[c];
+    if (t.owns_node(gi)) {
+      w.n[gi] = n;
+      w.nraw[gi] = nr;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w.u[c * nxn + gi] = u[c];
+      if (tn) {
+        tn[gi] = n;
+        tr[gi] = nr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tu[c * nxn + gi] = u[c];
+      }
+    }
+  }
+  __syncthreads();
+  for (int sub = 0; sub < n_sub; ++sub) {
+    for (int stage = 1; stage <= 4; ++stage) {
+      const T* Bin = (stage == 1) ? sB : sBs;
+      for (int i = t0; i < Ln; i += nt) {
+        T E[3], Bb[3];
+        tile_ohm<T>(t, t.lo + i, Bin, sn, su, ph, E, Bb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sE[c * Ln + i] = E[c];
+      }
+      __syncthreads();
+      for (int c = t0; c < L; c += nt) tile_faraday<T>(t, c, sE, sB, sBs, sK, stage, ph);
+      __syncthreads();
+    }
+  }
+  for (int i = t0; i < Ln; i += nt) {
+    const int gi = t.lo + i;
+    if (!t.owns_node(gi)) continue;
+    T E[3], Bb[3];
+    tile_ohm<T>(t, gi, sB, sn, su, ph, E, Bb);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w.E[c * nxn + gi] = E[c];
+      w.Bb[c * nxn + gi] = Bb[c];
+    }
+  }
+  for (int k = t0; k < 3 * L; k += nt) {
+    const int q = k / L, gc = t.lo + k - q * L;
+    if (t.owns_cell(gc)) Bout[q * nx + gc] = sB[k];
+  }
+}
+
+// Reverse of one step's field update and moments. In: B^n (Bn, tape),
+// M^{n+1} (n1, u1, nr1), M^n (n0, u0), lBin = adjoint of B^{n+1}, lNm, lUm
+// = what E^{n+1}'s Ohm added to the adjoint of M^{n+1}. Per tile:
+//   1. the RK4 stage inputs from B^n with n, u frozen at M^{n+1}, recomputed
+//      with the forward's arithmetic (Y);
+//   2. the stages in reverse: per stage the node part of Ohm's adjoint
+//      (partials P, the n and u adjoints), then the centre part (the running
+//      sum, the next stage's adjoint gk), to the adjoint of B^n (lBout);
+//   3. the adjoints of the raw deposit sums (lNr, lJ) from those of M^{n+1};
+//   4. E^n, Bbar^n from B^n and M^n for the particle adjoint; lE = lBb = 0;
+//      lNm = lUm = 0 for the next Ohm adjoint.
+template <typename T>
+__global__ void __launch_bounds__(kTbThreads)
+    k_win_rk4_adj(Win<T> w, Geo g, Phys ph, int ns, const T* Bn, const T* n1, const T* u1,
+                  const T* nr1, const T* n0, const T* u0, const double* lBin, double* lBout) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nx = g.nx, nxn = g.nxn, t0 = threadIdx.x, nt = blockDim.x;
+  const Tile t(blockIdx.x, nx, halo_rk4_adj(ns));
+  const int L = t.L, Ln = L + 1;
+  double* Y = (double*)smem;        // [4 ns][3][L]
+  double* lB = Y + 12 * ns * L;     // [3][L]
+  double* lend = lB + 3 * L;        // [3][L]
+  double* lsum = lend + 3 * L;      // [3][L]
+  double* gk = lsum + 3 * L;        // [3][L]
+  double* P = gk + 3 * L;           // [4][Ln]
+  double* lN = P + 4 * Ln;          // [Ln]
+  double* lU = lN + Ln;             // [3][Ln]
+  double* lnS = lU + 3 * Ln;        // [Ln]
+  double* lpS = lnS + Ln;           // [Ln]
+  T* sB = (T*)(lpS + Ln);           // [3][L]
+  T* sBs = sB + 3 * L;
+  T* sK = sBs + 3 * L;
+  T* sE = sK + 3 * L;               // [3][Ln]
+  T* sn = sE + 3 * Ln;              // [Ln]
+  T* su = sn + Ln;                  // [3][Ln]
+  const double h = ph.h, hh = ph.hh, h6 = ph.h6, idx = ph.idx;
+  for (int k = t0; k < 3 * L; k += nt) {
+    const int q = k / L, gc = t.lo + k - q * L;
+    sB[k] = Bn[q * nx + gc];
+    lB[k] = lBin[q * nx + gc];
+  }
+  for (int i = t0; i < Ln; i += nt) {
+    const int gi = t.lo + i;
+    const bool own = t.owns_node(gi);
+    sn[i] = n1[gi];
+    lN[i] = own ? w.lNm[gi] : 0.0;
+    if (own) w.lNm[gi] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      su[c * Ln + i] = u1[c * nxn + gi];
+      lU[c * Ln + i] = own ? w.lUm[c * nxn + gi] : 0.0;
+      if (own) w.lUm[c * nxn + gi] = 0.0;
+    }
+  }
+  __syncthreads();
+  // 1.
+  for (int sub = 0; sub < ns; ++sub) {
+    for (int stage = 1; stage <= 4; ++stage) {
+      const T* Bin = (stage == 1) ? sB : sBs;
+      double* y = Y + (size_t)(4 * sub + stage - 1) * 3 * L;
+      for (int k = t0; k < 3 * L; k += nt) y[k] = (double)Bin[k];
+      for (int i = t0; i < Ln; i += nt) {
+        T E[3], Bb[3];
+        tile_ohm<T>(t, t.lo + i, Bin, sn, su, ph, E, Bb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sE[c * Ln + i] = E[c];
+      }
+      __syncthreads();
+      for (int c = t0; c < L; c += nt) tile_faraday<T>(t, c, sE, sB, sBs, sK, stage, ph);
+      __syncthreads();
+    }
+  }
+  // 2. lambda_start = lambda_end + sum over the stages of lambda_Y; the stage
+  //    adjoints g4 = h6 lend, g3 = 2 h6 lend + h lY4, g2 = 2 h6 lend + hh lY3,
+  //    g1 = h6 lend + hh lY2
+  const double an[3] = {2 * h6, 2 * h6, h6};
+  const double bn[3] = {h, hh, hh};
+  for (int sub = ns - 1; sub >= 0; --sub) {
+    for (int k = t0; k < 3 * L; k += nt) {
+      const double l = lB[k];
+      lend[k] = l;
+      lsum[k] = l;
+      gk[k] = h6 * l;
+    }
+    __syncthreads();
+    for (int s = 3; s >= 0; --s) {
+      const double* y = Y + (size_t)(4 * sub + s) * 3 * L;
+      for (int i = t0; i < Ln; i += nt) {
+        const int gi = t.lo + i;
+        const int cm = t.cell(gi - 1), cp = t.cell(gi);
+        // E adjoint at the node from K's: K_y(c) = (E_z(c+1) - E_z(c))/dx,
+        // K_z(c) = -(E_y(c+1) - E_y(c))/dx
+        const double gym = (gi >= 1) ? gk[L + cm] : 0.0, gy = (gi < nx) ? gk[L + cp] : 0.0;
+        const double gzm = (gi >= 1) ? gk[2 * L + cm] : 0.0, gz = (gi < nx) ? gk[2 * L + cp] : 0.0;
+        const double Bm[3] = {y[cm], y[L + cm], y[2 * L + cm]};
+        const double Bp[3] = {y[cp], y[L + cp], y[2 * L + cp]};
+        const double u[3] = {(double)su[i], (double)su[Ln + i], (double)su[2 * Ln + i]};
+        const OhmAdj r = ohm_adj_point(Bm, Bp, (double)sn[i], (double)sn[t.node(gi + 1)],
+                                       (double)sn[t.node(gi - 1)], u, 0.0, (gz - gzm) * idx,
+                                       (gym - gy) * idx, ph);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P[q * Ln + i] = r.P[q];
+        lnS[i] = r.ln;
+        lpS[i] = r.lp;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) lU[c * Ln + i] += r.lu[c];
+      }
+      __syncthreads();
+      const int q = 3 - s;
+      for (int c = t0; c < L; c += nt) {
+        const int gc = t.lo + c;
+        const double Pc[4] = {P[c], P[Ln + c], P[2 * Ln + c], P[3 * Ln + c]};
+        const double Pc1[4] = {P[c + 1], P[Ln + c + 1], P[2 * Ln + c + 1], P[3 * Ln + c + 1]};
+        double ly, lz;
+        curl_adj_point(Pc, Pc1, gc == 0, gc == nx - 1, idx, ly, lz);
+        lsum[L + c] += ly;
+        lsum[2 * L + c] += lz;
+        if (s > 0) {
+          gk[c] = 0.0;
+          gk[L + c] = an[q] * lend[L + c] + bn[q] * ly;
+          gk[2 * L + c] = an[q] * lend[2 * L + c] + bn[q] * lz;
+        }
+      }
+      // n adjoint: the node's own term and its neighbours' pressure weights
+      // (node j - 1 adds lp at j, node j + 1 adds -lp at j; the mirrored
+      // wall nodes 0 and nx add their other term at 1 and nx - 1)
+      for (int j = t0; j < Ln; j += nt) {
+        const int gj = t.lo + j;
+        double a = lnS[j];
+        if (gj >= 1) a += lpS[t.node(gj - 1)];
+        if (gj + 1 <= nx) a -= lpS[t.node(gj + 1)];
+        if (gj == nx - 1) a += lpS[t.node(nx)];
+        if (gj == 1) a -= lpS[t.node(0)];
+        lN[j] += a;
+      }
+      __syncthreads();
+    }
+    for (int k = t0; k < 3 * L; k += nt) lB[k] = lsum[k];
+    __syncthreads();
+  }
+  // 3., 4.
+  for (int i = t0; i < Ln; i += nt) {
+    const int gi = t.lo + i;
+    if (!t.owns_node(gi)) continue;
+    const double lu[3] = {lU[i], lU[Ln + i], lU[2 * Ln + i]};
+    moments_adj_node<T>(gi, n1, u1, nr1, lN[i], lu, w.lNr, w.lJ, g, ph);
+    ohm_node<T, 1>(gi, Bn, n0, u0, nullptr, w.E, w.Bb, nullptr, g, ph);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w.lE[c * nxn + gi] = 0.0;
+      w.lBb[c * nxn + gi] = 0.0;
+    }
+  }
+  for (int k = t0; k < 3 * L; k += nt) {
+    const int q = k / L, gc = t.lo + k - q * L;
+    if (t.owns_cell(gc)) lBout[q * nx + gc] = lB[k];
+  }
+}
+
+// The adjoint of Ohm's law at the start of step n (B^n in Bn, M^n in n0,
+// u0), after the particle adjoint (lE, lBb): lB += its share at the owned
+// cells; the owned nodes add their n, u adjoints to lNm (atomics: the
+// pressure term reaches the neighbours) and lUm.
+template <typename T>
+__global__ void __launch_bounds__(kTbThreads)
+    k_win_ohm_adj_step(Win<T> w, Geo g, Phys ph, const T* Bn, const T* n0, const T* u0) {
+  __shared__ double P[4][kTbCells + 1];
+  const int nx = g.nx, nxn = g.nxn, t0 = threadIdx.x, nt = blockDim.x;
+  const int c0 = blockIdx.x * kTbCells, c1 = min(nx, c0 + kTbCells);
+  for (int k = t0; k <= c1 - c0; k += nt) {  // nodes c0 .. c1
+    const int gi = c0 + k;
+    const int im = min(max(gi - 1, 0), nx - 1), ip = min(gi, nx - 1);
+    const double Bm[3] = {(double)Bn[im], (double)Bn[nx + im], (double)Bn[2 * nx + im]};
+    const double Bp[3] = {(double)Bn[ip], (double)Bn[nx + ip], (double)Bn[2 * nx + ip]};
+    const int ipn = (gi + 1 > nx) ? 2 * nx - (gi + 1) : gi + 1;
+    const int imn = (gi - 1 < 0) ? -(gi - 1) : gi - 1;
+    const double u[3] = {(double)u0[gi], (double)u0[nxn + gi], (double)u0[2 * nxn + gi]};
+    const OhmAdj r = ohm_adj_point(Bm, Bp, (double)n0[gi], (double)n0[ipn], (double)n0[imn], u,
+                                   w.lE[gi], w.lE[nxn + gi], w.lE[2 * nxn + gi], ph);
+    P[0][k] = r.P[0] + w.lBb[nxn + gi];
+    P[1][k] = r.P[1] + w.lBb[2 * nxn + gi];
+    P[2][k] = r.P[2];
+    P[3][k] = r.P[3];
+    if (gi < c1 || gi == nx) {  // owned node
+      atomicAdd(&w.lNm[gi], r.ln);
+      if (r.lp != 0.0) {
+        atomicAdd(&w.lNm[ipn], r.lp);
+        atomicAdd(&w.lNm[imn], -r.lp);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w.lUm[c * nxn + gi] += r.lu[c];
+    }
+  }
+  __syncthreads();
+  for (int k = t0; k < c1 - c0; k += nt) {
+    const int gc = c0 + k;
+    const double Pc[4] = {P[0][k], P[1][k], P[2][k], P[3][k]};
+    const double Pc1[4] = {P[0][k + 1], P[1][k + 1], P[2][k + 1], P[3][k + 1]};
+    double ly, lz;
+    curl_adj_point(Pc, Pc1, gc == 0, gc == nx - 1, ph.idx, ly, lz);
+    w.lB[nx + gc] += ly;
+    w.lB[2 * nx + gc] += lz;
+  }
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -672,6 +1043,7 @@ namespace {
 constexpr size_t kAl = 256;
 inline size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 inline int blocks(long long n) { return (int)std::max<long long>(1, (n + kBlock - 1) / kBlock); }
+inline int tiles(int nx) { return (nx + kTbCells - 1) / kTbCells; }
 }  // namespace
 
 struct fs_window {
@@ -693,6 +1065,7 @@ struct fs_window {
   std::vector<int> ninj;
   std::vector<unsigned long long> first_id;
   bool have_forward = false;
+  int bsel = 0;  // which of the two B buffers holds the current field
   long long counts[5] = {0, 0, 0, 0, 0};  // of the last forward
 };
 
@@ -724,6 +1097,9 @@ int window_sizes(const fs_params* p, int steps, int ckpt, long long n_init, int 
                  Phys* ph, int* cap, size_t* total, size_t off[11]) {
   if (!p || steps < 1 || ckpt < 1 || n_init < 0 || M < 0 || M > 4096) return FS_EINVAL;
   if (p->dim != 1 || p->bc_x != FS_BC_FAUXSHOCK || p->c_light != 0.0) return FS_EINVAL;
+  // the blocked field kernels keep a tile's RK4 stage inputs in shared memory
+  const size_t tb = (p->precision == FS_FP64) ? 8 : 4;
+  if (p->n_sub < 1 || p->n_sub > 64 || rk4_adj_smem(p->n_sub, tb) > kMaxSmem) return FS_EINVAL;
   int rc = derive_geometry(p, g, ph);
   if (rc) return rc;
   std::vector<int> ninj;
@@ -745,13 +1121,12 @@ int window_sizes(const fs_params* p, int steps, int ckpt, long long n_init, int 
   off[3] = o; o += (size_t)K * al((size_t)*cap);                           // events
   off[4] = o; o += (size_t)(K + 1) * al(3 * tsz * nx);                     // B^n tape
   off[5] = o; o += (size_t)(K + 1) * mom_bytes(nxn, tsz);                  // moments tape
-  off[6] = o; o += 3 * al(3 * tsz * nxn) + 3 * al(3 * tsz * nx) + mom_bytes(nxn, tsz);
+  off[6] = o; o += 2 * al(3 * tsz * nxn) + 2 * al(3 * tsz * nx) + mom_bytes(nxn, tsz);
   off[7] = o; o += al(8 * 4 * (size_t)nxn);                                // fixed-point sums
   off[8] = o; o += al(8 * 8);                                              // counters
   off[9] = o;
   o += al(tsz * *cap) + al(3 * tsz * *cap);                                // lf, lv
-  o += 14 * al(8 * 3 * (size_t)(nx + nxn));                                // field adjoints
-  o += al(8 * (size_t)p->n_sub * 4 * 3 * nx);                              // stage inputs
+  o += 8 * al(8 * 3 * (size_t)(nx + nxn));                                 // field adjoints
   off[10] = o; o += al(8 * (size_t)(3 * M + 2));                           // amps, phases, grad
   *total = o;
   return FS_OK;
@@ -778,11 +1153,11 @@ Win<T> win_ptrs(fs_window* w) {
   size_t o = 0;
   auto take = [&](size_t bytes) { char* q = f + o; o += al(bytes); return q; };
   r.E = (T*)take(3 * sizeof(T) * nxn);
-  r.Es = (T*)take(3 * sizeof(T) * nxn);
   r.Bb = (T*)take(3 * sizeof(T) * nxn);
-  r.B = (T*)take(3 * sizeof(T) * nx);
-  r.Bs = (T*)take(3 * sizeof(T) * nx);
-  r.Bsum = (T*)take(3 * sizeof(T) * nx);
+  T* B0 = (T*)take(3 * sizeof(T) * nx);
+  T* B1 = (T*)take(3 * sizeof(T) * nx);
+  r.B = w->bsel ? B1 : B0;  // the current B
+  r.Bx = w->bsel ? B0 : B1;
   r.n = (T*)take(sizeof(T) * nxn);
   r.u = (T*)take(3 * sizeof(T) * nxn);
   r.nraw = (T*)take(sizeof(T) * nxn);
@@ -795,22 +1170,25 @@ Win<T> win_ptrs(fs_window* w) {
   r.lv = (T*)tka(3 * sizeof(T) * w->cap);
   const size_t fb = 8 * 3 * (size_t)(nx + nxn);
   r.lB = (double*)tka(fb);
+  r.lBx = (double*)tka(fb);
   r.lE = (double*)tka(fb);
   r.lBb = (double*)tka(fb);
-  r.lN = (double*)tka(fb);
-  r.lU = (double*)tka(fb);
   r.lNm = (double*)tka(fb);
   r.lUm = (double*)tka(fb);
   r.lNr = (double*)tka(fb);
   r.lJ = (double*)tka(fb);
-  r.P = (double*)tka(fb);
-  r.g = (double*)tka(fb);
-  r.lY = (double*)tka(fb);
-  r.lsum = (double*)tka(fb);
-  r.lend = (double*)tka(fb);
-  r.Y = (double*)tka(8 * (size_t)w->p.n_sub * 4 * 3 * nx);
   r.grad = (double*)(w->base + w->o_params) + 2 * w->M;
   return r;
+}
+
+// dynamic shared memory of the blocked field kernels beyond the default 48 KB
+template <typename T>
+bool smem_opt_in(int n_sub) {
+  const int f = (int)fields_smem(n_sub, sizeof(T)), a = (int)rk4_adj_smem(n_sub, sizeof(T));
+  return cudaFuncSetAttribute(k_win_fields<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, f) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(k_win_rk4_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, a) ==
+             cudaSuccess;
 }
 
 // checkpoint c: slots, B, moments
@@ -851,46 +1229,31 @@ void cpy(void* d, const void* s, size_t n, cudaStream_t st) {
   cudaMemcpyAsync(d, s, n, cudaMemcpyDeviceToDevice, st);
 }
 
-// RK4 substeps and the final Ohm of one step (the engine's kernels).
-template <typename T>
-void fields_step(fs_window* w, Win<T>& r) {
-  const int nx = w->g.nx, nxn = w->g.nxn;
-  const int gn = blocks(nxn), gc = blocks(nx);
-  for (int sub = 0; sub < w->p.n_sub; ++sub) {
-    for (int stage = 1; stage <= 4; ++stage) {
-      const T* Bin = (stage == 1) ? r.B : r.Bs;
-      k_ohm<T, 1><<<gn, kBlock, 0, w->st>>>(Bin, r.n, r.u, nullptr, r.Es, nullptr, nullptr, w->g,
-                                             w->ph);
-      k_faraday<T, 1><<<gc, kBlock, 0, w->st>>>(r.Es, r.B, r.Bs, r.Bsum, stage, w->g, w->ph);
-    }
-  }
-  k_ohm<T, 1><<<gn, kBlock, 0, w->st>>>(r.B, r.n, r.u, nullptr, r.E, r.Bb, nullptr, w->g, w->ph);
-}
-
 // one forward step n; with tape index k >= 0 the step's inputs are taped
 template <typename T>
 void forward_step(fs_window* w, Win<T>& r, int n, int k) {
   const int np = w->np_at[n];
   Slots<T> tp{};
   uint8_t* ev = nullptr;
+  T *tn = nullptr, *tu = nullptr, *tr = nullptr, *tB = nullptr;
   if (k >= 0) {
     tp = tape_at<T>(w, k);
     ev = ev_at(w, k);
-    cpy(tapeB_at<T>(w, k), r.B, 3 * sizeof(T) * w->g.nx, w->st);
+    tB = tapeB_at<T>(w, k);
+    mom_ptrs<T>(tapeM_at(w, k + 1), w->g.nxn, &tn, &tu, &tr);
   }
-  if (np > 0)
-    k_win_push<T><<<blocks(np), kBlock, 0, w->st>>>(r, tp, ev, w->g, w->ph, n, np);
   const int kinds = (w->ph.inject_thermal ? 1 : 0) + (w->ph.cr_enable ? 1 : 0);
   const int nadd = w->ninj[n] * kinds;
-  if (nadd > 0)
-    k_win_inject<T><<<blocks(nadd), kBlock, 0, w->st>>>(r, w->g, w->ph, n, np, w->ninj[n],
-                                                        w->first_id[n]);
+  const int ib = (nadd > 0) ? blocks(nadd) : 0;
+  const int pb = (np > 0) ? blocks(np) : 1;  // one block at least: it clears the sums
+  k_win_push_inject<T><<<ib + pb, kBlock, 0, w->st>>>(r, tp, ev, w->g, w->ph, n, np, w->ninj[n],
+                                                      w->first_id[n], ib);
   const int np1 = w->np_at[n + 1];
   if (np1 > 0) k_win_deposit<T><<<blocks(np1), kBlock, 0, w->st>>>(r, w->g, w->ph, np1);
-  T *tn = nullptr, *tu = nullptr, *tr = nullptr;
-  if (k >= 0) mom_ptrs<T>(tapeM_at(w, k + 1), w->g.nxn, &tn, &tu, &tr);
-  k_win_moments<T><<<blocks(w->g.nxn), kBlock, 0, w->st>>>(r, w->g, w->ph, tn, tu, tr);
-  fields_step<T>(w, r);
+  k_win_fields<T><<<tiles(w->g.nx), kTbThreads, fields_smem(w->p.n_sub, sizeof(T)), w->st>>>(
+      r, w->g, w->ph, w->p.n_sub, r.Bx, tn, tu, tr, tB);
+  std::swap(r.B, r.Bx);  // the step's B went to the other buffer
+  w->bsel ^= 1;
 }
 
 template <typename T>
@@ -940,18 +1303,17 @@ int do_forward(fs_window* w, const double* theta, double* loss) {
   cudaMemsetAsync(r.q, 0, 8 * 4 * (size_t)w->g.nxn, w->st);
   const int np0 = w->np_at[0];
   if (np0 > 0) k_win_deposit<T><<<blocks(np0), kBlock, 0, w->st>>>(r, w->g, w->ph, np0);
-  k_win_moments<T><<<blocks(w->g.nxn), kBlock, 0, w->st>>>(r, w->g, w->ph, nullptr, nullptr,
-                                                            nullptr);
+  k_win_moments<T><<<blocks(w->g.nxn), kBlock, 0, w->st>>>(r, w->g, w->ph);
   k_ohm<T, 1><<<blocks(w->g.nxn), kBlock, 0, w->st>>>(r.B, r.n, r.u, nullptr, r.E, r.Bb,
                                                        nullptr, w->g, w->ph);
   for (int n = 0; n < w->steps; ++n) {
     if (n % w->ckpt == 0) save_ckpt<T>(w, r, n / w->ckpt);
     forward_step<T>(w, r, n, -1);
   }
-  double* dl = r.lsum;  // scratch for the loss
+  double* dl = r.lBx;  // scratch for the loss (free outside the backward)
   cudaMemsetAsync(dl, 0, 8, w->st);
   k_win_loss<T><<<blocks(w->g.nx), kBlock, 0, w->st>>>(r.B, w->g, w->ph, w->loss_i0, w->p.dx,
-                                                       dl, nullptr);
+                                                       dl, nullptr, 1.0);
   unsigned long long c[5];
   if (cudaMemcpyAsync(loss, dl, 8, cudaMemcpyDeviceToHost, w->st) != cudaSuccess ||
       cudaMemcpyAsync(c, r.ctr, sizeof(c), cudaMemcpyDeviceToHost, w->st) != cudaSuccess ||
@@ -960,51 +1322,6 @@ int do_forward(fs_window* w, const double* theta, double* loss) {
   for (int k = 0; k < 5; ++k) w->counts[k] = (long long)c[k];
   w->have_forward = true;
   return FS_OK;
-}
-
-// Adjoint of one step's RK4 substeps (n, u frozen at the tape moments n1,
-// u1), from B^n: the stage inputs are recomputed with the engine's kernels;
-// on entry r.lB is the adjoint of B^{n+1}, on exit that of B^n; the moment
-// adjoints accumulate into r.lN, r.lU.
-template <typename T>
-void rk4_adjoint(fs_window* w, Win<T>& r, const T* Bn, const T* n1, const T* u1) {
-  const int nx = w->g.nx, nxn = w->g.nxn;
-  const int gn = blocks(nxn), gc = blocks(nx);
-  const double h = w->ph.h, hh = w->ph.hh, h6 = w->ph.h6;
-  const int ns = w->p.n_sub;
-  auto Yp = [&](int sub, int s) { return r.Y + ((size_t)sub * 4 + s) * 3 * nx; };
-  cpy(r.Bs, Bn, 3 * sizeof(T) * nx, w->st);
-  T* Bsub = r.Bs;    // start of the substep (advanced in place by stage 4)
-  T* Bst = r.Es;     // stage input (a node-sized buffer holds a centre field)
-  T* Ksum = r.Bsum;
-  T* Etmp = r.E;     // overwritten; E^n is recomputed after this
-  for (int sub = 0; sub < ns; ++sub) {
-    for (int stage = 1; stage <= 4; ++stage) {
-      const T* Bin = (stage == 1) ? Bsub : Bst;
-      k_win_to_double<T><<<blocks(3 * nx), kBlock, 0, w->st>>>(Yp(sub, stage - 1), Bin, 3 * nx);
-      k_ohm<T, 1><<<gn, kBlock, 0, w->st>>>(Bin, n1, u1, nullptr, Etmp, nullptr, nullptr, w->g,
-                                             w->ph);
-      k_faraday<T, 1><<<gc, kBlock, 0, w->st>>>(Etmp, Bsub, Bst, Ksum, stage, w->g, w->ph);
-    }
-  }
-  for (int sub = ns - 1; sub >= 0; --sub) {
-    cpy(r.lend, r.lB, 8 * 3 * nx, w->st);
-    cpy(r.lsum, r.lB, 8 * 3 * nx, w->st);  // lambda_start = lambda_end + sum lambda_Y
-    // g4 = h6 lend; then g3 = 2 h6 lend + h lY4, g2 = 2 h6 lend + hh lY3,
-    // g1 = h6 lend + hh lY2
-    k_win_axpy<<<blocks(3 * nx), kBlock, 0, w->st>>>(r.g, r.lend, h6, nullptr, 0.0, 3 * nx);
-    const double an[3] = {2 * h6, 2 * h6, h6};
-    const double bn[3] = {h, hh, hh};
-    for (int s = 3; s >= 0; --s) {
-      k_win_ohm_adj<T><<<gn, kBlock, 0, w->st>>>(Yp(sub, s), n1, u1, r.g, nullptr, nullptr, r.P,
-                                                  r.lN, r.lU, w->g, w->ph);
-      const int q = 3 - s;
-      k_win_curl_adj<<<gc, kBlock, 0, w->st>>>(r.P, r.lY, r.lsum, s > 0 ? r.g : nullptr, r.lend,
-                                               s > 0 ? an[q] : 0.0, s > 0 ? bn[q] : 0.0, w->g,
-                                               w->ph);
-    }
-    cpy(r.lB, r.lsum, 8 * 3 * nx, w->st);
-  }
 }
 
 template <typename T>
@@ -1020,8 +1337,7 @@ int do_backward(fs_window* w, double dloss, double* grad) {
   cudaMemsetAsync(r.lUm, 0, fb, w->st);
   // d loss / d B at the end (r.B holds the final field after the forward)
   k_win_loss<T><<<blocks(nx), kBlock, 0, w->st>>>(r.B, w->g, w->ph, w->loss_i0, w->p.dx,
-                                                  nullptr, r.lB);
-  k_win_axpy<<<blocks(3 * nx), kBlock, 0, w->st>>>(r.lB, r.lB, dloss, nullptr, 0.0, 3 * nx);
+                                                  nullptr, r.lB, dloss);
   for (int seg = w->nseg - 1; seg >= 0; --seg) {
     const int n0 = seg * w->ckpt;
     const int n1 = std::min(w->steps, n0 + w->ckpt);
@@ -1046,29 +1362,18 @@ int do_backward(fs_window* w, double dloss, double* grad) {
       T *mn1, *mu1, *mr1, *mn0, *mu0, *mr0;
       mom_ptrs<T>(tapeM_at(w, k + 1), nxn, &mn1, &mu1, &mr1);
       mom_ptrs<T>(tapeM_at(w, k), nxn, &mn0, &mu0, &mr0);
-      // lN, lU: adjoint of the moments M^{n+1}, starting from what E^{n+1} added
-      cpy(r.lN, r.lNm, fb, w->st);
-      cpy(r.lU, r.lUm, fb, w->st);
-      rk4_adjoint<T>(w, r, tapeB_at<T>(w, k), mn1, mu1);
-      k_win_moments_adj<T><<<blocks(nxn), kBlock, 0, w->st>>>(mn1, mu1, mr1, r.lN, r.lU, r.lNr,
-                                                              r.lJ, w->g, w->ph);
-      // E^n, Bbar^n from B^n and M^n, as the forward had them
-      k_ohm<T, 1><<<blocks(nxn), kBlock, 0, w->st>>>(tapeB_at<T>(w, k), mn0, mu0, nullptr, r.E,
-                                                     r.Bb, nullptr, w->g, w->ph);
-      cudaMemsetAsync(r.lE, 0, fb, w->st);
-      cudaMemsetAsync(r.lBb, 0, fb, w->st);
+      const T* Bn = tapeB_at<T>(w, k);
+      // the step's field update and moments in reverse; E^n, Bbar^n as the
+      // forward had them
+      k_win_rk4_adj<T><<<tiles(w->g.nx), kTbThreads, rk4_adj_smem(w->p.n_sub, sizeof(T)), w->st>>>(
+          r, w->g, w->ph, w->p.n_sub, Bn, mn1, mu1, mr1, mn0, mu0, r.lB, r.lBx);
+      std::swap(r.lB, r.lBx);
       const int npa = w->np_at[n], npb = w->np_at[n + 1];
       if (npb > 0)
         k_win_particle_adj<T><<<blocks(npb), kBlock, 0, w->st>>>(
             r, tape_at<T>(w, k), tape_at<T>(w, k + 1), ev_at(w, k), w->g, w->ph, n, npa, npb, M);
       // Ohm at the start of the step: lB += ..., lNm, lUm = adjoint of M^n
-      cudaMemsetAsync(r.lNm, 0, fb, w->st);
-      cudaMemsetAsync(r.lUm, 0, fb, w->st);
-      k_win_to_double<T><<<blocks(3 * nx), kBlock, 0, w->st>>>(r.Y, tapeB_at<T>(w, k), 3 * nx);
-      k_win_ohm_adj<T><<<blocks(nxn), kBlock, 0, w->st>>>(r.Y, mn0, mu0, nullptr, r.lE, r.lBb,
-                                                          r.P, r.lNm, r.lUm, w->g, w->ph);
-      k_win_curl_adj<<<blocks(nx), kBlock, 0, w->st>>>(r.P, r.lY, r.lB, nullptr, nullptr, 0.0,
-                                                       0.0, w->g, w->ph);
+      k_win_ohm_adj_step<T><<<tiles(w->g.nx), kTbThreads, 0, w->st>>>(r, w->g, w->ph, Bn, mn0, mu0);
     }
   }
   double* phases = (double*)(w->base + w->o_params) + M;
@@ -1167,7 +1472,8 @@ int fs_window_init(const fs_params* p, int steps, int ckpt_every, long long n_in
     }
   }
   Ck c0 = ckpt_at(w, 0);
-  bool ok = cudaMemcpyAsync(c0.slots, host.data(), host.size(), cudaMemcpyHostToDevice, w->st) ==
+  bool ok = (tsz == 8 ? smem_opt_in<double>(p->n_sub) : smem_opt_in<float>(p->n_sub)) &&
+            cudaMemcpyAsync(c0.slots, host.data(), host.size(), cudaMemcpyHostToDevice, w->st) ==
                 cudaSuccess &&
             (n_modes == 0 ||
              cudaMemcpyAsync(w->base + w->o_params + 8 * (size_t)n_modes, mode_phase,
