@@ -23,7 +23,6 @@
 namespace fsx {
 namespace win {
 
-constexpr double kFix = 1099511627776.0;  // 2^40
 constexpr double kUnfix = 1.0 / 1099511627776.0;
 enum : uint8_t { kEvNone = 0, kEvReturned = 1, kEvRemoved = 2 };
 
@@ -229,8 +228,27 @@ __global__ void k_win_push_inject(Win<T> w, Slots<T> tape, uint8_t* ev, Geo g, P
     push_slot<T>(p, w, tape, ev, g, ph, step);
 }
 
+// c * 2^40 rounded to the nearest integer, ties to even (the value of
+// __double2ll_rn(c * 2^40) for |c| < 2^23), on the bit pattern with integer
+// operations: the significand shifted right by 1035 - e with the rounding
+// of the bits shifted out, kept off the FP64 pipe.
 __device__ __forceinline__ unsigned long long fix(double c) {
-  return (unsigned long long)__double2ll_rn(c * kFix);
+  const long long b = __double_as_longlong(c);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const long long mant = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  const int sh = 1035 - e;
+  long long r;
+  if (e == 0 || sh > 53) {
+    r = 0;  // zero, subnormal, or |c| 2^40 < 1/2
+  } else if (sh <= 0) {
+    r = mant << (-sh);
+  } else {
+    const long long q = mant >> sh;
+    const long long rem = mant - (q << sh);
+    const long long half = 1LL << (sh - 1);
+    r = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+  }
+  return (unsigned long long)(b < 0 ? -r : r);
 }
 
 // Sum of v over the lanes of `mask` (all of which call it with that mask),
@@ -345,12 +363,14 @@ __global__ void k_win_seed_B(T* B, Geo g, Phys ph, double dx, const double* amps
 }
 
 // loss = sum_{i >= i0} |B_perp - B0_perp|^2 dx (into *out), and its
-// gradient with respect to B times `scale` (into lB) when lB is given
+// gradient with respect to B times `scale` (into lB) when lB is given. One
+// CTA: the sum is taken in a fixed order, so the loss is reproducible.
 template <typename T>
-__global__ void k_win_loss(const T* B, Geo g, Phys ph, int i0, double dx, double* out,
-                           double* lB, double scale) {
+__global__ void __launch_bounds__(kBlock) k_win_loss(const T* B, Geo g, Phys ph, int i0, double dx,
+                                                     double* out, double* lB, double scale) {
+  __shared__ double red[kBlock / 32];
   double s = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
     double dy = 0.0, dz = 0.0;
     if (i >= i0) {
       dy = (double)B[g.nx + i] - ph.b0y;
@@ -364,7 +384,13 @@ __global__ void k_win_loss(const T* B, Geo g, Phys ph, int i0, double dx, double
     }
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0 && out) atomicAdd(out, s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0 && out) {
+    double tot = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += red[k];
+    *out = tot;
+  }
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -828,26 +854,33 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Adjoint of one step for every slot p < np1 (slots alive at the end of the
-// step or born in it). In: lf, lv = adjoints of the state after the step;
+// Adjoint of one step for slot p < np1 (alive at the end of the step or born
+// in it). In: lf, lv = adjoints of the state after the step;
 // lNr, lJ = adjoints of the step's deposit; E, Bb = the node fields the
 // step's gather used. Out: lf, lv = adjoints of the state before the step
-// (zero for slots born or removed in it); lE, lBb (atomics); grad[M] (u_cr),
-// grad[M + 1] (u2).
+// (zero for slots born or removed in it); the slot's shares of lE, lBb at
+// the nodes c0, c0 + 1 (out; returns c0, or -1 when it has none); its terms
+// of grad[M] (u_cr, into gucr) and grad[M + 1] (u2, into gu2). The
+// deposit's adjoint, the injection's and the faux-shock
+// return's are taken in FP64; the push's (Boris, gather) in the run's
+// precision, that of the per-slot adjoints lf, lv; the sums into lE, lBb and
+// the gradient are FP64.
 template <typename T>
-__global__ void k_win_particle_adj(Win<T> w, Slots<T> t0, Slots<T> t1, const uint8_t* ev,
-                                   Geo g, Phys ph, long long step, int np0, int np1, int M) {
+__device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const Slots<T>& t0,
+                                                 const Slots<T>& t1, const uint8_t* ev,
+                                                 const Geo& g, const Phys& ph, long long step,
+                                                 int np0, double& gu2, double& gucr, T out[12]) {
+  using A = T;  // arithmetic of the push's adjoint
   const int nxn = g.nxn;
   const int cap = w.cap;
-  double gu2 = 0.0, gucr = 0.0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np1; p += gridDim.x * blockDim.x) {
+  {
     const bool born = p >= np0;
     const uint8_t e = born ? (uint8_t)kEvNone : ev[p];
     const int c1 = t1.ci[p];
     if (c1 < 0 || (!born && t0.ci[p] < 0) || e == kEvRemoved) {
       w.lf[p] = (T)0;
       w.lv[p] = w.lv[cap + p] = w.lv[2 * cap + p] = (T)0;
-      continue;
+      return -1;
     }
     // ---- deposit at the state after the step
     const uint32_t id = w.s.id[p];
@@ -881,28 +914,28 @@ __global__ void k_win_particle_adj(Win<T> w, Slots<T> t0, Slots<T> t1, const uin
       }
       w.lf[p] = (T)0;
       w.lv[p] = w.lv[cap + p] = w.lv[2 * cap + p] = (T)0;
-      continue;
+      return -1;
     }
     // ---- recompute the push from the state before the step
     const int c0 = t0.ci[p];
-    const double f0 = (double)t0.f[p];
+    const A f0 = (A)t0.f[p];
     const T ft0 = t0.f[p];
     const T g0t = (T)1 - ft0;
     T Ep[3], Bp[3];
-    double Ed[3], Bd[3];
+    A Ed[3], Bd[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       Ep[c] = fmaT(ft0, w.E[c * nxn + c0 + 1], g0t * w.E[c * nxn + c0]);
       Bp[c] = fmaT(ft0, w.Bb[c * nxn + c0 + 1], g0t * w.Bb[c * nxn + c0]);
-      Ed[c] = (double)w.E[c * nxn + c0 + 1] - (double)w.E[c * nxn + c0];
-      Bd[c] = (double)w.Bb[c * nxn + c0 + 1] - (double)w.Bb[c * nxn + c0];
+      Ed[c] = (A)w.E[c * nxn + c0 + 1] - (A)w.E[c * nxn + c0];
+      Bd[c] = (A)w.Bb[c * nxn + c0 + 1] - (A)w.Bb[c * nxn + c0];
     }
-    const double v0[3] = {(double)t0.v[p], (double)t0.v[cap + p], (double)t0.v[2 * cap + p]};
+    const A v0[3] = {(A)t0.v[p], (A)t0.v[cap + p], (A)t0.v[2 * cap + p]};
     T vxt = t0.v[p], vyt = t0.v[cap + p], vzt = t0.v[2 * cap + p];
     boris<T>(vxt, vyt, vzt, Ep, Bp, (T)ph.hdt);
-    const double vp[3] = {(double)vxt, (double)vyt, (double)vzt};  // before the return
-    double lvp[3];  // adjoint of vp
-    double lf0;
+    const A vp[3] = {(A)vxt, (A)vyt, (A)vzt};  // before the return
+    A lvp[3];  // adjoint of vp
+    A lf0;
     if (e == kEvReturned) {
       // vnew = R(vp; u2), f1 = clamp(gf * vnew_x * dtdx), gf = Xn/(Xn - Xo)
       const Philox4 r = draw4(ph.seed, id & kIdMask, step, kPurposeFS);
@@ -910,14 +943,14 @@ __global__ void k_win_particle_adj(Win<T> w, Slots<T> t0, Slots<T> t1, const uin
       double cs, sn2;
       fs_sincos2pi(u01(r.x[2]), &cs, &sn2);
       const double u2 = ph.u2;
-      const double wx = vp[0] + u2;
-      const double wv = sqrt(wx * wx + vp[1] * vp[1] + vp[2] * vp[2]);
+      const double wx = (double)vp[0] + u2;
+      const double wv = sqrt(wx * wx + (double)vp[1] * vp[1] + (double)vp[2] * vp[2]);
       const double a = u2 / wv;
       const double mu = a + (1.0 - a) * s1;
       const double snm = sqrt(fmax(1.0 - mu * mu, 0.0));
       const double vnx = wv * mu - u2;
-      const double av = vp[0] * ph.dtdx;  // Xn - Xo
-      const double Xo = (double)c0 + f0;
+      const double av = (double)vp[0] * ph.dtdx;  // Xn - Xo
+      const double Xo = (double)c0 + (double)f0;
       const double gf = (Xo + av) / av;
       const double fraw = gf * vnx * ph.dtdx;
       double Lx = lv[0], Ly = lv[1], Lz = lv[2];
@@ -937,66 +970,121 @@ __global__ void k_win_particle_adj(Win<T> w, Slots<T> t0, Slots<T> t1, const uin
       double Lu2 = -Lx + La / wv;
       Lu2 += Lw * wx / wv;
       gu2 += Lu2;
-      lvp[0] = Lw * wx / wv + lav * ph.dtdx;
-      lvp[1] = Lw * vp[1] / wv;
-      lvp[2] = Lw * vp[2] / wv;
-      lf0 = lXo;
+      lvp[0] = (A)(Lw * wx / wv + lav * ph.dtdx);
+      lvp[1] = (A)(Lw * vp[1] / wv);
+      lvp[2] = (A)(Lw * vp[2] / wv);
+      lf0 = (A)lXo;
     } else {
-      lvp[0] = lv[0] + lf1 * ph.dtdx;
-      lvp[1] = lv[1];
-      lvp[2] = lv[2];
-      lf0 = lf1;
+      lvp[0] = (A)(lv[0] + lf1 * ph.dtdx);
+      lvp[1] = (A)lv[1];
+      lvp[2] = (A)lv[2];
+      lf0 = (A)lf1;
     }
     // ---- Boris adjoint: v+ = q + em, q = vm + p x s, p = vm + vm x t,
     //      s = (2 / (1 + t.t)) t, t = hdt B, vm = v + em, em = hdt E
-    const double hdt = ph.hdt;
-    double em[3], vm[3], t[3], sv[3], pp[3];
+    const A hdt = (A)ph.hdt;
+    A em[3], vm[3], t[3], sv[3], pp[3];
     for (int c = 0; c < 3; ++c) {
-      em[c] = hdt * (double)Ep[c];
+      em[c] = hdt * (A)Ep[c];
       vm[c] = v0[c] + em[c];
-      t[c] = hdt * (double)Bp[c];
+      t[c] = hdt * (A)Bp[c];
     }
-    const double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-    const double fct = 2.0 / (1.0 + tt);
+    const A tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const A fct = (A)2 / ((A)1 + tt);
     for (int c = 0; c < 3; ++c) sv[c] = fct * t[c];
     pp[0] = vm[0] + (vm[1] * t[2] - vm[2] * t[1]);
     pp[1] = vm[1] + (vm[2] * t[0] - vm[0] * t[2]);
     pp[2] = vm[2] + (vm[0] * t[1] - vm[1] * t[0]);
-    const double* Lq = lvp;
-    double Lem[3] = {lvp[0], lvp[1], lvp[2]};
-    double Lvm[3] = {Lq[0], Lq[1], Lq[2]};
+    const A* Lq = lvp;
+    A Lem[3] = {lvp[0], lvp[1], lvp[2]};
+    A Lvm[3] = {Lq[0], Lq[1], Lq[2]};
     // q = vm + p x s: L_p = s x L_q, L_s = L_q x p
-    const double Lp[3] = {sv[1] * Lq[2] - sv[2] * Lq[1], sv[2] * Lq[0] - sv[0] * Lq[2],
+    const A Lp[3] = {sv[1] * Lq[2] - sv[2] * Lq[1], sv[2] * Lq[0] - sv[0] * Lq[2],
                           sv[0] * Lq[1] - sv[1] * Lq[0]};
-    const double Ls[3] = {Lq[1] * pp[2] - Lq[2] * pp[1], Lq[2] * pp[0] - Lq[0] * pp[2],
+    const A Ls[3] = {Lq[1] * pp[2] - Lq[2] * pp[1], Lq[2] * pp[0] - Lq[0] * pp[2],
                           Lq[0] * pp[1] - Lq[1] * pp[0]};
     // p = vm + vm x t: L_vm += L_p + t x L_p, L_t = L_p x vm
     Lvm[0] += Lp[0] + (t[1] * Lp[2] - t[2] * Lp[1]);
     Lvm[1] += Lp[1] + (t[2] * Lp[0] - t[0] * Lp[2]);
     Lvm[2] += Lp[2] + (t[0] * Lp[1] - t[1] * Lp[0]);
-    double Lt[3] = {Lp[1] * vm[2] - Lp[2] * vm[1], Lp[2] * vm[0] - Lp[0] * vm[2],
+    A Lt[3] = {Lp[1] * vm[2] - Lp[2] * vm[1], Lp[2] * vm[0] - Lp[0] * vm[2],
                     Lp[0] * vm[1] - Lp[1] * vm[0]};
     // s = fct t, fct = 2 / (1 + tt)
-    const double Lf = Ls[0] * t[0] + Ls[1] * t[1] + Ls[2] * t[2];
-    const double Ltt = -Lf * fct * fct * 0.5;
+    const A Lf = Ls[0] * t[0] + Ls[1] * t[1] + Ls[2] * t[2];
+    const A Ltt = -Lf * fct * fct * (A)0.5;
     for (int c = 0; c < 3; ++c) {
-      Lt[c] += fct * Ls[c] + 2.0 * Ltt * t[c];
+      Lt[c] += fct * Ls[c] + (A)2 * Ltt * t[c];
       Lem[c] += Lvm[c];
     }
-    const double LE[3] = {hdt * Lem[0], hdt * Lem[1], hdt * Lem[2]};
-    const double LB[3] = {hdt * Lt[0], hdt * Lt[1], hdt * Lt[2]};
-    // ---- gather adjoint at the state before the step
+    const A LE[3] = {hdt * Lem[0], hdt * Lem[1], hdt * Lem[2]};
+    const A LB[3] = {hdt * Lt[0], hdt * Lt[1], hdt * Lt[2]};
+    // ---- gather adjoint at the state before the step: the shares of the
+    //      nodes c0, c0 + 1 in lE, lBb go to the caller
     for (int c = 0; c < 3; ++c) {
-      atomicAdd(&w.lE[c * nxn + c0], (1.0 - f0) * LE[c]);
-      atomicAdd(&w.lE[c * nxn + c0 + 1], f0 * LE[c]);
-      atomicAdd(&w.lBb[c * nxn + c0], (1.0 - f0) * LB[c]);
-      atomicAdd(&w.lBb[c * nxn + c0 + 1], f0 * LB[c]);
+      out[4 * c] = ((A)1 - f0) * LE[c];
+      out[4 * c + 1] = f0 * LE[c];
+      out[4 * c + 2] = ((A)1 - f0) * LB[c];
+      out[4 * c + 3] = f0 * LB[c];
       lf0 += LE[c] * Ed[c] + LB[c] * Bd[c];
     }
     w.lf[p] = (T)lf0;
     w.lv[p] = (T)Lvm[0];
     w.lv[cap + p] = (T)Lvm[1];
     w.lv[2 * cap + p] = (T)Lvm[2];
+    return c0;
+  }
+}
+
+// Adds one slot's shares (out of particle_adj_slot) to lE, lBb at c0, c0 + 1.
+template <typename T>
+__device__ __forceinline__ void add_node_shares(const Win<T>& w, int nxn, int c0, const T a[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    atomicAdd(&w.lE[c * nxn + c0], (double)a[4 * c]);
+    atomicAdd(&w.lE[c * nxn + c0 + 1], (double)a[4 * c + 1]);
+    atomicAdd(&w.lBb[c * nxn + c0], (double)a[4 * c + 2]);
+    atomicAdd(&w.lBb[c * nxn + c0 + 1], (double)a[4 * c + 3]);
+  }
+}
+// Adjoint of one step for every slot p < np1 (slots alive at the end of the
+// step or born in it): particle_adj_slot per slot. In the FP32 run the lanes
+// of a warp whose slots sit in at most 4 cells first add the shares of each
+// cell (slots in birth order share cells), so that one lane per cell issues
+// its atomics; otherwise every lane issues its own.
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 4)
+    k_win_particle_adj(Win<T> w, Slots<T> t0, Slots<T> t1, const uint8_t* ev, Geo g, Phys ph,
+                       long long step, int np0, int np1, int M) {
+  const int nxn = g.nxn;
+  const int lane = threadIdx.x & 31;
+  double gu2 = 0.0, gucr = 0.0;
+  for (int base = blockIdx.x * blockDim.x + threadIdx.x - lane; base < np1;
+       base += gridDim.x * blockDim.x) {
+    const int p = base + lane;
+    T a[12];
+    const int c0 =
+        (p < np1) ? particle_adj_slot<T>(p, w, t0, t1, ev, g, ph, step, np0, gu2, gucr, a) : -1;
+    if (sizeof(T) == 4) {
+      const unsigned grp = __match_any_sync(0xffffffffu, c0);
+      const bool lead = c0 >= 0 && lane == __ffs(grp) - 1;
+      unsigned leads = __ballot_sync(0xffffffffu, lead);
+      if (__popc(leads) <= 4) {
+        while (leads) {
+          const int l = __ffs(leads) - 1;
+          leads &= leads - 1;
+          const int key = __shfl_sync(0xffffffffu, c0, l);
+          T s[12];
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            s[k] = (c0 == key) ? a[k] : (T)0;
+            for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+          }
+          if (lane == l) add_node_shares<T>(w, nxn, key, s);
+        }
+        continue;
+      }
+    }
+    if (c0 >= 0) add_node_shares<T>(w, nxn, c0, a);
   }
   gu2 = warp_sum_d(gu2);
   gucr = warp_sum_d(gucr);
@@ -1311,8 +1399,7 @@ int do_forward(fs_window* w, const double* theta, double* loss) {
     forward_step<T>(w, r, n, -1);
   }
   double* dl = r.lBx;  // scratch for the loss (free outside the backward)
-  cudaMemsetAsync(dl, 0, 8, w->st);
-  k_win_loss<T><<<blocks(w->g.nx), kBlock, 0, w->st>>>(r.B, w->g, w->ph, w->loss_i0, w->p.dx,
+  k_win_loss<T><<<1, kBlock, 0, w->st>>>(r.B, w->g, w->ph, w->loss_i0, w->p.dx,
                                                        dl, nullptr, 1.0);
   unsigned long long c[5];
   if (cudaMemcpyAsync(loss, dl, 8, cudaMemcpyDeviceToHost, w->st) != cudaSuccess ||
@@ -1336,7 +1423,7 @@ int do_backward(fs_window* w, double dloss, double* grad) {
   cudaMemsetAsync(r.lNm, 0, fb, w->st);
   cudaMemsetAsync(r.lUm, 0, fb, w->st);
   // d loss / d B at the end (r.B holds the final field after the forward)
-  k_win_loss<T><<<blocks(nx), kBlock, 0, w->st>>>(r.B, w->g, w->ph, w->loss_i0, w->p.dx,
+  k_win_loss<T><<<1, kBlock, 0, w->st>>>(r.B, w->g, w->ph, w->loss_i0, w->p.dx,
                                                   nullptr, r.lB, dloss);
   for (int seg = w->nseg - 1; seg >= 0; --seg) {
     const int n0 = seg * w->ckpt;
