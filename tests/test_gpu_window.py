@@ -148,3 +148,33 @@ def test_fp32_window_gradient_tracks_fp64(fsw, full_fp64):
     assert np.abs(g32[:16] - g64[:16]).max() <= 2e-2 * gm
     assert g32[17] == pytest.approx(g64[17], rel=5e-2)
     w.close()
+
+
+@pytest.mark.parametrize("nx,n_sub", [(40, 2), (72, 1), (88, 3)])
+def test_ragged_tiles_and_substeps_match_the_oracle(fsw, nx, n_sub):
+    """The field kernels work on 16-cell tiles with halos of 4 n_sub + 2
+    (forward) and 8 n_sub + 3 (reverse) cells: grids that end in a partial
+    tile, with one to three RK4 substeps per step, against the oracle."""
+    from oracle import window as wo
+    X, V = WI.plasma(nx, 8)
+    amps, ph = WI.modes()
+    th = WI.theta(amps)
+    spec = wo.WindowSpec(nx=nx, ppc=8, X0=X, V0=V, phases=ph, n_sub=n_sub, **WI.COMMON)
+    L0, g0, win = wo.loss_and_grad(spec, th, 100)
+    w = fsw.FauxShockWindow(X, V, ph, steps=100, ckpt=20, nx=nx, ny=1, ppc=8, n_sub=n_sub,
+                            precision=0, cr_enable=1, fs_mode_thermal=1, p_iso=100.0,
+                            n_cr_ratio=0.01, **WI.COMMON)
+    L, g = w.loss_and_grad(th)
+    assert w.counts() == win.counts
+    assert L == pytest.approx(L0, rel=1e-9)
+    gm = np.abs(g0[:16]).max()
+    np.testing.assert_allclose(g[:16], g0[:16], rtol=0, atol=1e-6 * gm)
+    assert g[16] == pytest.approx(g0[16], rel=1e-5)
+    assert g[17] == pytest.approx(g0[17], rel=1e-6)
+    # the FP32 window on the same ragged grid tracks it
+    w32 = fsw.FauxShockWindow(X, V, ph, steps=100, ckpt=20, nx=nx, ny=1, ppc=8, n_sub=n_sub,
+                              precision=1, cr_enable=1, fs_mode_thermal=1, p_iso=100.0,
+                              n_cr_ratio=0.01, **WI.COMMON)
+    L32, g32 = w32.loss_and_grad(th)
+    assert L32 == pytest.approx(L0, rel=1e-3)
+    assert np.abs(g32[:16] - g0[:16]).max() <= 2e-2 * gm
