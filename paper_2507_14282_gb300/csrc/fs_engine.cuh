@@ -859,6 +859,212 @@ __global__ void k_faraday(const T* __restrict__ En, T* __restrict__ B,
 }
 
 // ------------------------------------------------------------------------
+// One RK4 substep of the 2D field advance by tiles, for boxes with x walls
+// (as separate passes it is memory-bound in FP32: each stage's Ohm and
+// Faraday re-read and re-write the grid). A CTA owns kFTX x kFTY cells (and
+// their lower-left nodes; the last tile in x also the wall nodes nx) and
+// runs the four stages in shared memory over its cells plus a halo of 4
+// cells (5 when it also forms E), which it recomputes: a stage's stencils reach one cell (node (i, j) reads
+// cells i-1..i, j-1..j and n at i±1, j±1; cell (i, j) reads nodes i..i+1,
+// j..j+1), so values made wrong at a tile's inner edges (read there with
+// indices clamped to the tile) move in by one cell per pass and stay outside
+// the owned cells. At an x wall the tile ends at the wall, where the clamped
+// indices are the wall's zero-gradient ghost cells and the density is
+// mirrored as in density_terms; y is periodic (rows wrap when loaded).
+// Reads B from Bin and writes the new B to Bout (neighbouring tiles read
+// Bin's cells). With `fin`, also Ohm's E and Bbar at the owned nodes from
+// the new B (Eo, Bbo, and the packed gather block G with its ghost row), as
+// the step's final k_ohm does. Same per-element arithmetic as ohm_node /
+// faraday_cell (2D).
+constexpr int kFTX = 32, kFTY = 16, kFH = 5;  // owned cells; halo of the last substep
+constexpr int kFLX = kFTX + 2 * kFH, kFLY = kFTY + 2 * kFH;
+constexpr int kFNPT = ((kFLX + 1) * (kFLY + 1) + kBlock - 1) / kBlock;  // nodes per thread
+template <typename T>
+constexpr size_t field_tile_smem() {
+  return sizeof(T) * (9 * (size_t)kFLX * kFLY + 4 * (size_t)(kFLX + 1) * (kFLY + 1));
+}
+
+// Walks the elements k = t0, t0 + kBlock, ... of an nx-by-ny local array,
+// keeping (a, b) = (k mod nx, k div nx) by increments.
+struct TileWalk {
+  int k, a, b, da, db, n, w;
+  __device__ __forceinline__ TileWalk(int t0, int w_, int h_) : k(t0), n(w_ * h_), w(w_) {
+    b = t0 / w_;
+    a = t0 - b * w_;
+    db = kBlock / w_;
+    da = kBlock - db * w_;
+  }
+  __device__ __forceinline__ void next() {
+    k += kBlock;
+    a += da;
+    b += db;
+    if (a >= w) {
+      a -= w;
+      ++b;
+    }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+    k_field_substep2(const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ nN,
+                     const T* __restrict__ uN, T* __restrict__ Eo, T* __restrict__ Bbo,
+                     T* __restrict__ G, Geo g, Phys ph, int fin) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nx = g.nx, ny = g.ny, nxn = g.nxn;
+  const int nc = nx * ny, nn = nxn * ny;
+  const int H = fin ? kFH : kFH - 1;  // four stages need 4 cells, the final Ohm one more
+  const int cx0 = blockIdx.x * kFTX, cx1 = min(nx, cx0 + kFTX);
+  const int cy0 = blockIdx.y * kFTY, cy1 = min(ny, cy0 + kFTY);
+  const int lx0 = max(0, cx0 - H), LX = min(nx, cx1 + H) - lx0;  // local cell columns
+  const int ly0 = cy0 - H, LY = (cy1 - cy0) + 2 * H;             // local rows (unwrapped)
+  const int NX = LX + 1, NC = LX * LY, NN = NX * (LY + 1);        // nodes: NX x (LY + 1)
+  T* sB = (T*)smem;
+  T* sBs = sB + 3 * NC;
+  T* sK = sBs + 3 * NC;
+  T* sE = sK + 3 * NC;  // [3][NN]
+  T* sn = sE + 3 * NN;  // [NN]
+  const int t0 = threadIdx.x;
+  auto row = [&](int b) { return wrap(ly0 + b, ny); };
+  for (TileWalk w(t0, LX, 3 * LY); w.k < 3 * NC; w.next()) {
+    const int c = w.b / LY, b = w.b - c * LY;
+    sB[w.k] = Bin[(size_t)c * nc + (size_t)row(b) * nx + lx0 + w.a];
+  }
+  // this thread's nodes: u and (after the barrier) the density terms, fixed
+  // for the substep, stay in registers
+  T u[kFNPT][3], inv_n[kFNPT], pgx[kFNPT], pgy[kFNPT];
+  {
+    TileWalk w(t0, NX, LY + 1);
+#pragma unroll
+    for (int r = 0; r < kFNPT; ++r, w.next()) {
+      if (w.k < NN) {
+        const size_t q = (size_t)row(w.b) * nxn + lx0 + w.a;
+        sn[w.k] = nN[q];
+        u[r][0] = uN[q];
+        u[r][1] = uN[nn + q];
+        u[r][2] = uN[2 * nn + q];
+      }
+    }
+  }
+  __syncthreads();
+  const T hdx = (T)ph.hdx, hdy = (T)ph.hdy, te = (T)ph.te;
+  const T jcr = (T)ph.jcr, eta = (T)ph.eta;
+  const bool resist = ph.eta != 0.0;
+  {
+    TileWalk w(t0, NX, LY + 1);
+#pragma unroll
+    for (int r = 0; r < kFNPT; ++r, w.next()) {
+      if (w.k < NN) {
+        // x neighbours mirrored at the walls, y neighbours in the tile
+        const int gx = lx0 + w.a;
+        const int xp = ((gx + 1 > nx) ? 2 * nx - (gx + 1) : gx + 1) - lx0;
+        const int xm = ((gx - 1 < 0) ? -(gx - 1) : gx - 1) - lx0;
+        const int rb = w.b * NX;
+        const T dnx = (sn[rb + min(max(xp, 0), LX)] - sn[rb + min(max(xm, 0), LX)]) * hdx;
+        const T dny = (sn[min(w.b + 1, LY) * NX + w.a] - sn[max(w.b - 1, 0) * NX + w.a]) * hdy;
+        inv_n[r] = (T)1 / sn[w.k];
+        pgx[r] = -(te * dnx);
+        pgy[r] = -(te * dny);
+      }
+    }
+  }
+  // Ohm at local node (a, b), the r-th of this thread, from the centre field Bc
+  auto ohm = [&](const T* Bc, int a, int b, int r, T E[3], T Bb[3]) {
+    const int im = min(max(a - 1, 0), LX - 1), ip = min(a, LX - 1);
+    const int jm = min(max(b - 1, 0), LY - 1), jp = min(b, LY - 1);
+    const int cmm = jm * LX + im, cpm = jm * LX + ip, cmp = jp * LX + im, cpp = jp * LX + ip;
+    T v[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c][0] = Bc[c * NC + cmm];
+      v[c][1] = Bc[c * NC + cpm];
+      v[c][2] = Bc[c * NC + cmp];
+      v[c][3] = Bc[c * NC + cpp];
+    }
+    Bb[0] = (T)0.25 * ((v[0][0] + v[0][1]) + (v[0][2] + v[0][3]));
+    Bb[1] = (T)0.25 * ((v[1][0] + v[1][1]) + (v[1][2] + v[1][3]));
+    Bb[2] = (T)0.25 * ((v[2][0] + v[2][1]) + (v[2][2] + v[2][3]));
+    const T dxby = ((v[1][3] + v[1][1]) - (v[1][2] + v[1][0])) * hdx;
+    const T dxbz = ((v[2][3] + v[2][1]) - (v[2][2] + v[2][0])) * hdx;
+    const T dybx = ((v[0][3] + v[0][2]) - (v[0][1] + v[0][0])) * hdy;
+    const T dybz = ((v[2][3] + v[2][2]) - (v[2][1] + v[2][0])) * hdy;
+    ohm_e<T>(dybz, -dxbz, dxby - dybx, Bb[0], Bb[1], Bb[2], inv_n[r], pgx[r], pgy[r], u[r][0],
+             u[r][1], u[r][2], jcr, eta, resist, E[0], E[1], E[2]);
+  };
+  for (int stage = 1; stage <= 4; ++stage) {
+    const T* Bc = (stage == 1) ? sB : sBs;
+    {
+      TileWalk w(t0, NX, LY + 1);
+#pragma unroll
+      for (int r = 0; r < kFNPT; ++r, w.next()) {
+        if (w.k < NN) {
+          T E[3], Bb[3];
+          ohm(Bc, w.a, w.b, r, E, Bb);
+          sE[w.k] = E[0];
+          sE[NN + w.k] = E[1];
+          sE[2 * NN + w.k] = E[2];
+        }
+      }
+    }
+    __syncthreads();
+    for (TileWalk w(t0, LX, LY); w.k < NC; w.next()) {
+      const int k = w.k;
+      const int q00 = w.b * NX + w.a, q10 = q00 + 1, q01 = q00 + NX, q11 = q01 + 1;
+      const T dxey = ((sE[NN + q10] + sE[NN + q11]) - (sE[NN + q00] + sE[NN + q01])) * hdx;
+      const T dxez =
+          ((sE[2 * NN + q10] + sE[2 * NN + q11]) - (sE[2 * NN + q00] + sE[2 * NN + q01])) * hdx;
+      const T dyex = ((sE[q01] + sE[q11]) - (sE[q00] + sE[q10])) * hdy;
+      const T dyez =
+          ((sE[2 * NN + q01] + sE[2 * NN + q11]) - (sE[2 * NN + q00] + sE[2 * NN + q10])) * hdy;
+      const T K[3] = {-dyez, dxez, dyex - dxey};
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        rk4_stage<T>(stage, K[c], sK[c * NC + k], sBs[c * NC + k], sB[c * NC + k], (T)ph.h,
+                     (T)ph.hh, (T)ph.h6);
+    }
+    __syncthreads();
+  }
+  // owned cells: the new B
+  const int oa0 = cx0 - lx0, ob0 = H;
+  const int ow = cx1 - cx0, oh = cy1 - cy0;
+  for (TileWalk w(t0, ow, 3 * oh); w.k < 3 * ow * oh; w.next()) {
+    const int c = w.b / oh, y = w.b - c * oh;
+    Bout[(size_t)c * nc + (size_t)(cy0 + y) * nx + cx0 + w.a] =
+        sB[c * NC + (ob0 + y) * LX + oa0 + w.a];
+  }
+  if (!fin) return;
+  // owned nodes (and the wall nodes nx in the last tile): E, Bbar, G; each
+  // thread takes the owned nodes among its own (their density terms and u
+  // are in its registers)
+  const int ox1 = cx1 + (cx1 == nx ? 1 : 0);
+  TileWalk w(t0, NX, LY + 1);
+#pragma unroll
+  for (int r = 0; r < kFNPT; ++r, w.next()) {
+    if (w.k >= NN) continue;
+    const int i = lx0 + w.a, y = w.b - ob0;
+    if (i < cx0 || i >= ox1 || y < 0 || y >= oh) continue;
+    const int j = cy0 + y;
+    T E[3], Bb[3];
+    ohm(sB, w.a, w.b, r, E, Bb);
+    const size_t q = (size_t)j * nxn + i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Eo[(size_t)c * nn + q] = E[c];
+      Bbo[(size_t)c * nn + q] = Bb[c];
+    }
+    const T v[8] = {E[0], E[1], E[2], Bb[0], Bb[1], Bb[2], (T)0, (T)0};
+    T* dst = G + ((size_t)j * (nx + 1) + i) * 8;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) dst[c] = v[c];
+    if (j == 0) {
+      T* gh = G + ((size_t)ny * (nx + 1) + i) * 8;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) gh[c] = v[c];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
 // Initial load (Sec. 2 set-up): ppc particles per cell, ids in cell-major
 // order, position uniform in the cell, velocity a Maxwellian of thermal speed
 // sqrt(beta_i/2) drifting at -u_sh x.

@@ -142,7 +142,39 @@ struct OpsImpl {
     return cudaGetLastError();
   }
 
+  // FP32 2D boxes with x walls: each RK4 substep in one tiled launch
+  // (k_field_substep2); B alternates with the stage buffer Bs, which that
+  // path does not otherwise use.
+  static cudaError_t fields_tiled(Sim* s) {
+    static_assert(sizeof(T) == 4, "the tiled field advance is the FP32 path");
+    DevPtrs<T> d = P(s);
+    constexpr size_t smem = field_tile_smem<T>();
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_field_substep2<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    const dim3 grid((s->g.nx + kFTX - 1) / kFTX, (s->g.ny + kFTY - 1) / kFTY);
+    T* src = d.B;
+    T* dst = d.Bs;
+    for (int sub = 0; sub < s->p.n_sub; ++sub) {
+      const int fin = (sub + 1 == s->p.n_sub) ? 1 : 0;
+      k_field_substep2<T><<<grid, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb, d.G,
+                                                            s->g, s->ph, fin);
+      std::swap(src, dst);
+    }
+    if (src != d.B)  // odd n_sub: the field ended in the stage buffer
+      return cudaMemcpyAsync(d.B, src, 3 * sizeof(T) * (size_t)s->g.nx * s->g.ny,
+                             cudaMemcpyDeviceToDevice, s->stream);
+    return cudaGetLastError();
+  }
+
   static cudaError_t fields(Sim* s) {
+    if constexpr (sizeof(T) == 4) {
+      if (s->g.dim == 2 && s->g.bc_x != FS_BC_PERIODIC) return fields_tiled(s);
+    }
     DevPtrs<T> d = P(s);
     // FP64 (bound by the FP64 pipe): 1/n and the pressure terms once per
     // step; FP32 (bound by memory) forms them in every stage instead
