@@ -859,6 +859,121 @@ __global__ void k_faraday(const T* __restrict__ En, T* __restrict__ B,
 }
 
 // ------------------------------------------------------------------------
+// The whole field advance of a 1D step with x walls (n_sub RK4 substeps,
+// then Ohm's E and Bbar for the next gather) in one launch: on a 1D grid
+// the separate passes are tens of tiny launches per step. A CTA owns kF1
+// cells (and their left nodes; the last tile also node nx) and runs every
+// pass in shared memory over its cells plus field1_halo(n_sub) cells around
+// them, which it recomputes: each pass's stencil reaches one cell, so
+// values made wrong at a tile's inner edges (read with indices clamped to
+// the tile) move in by one cell per pass and stay outside the owned cells;
+// at a wall the clamped indices are the wall's ghost cells and the density
+// is mirrored as in density_terms. Reads B from Bin, writes the new B to
+// Bout (neighbouring tiles read Bin's cells), E, Bbar and the packed gather
+// block G at the owned nodes. Same per-element arithmetic as ohm_node /
+// faraday_cell (1D), so FP64 results are those of the separate passes.
+constexpr int kF1 = 64, kF1Threads = 128;
+__host__ __device__ inline int field1_halo(int n_sub) { return 4 * n_sub + 2; }
+template <typename T>
+inline size_t field1_smem(int n_sub) {
+  const size_t L = kF1 + 2 * (size_t)field1_halo(n_sub);
+  return sizeof(T) * (9 * L + 7 * (L + 1));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kF1Threads)
+    k_field_step1(const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ nN,
+                  const T* __restrict__ uN, T* __restrict__ Eo, T* __restrict__ Bbo,
+                  T* __restrict__ G, Geo g, Phys ph, int n_sub) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nx = g.nx, nxn = g.nxn, t0 = threadIdx.x, nt = blockDim.x;
+  const int H = field1_halo(n_sub);
+  const int c0 = blockIdx.x * kF1, c1 = min(nx, c0 + kF1);
+  const int lo = max(0, c0 - H), L = min(nx, c1 + H) - lo, Ln = L + 1;
+  T* sB = (T*)smem;
+  T* sBs = sB + 3 * L;
+  T* sK = sBs + 3 * L;
+  T* sE = sK + 3 * L;  // [3][Ln]
+  T* sn = sE + 3 * Ln;
+  T* su = sn + Ln;     // [3][Ln]
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    for (int a = t0; a < L; a += nt) sB[c * L + a] = Bin[c * nx + lo + a];
+  for (int a = t0; a < Ln; a += nt) {
+    sn[a] = nN[lo + a];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) su[c * Ln + a] = uN[c * nxn + lo + a];
+  }
+  __syncthreads();
+  const T idx = (T)ph.idx, hdx = (T)ph.hdx, te = (T)ph.te;
+  const T jcr = (T)ph.jcr, eta = (T)ph.eta;
+  const bool resist = ph.eta != 0.0;
+  // Ohm at local node a from the centre field Bc (local layout)
+  auto ohm = [&](const T* Bc, int a, T E[3], T Bb[3]) {
+    const int im = min(max(a - 1, 0), L - 1), ip = min(a, L - 1);
+    const T bmy = Bc[L + im], bpy = Bc[L + ip], bmz = Bc[2 * L + im], bpz = Bc[2 * L + ip];
+    Bb[0] = (T)0.5 * (Bc[im] + Bc[ip]);
+    Bb[1] = (T)0.5 * (bmy + bpy);
+    Bb[2] = (T)0.5 * (bmz + bpz);
+    const T dby = (bpy - bmy) * idx;
+    const T dbz = (bpz - bmz) * idx;
+    const int gi = lo + a;
+    const int xp = ((gi + 1 > nx) ? 2 * nx - (gi + 1) : gi + 1) - lo;
+    const int xm = ((gi - 1 < 0) ? -(gi - 1) : gi - 1) - lo;
+    const T dnx = (sn[min(max(xp, 0), L)] - sn[min(max(xm, 0), L)]) * hdx;
+    const T inv_n = (T)1 / sn[a];
+    ohm_e<T>((T)0, -dbz, dby, Bb[0], Bb[1], Bb[2], inv_n, -(te * dnx), -(te * (T)0), su[a],
+             su[Ln + a], su[2 * Ln + a], jcr, eta, resist, E[0], E[1], E[2]);
+  };
+  for (int sub = 0; sub < n_sub; ++sub) {
+    for (int stage = 1; stage <= 4; ++stage) {
+      const T* Bc = (stage == 1) ? sB : sBs;
+      for (int a = t0; a < Ln; a += nt) {
+        T E[3], Bb[3];
+        ohm(Bc, a, E, Bb);
+        sE[a] = E[0];
+        sE[Ln + a] = E[1];
+        sE[2 * Ln + a] = E[2];
+      }
+      __syncthreads();
+      for (int a = t0; a < L; a += nt) {
+        const T dxey = (sE[Ln + a + 1] - sE[Ln + a]) * idx;
+        const T dxez = (sE[2 * Ln + a + 1] - sE[2 * Ln + a]) * idx;
+        const T K[3] = {(T)0, dxez, -dxey};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          rk4_stage<T>(stage, K[c], sK[c * L + a], sBs[c * L + a], sB[c * L + a], (T)ph.h,
+                       (T)ph.hh, (T)ph.h6);
+      }
+      __syncthreads();
+    }
+  }
+  for (int a = t0; a < Ln; a += nt) {
+    const int gi = lo + a;
+    if (gi < c0 || (gi >= c1 && !(gi == nx && c1 == nx))) continue;
+    T E[3], Bb[3];
+    ohm(sB, a, E, Bb);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Eo[c * nxn + gi] = E[c];
+      Bbo[c * nxn + gi] = Bb[c];
+    }
+    const T v[8] = {E[0], E[1], E[2], Bb[0], Bb[1], Bb[2], (T)0, (T)0};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      G[(size_t)gi * 8 + c] = v[c];                  // row 0
+      G[((size_t)(nx + 1) + gi) * 8 + c] = v[c];     // its ghost copy (row ny = 1)
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    for (int a = t0; a < L; a += nt) {
+      const int gi = lo + a;
+      if (gi >= c0 && gi < c1) Bout[c * nx + gi] = sB[c * L + a];
+    }
+}
+
+// ------------------------------------------------------------------------
 // One RK4 substep of the 2D field advance by tiles, for boxes with x walls
 // (as separate passes it is memory-bound in FP32: each stage's Ohm and
 // Faraday re-read and re-write the grid). A CTA owns kFTX x kFTY cells (and

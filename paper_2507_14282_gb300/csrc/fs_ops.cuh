@@ -171,7 +171,27 @@ struct OpsImpl {
     return cudaGetLastError();
   }
 
+  // 1D boxes with x walls: the whole field advance in one tiled launch
+  // (k_field_step1), the new B written to the stage buffer and copied back.
+  static cudaError_t fields_tiled1(Sim* s) {
+    DevPtrs<T> d = P(s);
+    const size_t smem = field1_smem<T>(s->p.n_sub);
+    static size_t attr = 0;
+    if (smem > attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_field_step1<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = smem;
+    }
+    const int grid = (s->g.nx + kF1 - 1) / kF1;
+    k_field_step1<T><<<grid, kF1Threads, smem, s->stream>>>(d.B, d.Bs, d.n, d.u, d.E, d.Bb, d.G,
+                                                           s->g, s->ph, s->p.n_sub);
+    return cudaMemcpyAsync(d.B, d.Bs, 3 * sizeof(T) * (size_t)s->g.nx, cudaMemcpyDeviceToDevice,
+                           s->stream);
+  }
+
   static cudaError_t fields(Sim* s) {
+    if (s->g.dim == 1 && s->g.bc_x != FS_BC_PERIODIC && s->p.n_sub <= 16) return fields_tiled1(s);
     if constexpr (sizeof(T) == 4) {
       if (s->g.dim == 2 && s->g.bc_x != FS_BC_PERIODIC) return fields_tiled(s);
     }
