@@ -858,6 +858,20 @@ __global__ void k_faraday(const T* __restrict__ En, T* __restrict__ B,
     faraday_cell<T, DIM>(c, En, B, Bs, Bsum, stage, g, ph);
 }
 
+// The field kernels' constants in the run's precision, formed on the host
+// (kernel parameters of that type need no FP64 conversion on the device).
+template <typename T>
+struct FieldConst {
+  T idx, hdx, hdy, te, jcr, eta;  // 1/dx, 1/(2dx), 1/(2dy), T_e, j_cr, eta
+  T h, hh, h6;                    // RK4 substep h, h/2, h/6
+  int resist;                     // eta != 0
+};
+template <typename T>
+inline FieldConst<T> field_const(const Phys& ph) {
+  return FieldConst<T>{(T)ph.idx, (T)ph.hdx, (T)ph.hdy, (T)ph.te, (T)ph.jcr,
+                       (T)ph.eta, (T)ph.h,   (T)ph.hh,  (T)ph.h6, ph.eta != 0.0 ? 1 : 0};
+}
+
 // ------------------------------------------------------------------------
 // The whole field advance of a 1D step with x walls (n_sub RK4 substeps,
 // then Ohm's E and Bbar for the next gather) in one launch: on a 1D grid
@@ -884,7 +898,7 @@ template <typename T>
 __global__ void __launch_bounds__(kF1Threads)
     k_field_step1(const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ nN,
                   const T* __restrict__ uN, T* __restrict__ Eo, T* __restrict__ Bbo,
-                  T* __restrict__ G, Geo g, Phys ph, int n_sub) {
+                  T* __restrict__ G, Geo g, Phys ph, FieldConst<T> fc, int n_sub) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nx = g.nx, nxn = g.nxn, t0 = threadIdx.x, nt = blockDim.x;
   const int H = field1_halo(n_sub);
@@ -905,9 +919,9 @@ __global__ void __launch_bounds__(kF1Threads)
     for (int c = 0; c < 3; ++c) su[c * Ln + a] = uN[c * nxn + lo + a];
   }
   __syncthreads();
-  const T idx = (T)ph.idx, hdx = (T)ph.hdx, te = (T)ph.te;
-  const T jcr = (T)ph.jcr, eta = (T)ph.eta;
-  const bool resist = ph.eta != 0.0;
+  const T idx = fc.idx, hdx = fc.hdx, te = fc.te, jcr = fc.jcr, eta = fc.eta;
+  const T h = fc.h, hh = fc.hh, h6 = fc.h6;
+  const bool resist = fc.resist != 0;
   // Ohm at local node a from the centre field Bc (local layout)
   auto ohm = [&](const T* Bc, int a, T E[3], T Bb[3]) {
     const int im = min(max(a - 1, 0), L - 1), ip = min(a, L - 1);
@@ -942,8 +956,7 @@ __global__ void __launch_bounds__(kF1Threads)
         const T K[3] = {(T)0, dxez, -dxey};
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          rk4_stage<T>(stage, K[c], sK[c * L + a], sBs[c * L + a], sB[c * L + a], (T)ph.h,
-                       (T)ph.hh, (T)ph.h6);
+          rk4_stage<T>(stage, K[c], sK[c * L + a], sBs[c * L + a], sB[c * L + a], h, hh, h6);
       }
       __syncthreads();
     }
@@ -1024,7 +1037,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
     k_field_substep2(const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ nN,
                      const T* __restrict__ uN, T* __restrict__ Eo, T* __restrict__ Bbo,
-                     T* __restrict__ G, Geo g, Phys ph, int fin) {
+                     T* __restrict__ G, Geo g, Phys ph, FieldConst<T> fc, int fin) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nx = g.nx, ny = g.ny, nxn = g.nxn;
   const int nc = nx * ny, nn = nxn * ny;
@@ -1062,9 +1075,9 @@ __global__ void __launch_bounds__(kBlock)
     }
   }
   __syncthreads();
-  const T hdx = (T)ph.hdx, hdy = (T)ph.hdy, te = (T)ph.te;
-  const T jcr = (T)ph.jcr, eta = (T)ph.eta;
-  const bool resist = ph.eta != 0.0;
+  const T hdx = fc.hdx, hdy = fc.hdy, te = fc.te, jcr = fc.jcr, eta = fc.eta;
+  const T h = fc.h, hh = fc.hh, h6 = fc.h6;
+  const bool resist = fc.resist != 0;
   {
     TileWalk w(t0, NX, LY + 1);
 #pragma unroll
@@ -1134,8 +1147,7 @@ __global__ void __launch_bounds__(kBlock)
       const T K[3] = {-dyez, dxez, dyex - dxey};
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        rk4_stage<T>(stage, K[c], sK[c * NC + k], sBs[c * NC + k], sB[c * NC + k], (T)ph.h,
-                     (T)ph.hh, (T)ph.h6);
+        rk4_stage<T>(stage, K[c], sK[c * NC + k], sBs[c * NC + k], sB[c * NC + k], h, hh, h6);
     }
     __syncthreads();
   }

@@ -106,11 +106,28 @@ struct DevPtrs {
 // One run of a batched ensemble as the batched push reads it (device table,
 // records sizeof(BatchRun) apart: 16-byte aligned, so host and device agree
 // on the stride).
+// The push's per-step constants in the run's precision, formed on the host:
+// kernel parameters of that type are operands the push reads as they are,
+// with no FP64 conversion on the device.
+template <typename T>
+struct PushConst {
+  T dtdx, dtdy, hdt;  // dt/dx, dt/dy, dt/2
+  T wth, wcr;         // deposit weights (x 2^40 in FP64: the fixed-point scale)
+  T c2inv;            // 1/c^2 (0: non-relativistic)
+};
+template <typename T>
+inline PushConst<T> push_const(const Phys& ph) {
+  const double ws = sizeof(T) == 8 ? 0x1p40 : 1.0;
+  return PushConst<T>{(T)ph.dtdx, (T)ph.dtdy, (T)ph.hdt, (T)(ph.w_th * ws), (T)(ph.w_cr * ws),
+                      (T)ph.c2inv};
+}
+
 template <typename T>
 struct alignas(16) BatchRun {
   DevPtrs<T> d;
   Geo g;
   Phys ph;
+  PushConst<T> pc;
   int in, out;  // particle buffers read and written this step
   int ncta;     // CTAs of the run's group
   int pad;

@@ -49,7 +49,8 @@ cudaError_t launch_push(Sim* s, int in, long long step) {
   a.step = step;
   const long long want = (long long)n_sm * occ_blocks;
   const int grid = (int)std::min<long long>(want, s->g.ntiles);
-  k_push<T, DIM, CH, NS, REL><<<grid, kBlock, L.bytes, s->stream>>>(s->ptrs<T>(), a);
+  k_push<T, DIM, CH, NS, REL><<<grid, kBlock, L.bytes, s->stream>>>(s->ptrs<T>(), a,
+                                                                    push_const<T>(s->ph));
   return cudaGetLastError();
 }
 
@@ -162,7 +163,8 @@ struct OpsImpl {
     for (int sub = 0; sub < s->p.n_sub; ++sub) {
       const int fin = (sub + 1 == s->p.n_sub) ? 1 : 0;
       k_field_substep2<T><<<grid, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb, d.G,
-                                                            s->g, s->ph, fin);
+                                                            s->g, s->ph, field_const<T>(s->ph),
+                                                            fin);
       std::swap(src, dst);
     }
     if (src != d.B)  // odd n_sub: the field ended in the stage buffer
@@ -185,7 +187,8 @@ struct OpsImpl {
     }
     const int grid = (s->g.nx + kF1 - 1) / kF1;
     k_field_step1<T><<<grid, kF1Threads, smem, s->stream>>>(d.B, d.Bs, d.n, d.u, d.E, d.Bb, d.G,
-                                                           s->g, s->ph, s->p.n_sub);
+                                                           s->g, s->ph, field_const<T>(s->ph),
+                                                           s->p.n_sub);
     return cudaMemcpyAsync(d.B, d.Bs, 3 * sizeof(T) * (size_t)s->g.nx, cudaMemcpyDeviceToDevice,
                            s->stream);
   }
@@ -275,6 +278,7 @@ struct OpsImpl {
     r.d = const_cast<Sim*>(s)->ptrs<T>();
     r.g = s->g;
     r.ph = s->ph;
+    r.pc = push_const<T>(s->ph);
     r.in = in;
     r.out = 1 - in;
     r.ncta = ncta;

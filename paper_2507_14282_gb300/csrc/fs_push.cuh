@@ -276,7 +276,7 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
                                         uint32_t& id, int i0, int j0, int TX, int TY,
                                         int EX, int EY, int NE, const uint16_t* e2k,
                                         const Geo& g, const Phys& ph, T dtdx, T dtdy,
-                                        T hdt, long long step, PushTally* tl,
+                                        T hdt, T c2inv_t, long long step, PushTally* tl,
                                         int& status, bool inner) {
   const int i = cell & 0xFFFF, j = cell >> 16;
   const int lx = i - i0, ly = j - j0;
@@ -361,7 +361,7 @@ __device__ __forceinline__ int push_one(const T* __restrict__ F, int NFX, int& c
     }
   }
   // REL = false: the relativistic terms are compiled out (c2inv taken as 0)
-  const T c2inv = REL ? (T)ph.c2inv : (T)0;
+  const T c2inv = REL ? c2inv_t : (T)0;
   boris<T>(vx, vy, vz, Ep, Bp, hdt, c2inv);
   // the move uses the velocity (v = u / gamma for relativistic ions)
   T mvx = vx, mvy = vy, ig = (T)1;
@@ -626,8 +626,8 @@ __device__ __forceinline__ void drain_stages(unsigned char* sm, const PushLayout
 // group): tiles cta, cta + G, ... of the run; sm is the dynamic shared memory.
 template <typename T, int DIM, int CH, int NS, bool REL>
 __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, const Phys& ph,
-                                         int in, int out, int cta, int G,
-                                         unsigned char* sm) {
+                                         const PushConst<T>& pc, int in, int out, int cta,
+                                         int G, unsigned char* sm) {
   using A = typename Num<T>::acc;
   constexpr int PPT = (CH + kBlock - 1) / kBlock;
   const PushLayout<T, DIM> L(g.TX, g.TY, CH, NS);
@@ -646,13 +646,12 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
   const int* cnt_in = d.cnt[in];
   const Parts<T> PI = d.P[in];
   const Parts<T> PO = d.P[out];
-  const T dtdx = (T)ph.dtdx, dtdy = (T)ph.dtdy, hdt = (T)ph.hdt;
-  const T wth = (T)(ph.w_th * (double)deposit_weight_scale<T>());
-  const T wcr = (T)(ph.w_cr * (double)deposit_weight_scale<T>());
+  const T dtdx = pc.dtdx, dtdy = pc.dtdy, hdt = pc.hdt;
+  const T wth = pc.wth, wcr = pc.wcr;
   const long long step = d.ctr->step;  // device step counter (graph-replayable)
   // relativistic ions (REL and c2inv > 0): states hold u = gamma v
   const bool rel = REL && ph.c2inv > 0.0;
-  const T c2inv = REL ? (T)ph.c2inv : (T)0;
+  const T c2inv = REL ? pc.c2inv : (T)0;
 
   // ---- per-CTA tables: extended cell <-> sort key; zero accumulators
   for (int e = tid; e < NE; e += kBlock) {
@@ -746,7 +745,7 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
         T vx = svx[p], vy = svy[p], vz = svz[p];
         uint32_t id = sid[p];
         key = push_one<T, DIM, REL>(F, L.NFX, cell, fx, fy, vx, vy, vz, id, i0, j0, TX, TY, EX,
-                               EY, NE, e2k, g, ph, dtdx, dtdy, hdt, step, tl,
+                               EY, NE, e2k, g, ph, dtdx, dtdy, hdt, c2inv, step, tl,
                                status, inner);
         if (key == NE) {  // far mover: straight to the global far sums
           T dvx, dvy, dvz;  // the current uses the velocity
@@ -927,9 +926,10 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
 
 // REL: compiled with the relativistic terms (used when c2inv > 0).
 template <typename T, int DIM, int CH, int NS, bool REL>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2)) k_push(DevPtrs<T> d, StepArgs a) {
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
+    k_push(DevPtrs<T> d, StepArgs a, PushConst<T> pc) {
   extern __shared__ __align__(128) unsigned char sm[];
-  push_run<T, DIM, CH, NS, REL>(d, a.g, a.ph, a.in, a.out, blockIdx.x, gridDim.x, sm);
+  push_run<T, DIM, CH, NS, REL>(d, a.g, a.ph, pc, a.in, a.out, blockIdx.x, gridDim.x, sm);
 }
 
 // Batched push of an ensemble of independent runs in one persistent launch:
@@ -947,7 +947,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
   int* dst = reinterpret_cast<int*>(&R);
   for (int k = threadIdx.x; k < (int)(sizeof(BatchRun<T>) / 4); k += kBlock) dst[k] = src[k];
   __syncthreads();
-  push_run<T, DIM, CH, NS, REL>(R.d, R.g, R.ph, R.in, R.out, cm.y, R.ncta, sm);
+  push_run<T, DIM, CH, NS, REL>(R.d, R.g, R.ph, R.pc, R.in, R.out, cm.y, R.ncta, sm);
 }
 
 }  // namespace fsx

@@ -58,7 +58,7 @@ struct Win {
 template <typename T>
 __device__ __forceinline__ void push_slot(int p, const Win<T>& w, const Slots<T>& tape,
                                           uint8_t* ev, const Geo& g, const Phys& ph,
-                                          long long step) {
+                                          const PushConst<T>& pc, long long step) {
   const int nxn = g.nxn;
   {
     int ci = w.s.ci[p];
@@ -84,8 +84,8 @@ __device__ __forceinline__ void push_slot(int p, const Win<T>& w, const Slots<T>
       Ep[c] = fmaT(f, w.E[c * nxn + ci + 1], g0 * w.E[c * nxn + ci]);
       Bp[c] = fmaT(f, w.Bb[c * nxn + ci + 1], g0 * w.Bb[c * nxn + ci]);
     }
-    boris<T>(vx, vy, vz, Ep, Bp, (T)ph.hdt);
-    const T fr = fmaT(vx, (T)ph.dtdx, f);
+    boris<T>(vx, vy, vz, Ep, Bp, pc.hdt);
+    const T fr = fmaT(vx, pc.dtdx, f);
     const T k = Num<T>::fl(fr);
     int inew = ci + (int)k;
     T fn = fr - k;
@@ -214,8 +214,8 @@ __device__ __forceinline__ void inject_one(int k, const Win<T>& w, const Geo& g,
 // clears the fixed-point sums for the step's deposit.
 template <typename T>
 __global__ void k_win_push_inject(Win<T> w, Slots<T> tape, uint8_t* ev, Geo g, Phys ph,
-                                  long long step, int np, int n_new, unsigned long long first,
-                                  int ib) {
+                                  PushConst<T> pc, long long step, int np, int n_new,
+                                  unsigned long long first, int ib) {
   // the deposit sums, read by the previous step's field kernel, start over
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 4 * g.nxn; k += gridDim.x * blockDim.x)
     w.q[k] = 0ull;
@@ -225,7 +225,7 @@ __global__ void k_win_push_inject(Win<T> w, Slots<T> tape, uint8_t* ev, Geo g, P
   }
   const int stride = (gridDim.x - ib) * blockDim.x;
   for (int p = (blockIdx.x - ib) * blockDim.x + threadIdx.x; p < np; p += stride)
-    push_slot<T>(p, w, tape, ev, g, ph, step);
+    push_slot<T>(p, w, tape, ev, g, ph, pc, step);
 }
 
 // c * 2^40 rounded to the nearest integer, ties to even (the value of
@@ -525,37 +525,37 @@ struct Tile {
 // ohm_node).
 template <typename T>
 __device__ __forceinline__ void tile_ohm(const Tile& t, int gi, const T* B, const T* n,
-                                         const T* u, const Phys& ph, T E[3], T Bb[3]) {
+                                         const T* u, const Phys& ph, const FieldConst<T>& fc,
+                                         T E[3], T Bb[3]) {
   const int L = t.L, Ln = L + 1, i = gi - t.lo;
   const int im = t.cell(gi - 1), ip = t.cell(gi);
-  const T idx = (T)ph.idx;
+  const T idx = fc.idx;
   const T bmy = B[L + im], bpy = B[L + ip], bmz = B[2 * L + im], bpz = B[2 * L + ip];
   Bb[0] = (T)0.5 * (B[im] + B[ip]);
   Bb[1] = (T)0.5 * (bmy + bpy);
   Bb[2] = (T)0.5 * (bmz + bpz);
   const T dby = (bpy - bmy) * idx;
   const T dbz = (bpz - bmz) * idx;
-  const T te = (T)ph.te;
-  const T dnx = (n[t.node(gi + 1)] - n[t.node(gi - 1)]) * (T)ph.hdx;
+  const T te = fc.te;
+  const T dnx = (n[t.node(gi + 1)] - n[t.node(gi - 1)]) * fc.hdx;
   const T inv_n = (T)1 / n[i];
   ohm_e<T>((T)0, -dbz, dby, Bb[0], Bb[1], Bb[2], inv_n, -(te * dnx), -(te * (T)0), u[i],
-           u[Ln + i], u[2 * Ln + i], (T)ph.jcr, (T)ph.eta, ph.eta != 0.0, E[0], E[1], E[2]);
+           u[Ln + i], u[2 * Ln + i], fc.jcr, fc.eta, fc.resist != 0, E[0], E[1], E[2]);
 }
 
 // Faraday + RK4 stage update at local cell c of a tile (1D: K = (0, dEz/dx,
 // -dEy/dx) from the nodes c, c + 1).
 template <typename T>
 __device__ __forceinline__ void tile_faraday(const Tile& t, int c, const T* E, T* B, T* Bs,
-                                             T* K, int stage, const Phys& ph) {
+                                             T* K, int stage, const FieldConst<T>& fc) {
   const int L = t.L, Ln = L + 1;
-  const T idx = (T)ph.idx;
+  const T idx = fc.idx;
   const T dxey = (E[Ln + c + 1] - E[Ln + c]) * idx;
   const T dxez = (E[2 * Ln + c + 1] - E[2 * Ln + c]) * idx;
   const T Kc[3] = {(T)0, dxez, -dxey};
 #pragma unroll
   for (int q = 0; q < 3; ++q)
-    rk4_stage<T>(stage, Kc[q], K[q * L + c], Bs[q * L + c], B[q * L + c], (T)ph.h, (T)ph.hh,
-                 (T)ph.h6);
+    rk4_stage<T>(stage, Kc[q], K[q * L + c], Bs[q * L + c], B[q * L + c], fc.h, fc.hh, fc.h6);
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;  // shared memory a CTA may opt in to
@@ -573,9 +573,9 @@ inline size_t rk4_adj_smem(int n_sub, size_t tsz) {
 // n_sub RK4 substeps of Ohm + Faraday with n, u frozen, then E, Bbar for the
 // next gather and the new B (into Bout; B is read by neighbouring tiles).
 template <typename T>
-__global__ void __launch_bounds__(kTbThreads) k_win_fields(Win<T> w, Geo g, Phys ph, int n_sub,
-                                                           T* Bout, T* tn, T* tu, T* tr,
-                                                           T* tapeB) {
+__global__ void __launch_bounds__(kTbThreads)
+    k_win_fields(Win<T> w, Geo g, Phys ph, FieldConst<T> fc, int n_sub, T* Bout, T* tn, T* tu,
+                 T* tr, T* tapeB) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nx = g.nx, nxn = g.nxn, t0 = threadIdx.x, nt = blockDim.x;
   const Tile t(blockIdx.x, nx, halo_fields(n_sub));
@@ -618,12 +618,12 @@ __global__ void __launch_bounds__(kTbThreads) k_win_fields(Win<T> w, Geo g, Phys
       const T* Bin = (stage == 1) ? sB : sBs;
       for (int i = t0; i < Ln; i += nt) {
         T E[3], Bb[3];
-        tile_ohm<T>(t, t.lo + i, Bin, sn, su, ph, E, Bb);
+        tile_ohm<T>(t, t.lo + i, Bin, sn, su, ph, fc, E, Bb);
 #pragma unroll
         for (int c = 0; c < 3; ++c) sE[c * Ln + i] = E[c];
       }
       __syncthreads();
-      for (int c = t0; c < L; c += nt) tile_faraday<T>(t, c, sE, sB, sBs, sK, stage, ph);
+      for (int c = t0; c < L; c += nt) tile_faraday<T>(t, c, sE, sB, sBs, sK, stage, fc);
       __syncthreads();
     }
   }
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kTbThreads) k_win_fields(Win<T> w, Geo g, Phys
     const int gi = t.lo + i;
     if (!t.owns_node(gi)) continue;
     T E[3], Bb[3];
-    tile_ohm<T>(t, gi, sB, sn, su, ph, E, Bb);
+    tile_ohm<T>(t, gi, sB, sn, su, ph, fc, E, Bb);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       w.E[c * nxn + gi] = E[c];
@@ -657,8 +657,9 @@ __global__ void __launch_bounds__(kTbThreads) k_win_fields(Win<T> w, Geo g, Phys
 //      lNm = lUm = 0 for the next Ohm adjoint.
 template <typename T>
 __global__ void __launch_bounds__(kTbThreads)
-    k_win_rk4_adj(Win<T> w, Geo g, Phys ph, int ns, const T* Bn, const T* n1, const T* u1,
-                  const T* nr1, const T* n0, const T* u0, const double* lBin, double* lBout) {
+    k_win_rk4_adj(Win<T> w, Geo g, Phys ph, FieldConst<T> fc, int ns, const T* Bn, const T* n1,
+                  const T* u1, const T* nr1, const T* n0, const T* u0, const double* lBin,
+                  double* lBout) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nx = g.nx, nxn = g.nxn, t0 = threadIdx.x, nt = blockDim.x;
   const Tile t(blockIdx.x, nx, halo_rk4_adj(ns));
@@ -707,12 +708,12 @@ __global__ void __launch_bounds__(kTbThreads)
       for (int k = t0; k < 3 * L; k += nt) y[k] = (double)Bin[k];
       for (int i = t0; i < Ln; i += nt) {
         T E[3], Bb[3];
-        tile_ohm<T>(t, t.lo + i, Bin, sn, su, ph, E, Bb);
+        tile_ohm<T>(t, t.lo + i, Bin, sn, su, ph, fc, E, Bb);
 #pragma unroll
         for (int c = 0; c < 3; ++c) sE[c * Ln + i] = E[c];
       }
       __syncthreads();
-      for (int c = t0; c < L; c += nt) tile_faraday<T>(t, c, sE, sB, sBs, sK, stage, ph);
+      for (int c = t0; c < L; c += nt) tile_faraday<T>(t, c, sE, sB, sBs, sK, stage, fc);
       __syncthreads();
     }
   }
@@ -868,7 +869,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 template <typename T>
 __device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const Slots<T>& t0,
                                                  const Slots<T>& t1, const uint8_t* ev,
-                                                 const Geo& g, const Phys& ph, long long step,
+                                                 const Geo& g, const Phys& ph,
+                                                 const PushConst<T>& pc, long long step,
                                                  int np0, double& gu2, double& gucr, T out[12]) {
   using A = T;  // arithmetic of the push's adjoint
   const int nxn = g.nxn;
@@ -932,7 +934,7 @@ __device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const S
     }
     const A v0[3] = {(A)t0.v[p], (A)t0.v[cap + p], (A)t0.v[2 * cap + p]};
     T vxt = t0.v[p], vyt = t0.v[cap + p], vzt = t0.v[2 * cap + p];
-    boris<T>(vxt, vyt, vzt, Ep, Bp, (T)ph.hdt);
+    boris<T>(vxt, vyt, vzt, Ep, Bp, pc.hdt);
     const A vp[3] = {(A)vxt, (A)vyt, (A)vzt};  // before the return
     A lvp[3];  // adjoint of vp
     A lf0;
@@ -982,7 +984,7 @@ __device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const S
     }
     // ---- Boris adjoint: v+ = q + em, q = vm + p x s, p = vm + vm x t,
     //      s = (2 / (1 + t.t)) t, t = hdt B, vm = v + em, em = hdt E
-    const A hdt = (A)ph.hdt;
+    const A hdt = pc.hdt;
     A em[3], vm[3], t[3], sv[3], pp[3];
     for (int c = 0; c < 3; ++c) {
       em[c] = hdt * (A)Ep[c];
@@ -1054,7 +1056,7 @@ __device__ __forceinline__ void add_node_shares(const Win<T>& w, int nxn, int c0
 template <typename T>
 __global__ void __launch_bounds__(kBlock, 4)
     k_win_particle_adj(Win<T> w, Slots<T> t0, Slots<T> t1, const uint8_t* ev, Geo g, Phys ph,
-                       long long step, int np0, int np1, int M) {
+                       PushConst<T> pc, long long step, int np0, int np1, int M) {
   const int nxn = g.nxn;
   const int lane = threadIdx.x & 31;
   double gu2 = 0.0, gucr = 0.0;
@@ -1063,7 +1065,8 @@ __global__ void __launch_bounds__(kBlock, 4)
     const int p = base + lane;
     T a[12];
     const int c0 =
-        (p < np1) ? particle_adj_slot<T>(p, w, t0, t1, ev, g, ph, step, np0, gu2, gucr, a) : -1;
+        (p < np1) ? particle_adj_slot<T>(p, w, t0, t1, ev, g, ph, pc, step, np0, gu2, gucr, a)
+                   : -1;
     if (sizeof(T) == 4) {
       const unsigned grp = __match_any_sync(0xffffffffu, c0);
       const bool lead = c0 >= 0 && lane == __ffs(grp) - 1;
@@ -1334,12 +1337,13 @@ void forward_step(fs_window* w, Win<T>& r, int n, int k) {
   const int nadd = w->ninj[n] * kinds;
   const int ib = (nadd > 0) ? blocks(nadd) : 0;
   const int pb = (np > 0) ? blocks(np) : 1;  // one block at least: it clears the sums
-  k_win_push_inject<T><<<ib + pb, kBlock, 0, w->st>>>(r, tp, ev, w->g, w->ph, n, np, w->ninj[n],
+  k_win_push_inject<T><<<ib + pb, kBlock, 0, w->st>>>(r, tp, ev, w->g, w->ph,
+                                                      push_const<T>(w->ph), n, np, w->ninj[n],
                                                       w->first_id[n], ib);
   const int np1 = w->np_at[n + 1];
   if (np1 > 0) k_win_deposit<T><<<blocks(np1), kBlock, 0, w->st>>>(r, w->g, w->ph, np1);
   k_win_fields<T><<<tiles(w->g.nx), kTbThreads, fields_smem(w->p.n_sub, sizeof(T)), w->st>>>(
-      r, w->g, w->ph, w->p.n_sub, r.Bx, tn, tu, tr, tB);
+      r, w->g, w->ph, field_const<T>(w->ph), w->p.n_sub, r.Bx, tn, tu, tr, tB);
   std::swap(r.B, r.Bx);  // the step's B went to the other buffer
   w->bsel ^= 1;
 }
@@ -1453,12 +1457,14 @@ int do_backward(fs_window* w, double dloss, double* grad) {
       // the step's field update and moments in reverse; E^n, Bbar^n as the
       // forward had them
       k_win_rk4_adj<T><<<tiles(w->g.nx), kTbThreads, rk4_adj_smem(w->p.n_sub, sizeof(T)), w->st>>>(
-          r, w->g, w->ph, w->p.n_sub, Bn, mn1, mu1, mr1, mn0, mu0, r.lB, r.lBx);
+          r, w->g, w->ph, field_const<T>(w->ph), w->p.n_sub, Bn, mn1, mu1, mr1, mn0, mu0, r.lB,
+          r.lBx);
       std::swap(r.lB, r.lBx);
       const int npa = w->np_at[n], npb = w->np_at[n + 1];
       if (npb > 0)
         k_win_particle_adj<T><<<blocks(npb), kBlock, 0, w->st>>>(
-            r, tape_at<T>(w, k), tape_at<T>(w, k + 1), ev_at(w, k), w->g, w->ph, n, npa, npb, M);
+            r, tape_at<T>(w, k), tape_at<T>(w, k + 1), ev_at(w, k), w->g, w->ph,
+            push_const<T>(w->ph), n, npa, npb, M);
       // Ohm at the start of the step: lB += ..., lNm, lUm = adjoint of M^n
       k_win_ohm_adj_step<T><<<tiles(w->g.nx), kTbThreads, 0, w->st>>>(r, w->g, w->ph, Bn, mn0, mu0);
     }
