@@ -89,8 +89,11 @@ __device__ __forceinline__ float rcpT(float a) { return __frcp_rn(a); }
 __device__ __forceinline__ double rcpT(double a) { return __drcp_rn(a); }
 __device__ __forceinline__ float sqrtT(float a) { return __fsqrt_rn(a); }
 __device__ __forceinline__ double sqrtT(double a) { return __dsqrt_rn(a); }
-__device__ __forceinline__ double acc_to_double(float a) { return (double)a; }
-__device__ __forceinline__ double acc_to_double(unsigned long long a) {
+// an accumulator's value in the run's precision: FP32 sums as they are (no
+// round trip through FP64, whose conversions use GB300's narrow FP64 pipe),
+// FP64 fixed point scaled back by 2^-40
+__device__ __forceinline__ float acc_value(float a) { return a; }
+__device__ __forceinline__ double acc_value(unsigned long long a) {
   return (double)(long long)a * 0x1p-40;
 }
 
@@ -584,11 +587,7 @@ __global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
         }
       }
     }
-    double n = acc_to_double(s[0]);
-    double jx = acc_to_double(s[1]);
-    double jy = acc_to_double(s[2]);
-    double jz = acc_to_double(s[3]);
-    T nt = (T)n, jxt = (T)jx, jyt = (T)jy, jzt = (T)jz;
+    T nt = acc_value(s[0]), jxt = acc_value(s[1]), jyt = acc_value(s[2]), jzt = acc_value(s[3]);
     if (g.bc_x == FS_BC_FAUXSHOCK && (i == 0 || i == g.nx)) {
       nt = nt * (T)2; jxt = jxt * (T)2; jyt = jyt * (T)2; jzt = jzt * (T)2;
     }
