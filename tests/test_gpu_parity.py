@@ -93,6 +93,19 @@ def test_fp64_1d_config_full_1000_steps_bit_exact(fs):
     assert d["reflected"] > 0 and d["incident"] == d["transmitted"] + d["reflected"]
 
 
+@pytest.mark.parametrize("nx,n_sub", [(100, 2), (72, 3), (40, 1)])
+def test_fp64_1d_ragged_field_tiles_bit_exact(fs, nx, n_sub):
+    # the 1D field advance runs on 64-cell tiles with a 4 n_sub + 2 halo:
+    # grids ending in a partial tile, one to three RK4 substeps per step
+    cfg = W.scaled(W.CONFIG_1D, nx=nx, n_sub=n_sub)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**cfg)
+    for chunk in (1, 29):
+        gpu.step(chunk)
+        ref.step(chunk)
+        assert_state_equal(gpu, ref, fs)
+
+
 @pytest.mark.parametrize("tile", [(4, 2), (8, 4), (16, 1), (2, 8)])
 def test_fp64_2d_bit_exact_several_tiles(fs, tile):
     cfg = W.scaled(W.CONFIG_2D, nx=64, ny=16, ppc=8, mach_a=10.0, theta_bn_deg=20.0,
@@ -320,12 +333,16 @@ def test_inject_rejects_out_of_range(fs):
 
 
 # ---------------------------------------------------------------- FP32
-@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("dim", [1, 2, "2-ragged"])
 def test_fp32_fields_within_tolerance(fs, dim):
     if dim == 1:
         cfg = W.scaled(W.CONFIG_1D, nx=256)
-    else:
+    elif dim == 2:
         cfg = W.scaled(W.CONFIG_2D_FP32, nx=64, ny=16, ppc=16)
+    else:
+        # the 2D field advance runs on 32 x 16-cell tiles: partial tiles in
+        # x and y, three substeps (halo 4, then 5 in the last)
+        cfg = W.scaled(W.CONFIG_2D_FP32, nx=72, ny=20, ppc=16, n_sub=3)
     gpu = fs.FauxShock(precision=fs.FS_FP32, **cfg)
     ref = O.Oracle(**cfg)
     gpu.step(1)
