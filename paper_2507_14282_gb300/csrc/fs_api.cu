@@ -9,7 +9,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "fs.h"
@@ -387,6 +390,37 @@ void release_events(fs_handle* h) {
 }
 }  // namespace
 
+namespace {
+// Runs f(lo, hi) over [0, n) in slices on up to 16 host threads.
+template <typename F>
+void parallel_slices(long long n, F f) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  long long nt = std::min<long long>(hw ? hw : 1, 16);
+  nt = std::max<long long>(1, std::min<long long>(nt, n / (1 << 16)));
+  if (nt == 1) {
+    f(0LL, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve((size_t)nt);
+  for (long long k = 0; k < nt; ++k)
+    th.emplace_back(f, n * k / nt, n * (k + 1) / nt);
+  for (auto& x : th) x.join();
+}
+
+// Staged copies of the caller's columns: cell = (j << 16) | i from the i
+// column (in `cell`) and the j column (in `id`, 2D), then the ids first,
+// first + 1, ... in input order.
+__global__ void k_pack_staged(int* cell, uint32_t* id, int m, int dim,
+                              unsigned long long first) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const int j = (dim == 2) ? (int)id[k] : 0;
+    cell[k] = (j << 16) | cell[k];
+    id[k] = (uint32_t)(first + (unsigned long long)k);
+  }
+}
+}  // namespace
+
 extern "C" {
 
 int fs_params_default(int dim, fs_params* out) {
@@ -583,73 +617,112 @@ int fs_inject(fs_handle* h, long long n, const int* ci, const int* cj,
   if (n == 0) return FS_OK;
   if (!ci || !fx || !vx || !vy || !vz) return FS_EINVAL;
   if (s->g.dim == 2 && (!cj || !fy)) return FS_EINVAL;
-  for (long long k = 0; k < n; ++k) {
-    const int j = (s->g.dim == 2) ? cj[k] : 0;
-    if (ci[k] < 0 || ci[k] >= s->g.nx || j < 0 || j >= s->g.ny) return FS_EINVAL;
-    if (!(fx[k] >= 0.0 && fx[k] < 1.0)) return FS_EINVAL;
-    if (s->g.dim == 2 && !(fy[k] >= 0.0 && fy[k] < 1.0)) return FS_EINVAL;
-    if (!isfinite(vx[k]) || !isfinite(vy[k]) || !isfinite(vz[k])) return FS_EINVAL;
-  }
+  // every input is checked before anything reaches the device
+  const int dim = s->g.dim, nx = s->g.nx, ny = s->g.ny;
+  std::atomic<bool> bad(false);
+  parallel_slices(n, [&](long long lo, long long hi) {
+    for (long long k = lo; k < hi && !bad.load(std::memory_order_relaxed); ++k) {
+      const int j = (dim == 2) ? cj[k] : 0;
+      if (ci[k] < 0 || ci[k] >= nx || j < 0 || j >= ny || !(fx[k] >= 0.0 && fx[k] < 1.0) ||
+          (dim == 2 && !(fy[k] >= 0.0 && fy[k] < 1.0)) || !isfinite(vx[k]) ||
+          !isfinite(vy[k]) || !isfinite(vz[k]))
+        bad.store(true, std::memory_order_relaxed);
+    }
+  });
+  if (bad.load()) return FS_EINVAL;
   int r = sync_and_check(s);
   if (r) return r;
   unsigned long long next = 0;
   if (cudaMemcpy(&next, s->base + s->L.ctr + offsetof(Counters, next_id), 8,
                  cudaMemcpyDeviceToHost) != cudaSuccess)
     return s->sticky = FS_ECUDA;
+  if (!ids && next + (unsigned long long)n - 1 > kIdMask) return s->sticky = FS_EIDOVERFLOW;
   const bool dbl = (s->p.precision == FS_FP64);
   const size_t Tsz = dbl ? 8 : 4;
   // stage through the mover list (unused between steps) in large chunks
   const int chunk = s->g.mover_cap > s->g.staging_cap ? s->g.mover_cap : s->g.staging_cap;
   const size_t* stg = s->g.mover_cap > s->g.staging_cap ? s->L.mov : s->L.stg;
-  std::vector<int> cell(chunk);
-  std::vector<uint32_t> id(chunk);
-  std::vector<char> buf(5 * Tsz * (size_t)chunk);
-  for (long long k0 = 0; k0 < n; k0 += chunk) {
-    const int m = (int)((n - k0) < chunk ? (n - k0) : chunk);
-    char* cols[5];
-    for (int c = 0; c < 5; ++c) cols[c] = buf.data() + (size_t)c * Tsz * chunk;
-    for (int k = 0; k < m; ++k) {
-      const long long q = k0 + k;
-      const int j = (s->g.dim == 2) ? cj[q] : 0;
-      cell[k] = (j << 16) | ci[q];
-      uint32_t w;
-      if (ids) {
-        w = ids[q];
-        const unsigned long long num = w & kIdMask;
-        if (num >= next) next = num + 1;
-      } else {
-        if (next > kIdMask) return s->sticky = FS_EIDOVERFLOW;
-        w = (uint32_t)next++;
+  char* base = s->base;
+  auto h2d = [&](size_t off, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, s->stream);
+  };
+  if (dbl && !ids) {
+    // FP64 without caller ids: the caller's columns go to the staging area as
+    // they are (a pinned caller's arrays take the DMA path), the cell index
+    // and the ids are formed on the device; the stream orders the chunks
+    for (long long k0 = 0; k0 < n; k0 += chunk) {
+      const int m = (int)((n - k0) < chunk ? (n - k0) : chunk);
+      cudaError_t e = h2d(stg[0], ci + k0, 4 * (size_t)m);
+      if (e == cudaSuccess && dim == 2) e = h2d(stg[6], cj + k0, 4 * (size_t)m);
+      if (e == cudaSuccess) e = h2d(stg[1], fx + k0, 8 * (size_t)m);
+      if (e == cudaSuccess && dim == 2) e = h2d(stg[2], fy + k0, 8 * (size_t)m);
+      if (e == cudaSuccess) e = h2d(stg[3], vx + k0, 8 * (size_t)m);
+      if (e == cudaSuccess) e = h2d(stg[4], vy + k0, 8 * (size_t)m);
+      if (e == cudaSuccess) e = h2d(stg[5], vz + k0, 8 * (size_t)m);
+      if (e == cudaSuccess) {
+        k_pack_staged<<<std::min(1024, (m + 255) / 256), 256, 0, s->stream>>>(
+            (int*)(base + stg[0]), (uint32_t*)(base + stg[6]), m, dim, next + (unsigned long long)k0);
+        e = cudaGetLastError();
       }
-      id[k] = w;
-      const double vals[5] = {fx[q], s->g.dim == 2 ? fy[q] : 0.0, vx[q], vy[q], vz[q]};
-      for (int c = 0; c < 5; ++c) {
-        if (dbl) {
-          ((double*)cols[c])[k] = vals[c];
-        } else {
-          float f = (float)vals[c];
-          if (c < 2 && f >= 1.0f) f = 0x1.fffffep-1f;
-          ((float*)cols[c])[k] = f;
+      if (e == cudaSuccess) e = s->ops->insert_staged(s, s->cur, m, stg == s->L.mov);
+      if (e != cudaSuccess) return s->sticky = FS_ECUDA;
+    }
+    next += (unsigned long long)n;
+  } else {
+    std::vector<int> cell(chunk);
+    std::vector<uint32_t> id(chunk);
+    std::vector<char> buf(5 * Tsz * (size_t)chunk);
+    for (long long k0 = 0; k0 < n; k0 += chunk) {
+      const int m = (int)((n - k0) < chunk ? (n - k0) : chunk);
+      char* cols[5];
+      for (int c = 0; c < 5; ++c) cols[c] = buf.data() + (size_t)c * Tsz * chunk;
+      std::atomic<unsigned long long> top(next);
+      parallel_slices(m, [&](long long lo, long long hi) {
+        unsigned long long mx = 0;
+        for (long long k = lo; k < hi; ++k) {
+          const long long q = k0 + k;
+          const int j = (dim == 2) ? cj[q] : 0;
+          cell[k] = (j << 16) | ci[q];
+          uint32_t w;
+          if (ids) {
+            w = ids[q];
+            const unsigned long long num = w & kIdMask;
+            if (num + 1 > mx) mx = num + 1;
+          } else {
+            w = (uint32_t)(next + (unsigned long long)q);
+          }
+          id[k] = w;
+          const double vals[5] = {fx[q], dim == 2 ? fy[q] : 0.0, vx[q], vy[q], vz[q]};
+          for (int c = 0; c < 5; ++c) {
+            if (dbl) {
+              ((double*)cols[c])[k] = vals[c];
+            } else {
+              float f = (float)vals[c];
+              if (c < 2 && f >= 1.0f) f = 0x1.fffffep-1f;
+              ((float*)cols[c])[k] = f;
+            }
+          }
         }
+        unsigned long long cur = top.load();
+        while (mx > cur && !top.compare_exchange_weak(cur, mx)) {
+        }
+      });
+      cudaError_t e = h2d(stg[0], cell.data(), 4 * (size_t)m);
+      for (int c = 0; c < 5 && e == cudaSuccess; ++c) {
+        if (c == 1 && dim == 1) continue;
+        e = h2d(stg[1 + c], cols[c], Tsz * (size_t)m);
       }
+      if (e == cudaSuccess) e = h2d(stg[6], id.data(), 4 * (size_t)m);
+      if (e == cudaSuccess) e = s->ops->insert_staged(s, s->cur, m, stg == s->L.mov);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // host buffers reused
+      if (e != cudaSuccess) return s->sticky = FS_ECUDA;
+      next = ids ? top.load() : next;
     }
-    cudaError_t e = cudaMemcpyAsync(s->base + stg[0], cell.data(), 4 * (size_t)m,
-                                    cudaMemcpyHostToDevice, s->stream);
-    const int map[5] = {1, 2, 3, 4, 5};
-    for (int c = 0; c < 5 && e == cudaSuccess; ++c) {
-      if (c == 1 && s->g.dim == 1) continue;
-      e = cudaMemcpyAsync(s->base + stg[map[c]], cols[c], Tsz * (size_t)m,
-                          cudaMemcpyHostToDevice, s->stream);
-    }
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s->base + stg[6], id.data(), 4 * (size_t)m,
-                          cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = s->ops->insert_staged(s, s->cur, m, stg == s->L.mov);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return s->sticky = FS_ECUDA;
+    if (!ids) next += (unsigned long long)n;
   }
-  if (cudaMemcpy(s->base + s->L.ctr + offsetof(Counters, next_id), &next, 8,
-                 cudaMemcpyHostToDevice) != cudaSuccess)
+  if (cudaMemcpyAsync(s->base + s->L.ctr + offsetof(Counters, next_id), &next, 8,
+                      cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
     return s->sticky = FS_ECUDA;
   r = redeposit(s);
   if (r) return s->sticky = r;
