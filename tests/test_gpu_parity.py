@@ -332,6 +332,66 @@ def test_inject_rejects_out_of_range(fs):
         assert e.value.code == -1
 
 
+def test_inject_large_rejects_a_bad_value_and_inserts_nothing(fs):
+    # inputs over a million particles are checked on several host threads;
+    # one bad value deep inside fails the call before anything is inserted
+    gpu = fs.FauxShock(precision=fs.FS_FP64, dim=2, nx=256, ny=64, ppc=64, init_plasma=0,
+                       inject_thermal=0, capacity_factor=2.0)
+    rng = np.random.default_rng(9)
+    n = 1_200_000
+    a = dict(ci=rng.integers(0, 256, n).astype(np.int32),
+             cj=rng.integers(0, 64, n).astype(np.int32), fx=rng.uniform(0, 1, n),
+             fy=rng.uniform(0, 1, n), vx=rng.normal(0, 1, n), vy=rng.normal(0, 1, n),
+             vz=rng.normal(0, 1, n))
+    for key, val in (("fy", 1.0), ("cj", 64), ("vz", np.inf)):
+        b = {k: v.copy() for k, v in a.items()}
+        b[key][987_654] = val
+        with pytest.raises(fs.FsError) as e:
+            gpu.inject(**b)
+        assert e.value.code == -1
+        assert gpu.num_particles() == 0
+    gpu.inject(**a)
+    assert gpu.num_particles() == n
+    gpu.close()
+
+
+@pytest.mark.parametrize("prec,with_ids", [("fp64", False), ("fp64", True), ("fp32", False)])
+def test_inject_round_trip(fs, prec, with_ids):
+    # FP64 without ids: columns copied as they are, cell and ids formed on the
+    # device; with ids, and FP32: packed on the host. Every particle comes
+    # back with its cell, offsets, velocity and id (ids in input order when
+    # the library assigns them).
+    precision = fs.FS_FP64 if prec == "fp64" else fs.FS_FP32
+    gpu = fs.FauxShock(precision=precision, dim=2, nx=64, ny=32, ppc=64, init_plasma=0,
+                       inject_thermal=0, capacity_factor=2.0)
+    rng = np.random.default_rng(11)
+    n = 200_000
+    a = dict(ci=rng.integers(0, 64, n).astype(np.int32),
+             cj=rng.integers(0, 32, n).astype(np.int32), fx=rng.uniform(0, 1, n),
+             fy=rng.uniform(0, 1, n), vx=rng.normal(0, 1, n), vy=rng.normal(0, 1, n),
+             vz=rng.normal(0, 1, n))
+    ids = rng.permutation(n).astype(np.uint32) + 5 if with_ids else None
+    gpu.inject(**a, ids=ids)
+    p = gpu.particles()
+    assert len(p["id"]) == n
+    want = ids if with_ids else np.arange(n, dtype=np.uint32)
+    order = np.argsort(p["id"])
+    src = np.argsort(want)
+    assert np.array_equal(p["id"][order], want[src])
+    for k in ("ci", "cj"):
+        assert np.array_equal(p[k][order], a[k][src]), k
+    cast = (lambda x: x) if prec == "fp64" else (lambda x: x.astype(np.float32).astype(np.float64))
+    for k in ("fx", "fy", "vx", "vy", "vz"):
+        got, exp = p[k][order], cast(a[k][src])
+        if k in ("fx", "fy") and prec == "fp32":
+            exp = np.minimum(exp, np.float64(np.nextafter(np.float32(1), np.float32(0))))
+        assert np.array_equal(got, exp), k
+    # the next ids continue after the largest one in use
+    d = gpu.diag()
+    assert d["next_id"] == (int(want.max()) + 1)
+    gpu.close()
+
+
 # ---------------------------------------------------------------- FP32
 @pytest.mark.parametrize("dim", [1, 2, "2-ragged"])
 def test_fp32_fields_within_tolerance(fs, dim):
