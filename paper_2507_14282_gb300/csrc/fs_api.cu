@@ -297,12 +297,22 @@ int grid_blocks(long long n) {
 
 // Capture one step for each ping-pong parity on a private stream (the legacy
 // default stream cannot be captured); the graphs replay on the caller's stream.
-// Kernels one step launches: push, movers, injection (3), moments, [FP64:
-// Ohm density terms], 2 x 4 x n_sub field stages, final Ohm, step end.
+// Kernels one step launches: push, movers, injection (3), moments, the field
+// advance, step end. The field advance is one tiled launch in 1D boxes with
+// x walls, one per substep in FP32 2D boxes with x walls, else [FP64: Ohm
+// density terms], 2 x 4 x n_sub stage passes and the final Ohm (the same
+// choice as the field launcher makes).
 long long launches_per_step(const Sim* s) {
   const bool inj = s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable);
-  return 1 + 1 + (inj ? 3 : 0) + 1 + (s->p.precision == FS_FP64 ? 1 : 0) +
-         8LL * s->p.n_sub + 1 + 1;
+  const bool walls = s->g.bc_x != FS_BC_PERIODIC;
+  long long fields;
+  if (s->g.dim == 1 && walls && s->p.n_sub <= 16)
+    fields = 1;
+  else if (s->p.precision == FS_FP32 && s->g.dim == 2 && walls)
+    fields = s->p.n_sub;
+  else
+    fields = (s->p.precision == FS_FP64 ? 1 : 0) + 8LL * s->p.n_sub + 1;
+  return 1 + 1 + (inj ? 3 : 0) + 1 + fields + 1;
 }
 
 int build_graphs(Sim* s) {
