@@ -331,6 +331,15 @@ int fs_destroy(fs_handle* h);
 /* Name of a status code. */
 const char* fs_strerror(int status);
 
+/* Measurement utility (not part of the method): this GPU's FP64
+   fused multiply-add rate, the denominator of the FP64 push's roofline.
+   Runs a kernel of independent FP64 FMA chains on every SM at full
+   occupancy, `iters` FMAs per chain (1 <= iters <= 2^24), on `cuda_stream`
+   (0: the legacy default stream); returns FMA lane operations per second
+   in *ops_per_s (an FMA counted once: FLOP/s is twice this). Synchronises
+   the stream. FS_EINVAL for a bad argument, FS_ECUDA for a launch error. */
+int fs_fp64_fma_rate(int iters, void* cuda_stream, double* ops_per_s);
+
 /* ------------------------------------------------------------------------
    Differentiable window (1D faux-shock box): the gradient of a loss at the
    end of `steps` hybrid steps with respect to

@@ -431,6 +431,26 @@ __global__ void k_pack_staged(int* cell, uint32_t* id, int m, int dim,
 }
 }  // namespace
 
+namespace {
+// Independent FP64 FMA chains (8 per thread) for fs_fp64_fma_rate: x <- x a + b
+// with a = b = 1/2 converges to 1, so the values stay finite; the sink write
+// never happens but keeps the chains.
+constexpr int kFmaChains = 8;
+__global__ void __launch_bounds__(256) k_fp64_fma(double* sink, int iters, double a, double b) {
+  double x[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) x[k] = 1.0 + 1e-3 * (double)(threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) x[k] = __fma_rn(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) s += x[k];
+  if (s == -1.0) sink[blockIdx.x] = s;
+}
+}  // namespace
+
 extern "C" {
 
 int fs_params_default(int dim, fs_params* out) {
@@ -1282,6 +1302,35 @@ int fs_batch_destroy(fs_batch* b) {
 }
 
 extern "C" {
+
+int fs_fp64_fma_rate(int iters, void* cuda_stream, double* ops_per_s) {
+  if (!ops_per_s || iters < 1 || iters > (1 << 24)) return FS_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, nsm = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fp64_fma, 256, 0) != cudaSuccess ||
+      nsm < 1 || occ < 1)
+    return FS_ECUDA;
+  const int grid = nsm * occ;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return FS_ECUDA;
+  }
+  k_fp64_fma<<<grid, 256, 0, st>>>(nullptr, iters < 64 ? iters : 64, 0.5, 0.5);  // warm-up
+  cudaEventRecord(e0, st);
+  k_fp64_fma<<<grid, 256, 0, st>>>(nullptr, iters, 0.5, 0.5);
+  cudaEventRecord(e1, st);
+  float ms = 0.0f;
+  const bool ok = cudaGetLastError() == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return FS_ECUDA;
+  *ops_per_s = (double)grid * 256.0 * kFmaChains * (double)iters / (ms * 1e-3);
+  return FS_OK;
+}
 
 const char* fs_strerror(int status) {
   switch (status) {

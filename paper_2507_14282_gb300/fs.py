@@ -125,12 +125,26 @@ def lib():
         L.fs_window_backward.argtypes = [V, C.c_double, V]
         L.fs_window_counts.argtypes = [V, V]
         L.fs_window_destroy.argtypes = [V]
+        L.fs_fp64_fma_rate.argtypes = [C.c_int, V, P(C.c_double)]
         _lib = L
     return _lib
 
 
 def strerror(code: int) -> str:
     return lib().fs_strerror(code).decode()
+
+
+def fp64_fma_rate(iters: int = 1 << 14, stream=None) -> float:
+    """This GPU's FP64 fused multiply-add rate in FMA lane operations per
+    second (fs_fp64_fma_rate; the FP64 push's roofline denominator)."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("fp64_fma_rate needs a CUDA device")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    _check(lib().fs_fp64_fma_rate(int(iters), C.c_void_p(st.cuda_stream), C.byref(out)),
+           "fs_fp64_fma_rate")
+    return out.value
 
 
 def _check(code: int, what: str):

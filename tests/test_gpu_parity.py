@@ -498,3 +498,9 @@ def test_fp32_2d_precision_form_tiles_within_tolerance(fs, mode):
     sd = 4 * np.sqrt(max(dr["reflected"], 1)) + 2
     assert abs(d["reflected"] - dr["reflected"]) <= sd
     gpu.close()
+
+
+def test_fp64_fma_rate_is_plausible(fs):
+    # the FP64 roofline denominator: near GB300's nominal 0.625 T FMA/s
+    r = fs.fp64_fma_rate(1 << 12)
+    assert 0.2e12 < r < 1.0e12, r
