@@ -15,7 +15,7 @@
 // segment of `ckpt` steps is recomputed from its checkpoint during the
 // backward; the deposit sums are int64 fixed point, so a recomputed segment
 // reproduces the forward exactly in either precision.
-#include <mutex>
+#include <algorithm>
 #include <vector>
 
 #include "fs_engine.cuh"
