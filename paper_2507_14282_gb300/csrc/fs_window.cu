@@ -251,6 +251,19 @@ __device__ __forceinline__ unsigned long long fix(double c) {
   return (unsigned long long)(b < 0 ? -r : r);
 }
 
+// c * 2^40 rounded to the nearest integer for an FP32 value c (|c| < 2^23):
+// the scaling is exact; below 2^30 the int32 conversion rounds to nearest
+// (ties to even), at or above it the value is an integer already (its ulp is
+// at least 2^7) and its significand is shifted into place.
+__device__ __forceinline__ long long fix32(float c) {
+  const float y = c * 0x1p40f;
+  if (fabsf(y) < 0x1p30f) return (long long)__float2int_rn(y);
+  const int b = __float_as_int(y);
+  const int e = (b >> 23) & 0xFF;
+  const long long r = (long long)((b & 0x7FFFFF) | 0x800000) << (e - 150);
+  return b < 0 ? -r : r;
+}
+
 // Sum of v over the lanes of `mask` (all of which call it with that mask),
 // exact for |v| < 2^57: the 16-bit low parts and the 32-bit high part are
 // added as 32-bit integers and recombined.
@@ -264,9 +277,10 @@ __device__ __forceinline__ long long group_sum(unsigned mask, long long v) {
 // CIC deposit of every live slot into the fixed-point sums. The slots of a
 // warp sit mostly in a few cells (birth order), so the lanes of each cell
 // first add their contributions (integer sums: the result does not depend on
-// the grouping) and one lane per cell issues the atomics.
+// the grouping) and one lane per cell issues the atomics. The contributions
+// are formed in the run's precision (FP32 runs: no FP64 conversions).
 template <typename T>
-__global__ void k_win_deposit(Win<T> w, Geo g, Phys ph, int np) {
+__global__ void k_win_deposit(Win<T> w, Geo g, Phys ph, PushConst<T> pc, int np) {
   const int nxn = g.nxn;
   const int lane = threadIdx.x & 31;
   constexpr long long kBig = 1LL << 57;
@@ -276,17 +290,31 @@ __global__ void k_win_deposit(Win<T> w, Geo g, Phys ph, int np) {
     const int ci = (p < np) ? w.s.ci[p] : -1;
     long long a[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // n at ci, ci + 1; J_c at ci, ci + 1
     if (ci >= 0) {
-      const double wp = (w.s.id[p] & kIdCR) ? ph.w_cr : ph.w_th;
-      const double f = (double)w.s.f[p];
-      const double c0 = wp * (1.0 - f), c1 = wp * f;
-      const double v[3] = {(double)w.s.v[p], (double)w.s.v[w.cap + p],
-                           (double)w.s.v[2 * w.cap + p]};
-      a[0] = (long long)fix(c0);
-      a[1] = (long long)fix(c1);
+      if constexpr (sizeof(T) == 4) {
+        const float wp = (w.s.id[p] & kIdCR) ? pc.wcr : pc.wth;
+        const float f = w.s.f[p];
+        const float c0 = wp * (1.0f - f), c1 = wp * f;
+        const float v[3] = {w.s.v[p], w.s.v[w.cap + p], w.s.v[2 * w.cap + p]};
+        a[0] = fix32(c0);
+        a[1] = fix32(c1);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        a[2 + 2 * c] = (long long)fix(c0 * v[c]);
-        a[3 + 2 * c] = (long long)fix(c1 * v[c]);
+        for (int c = 0; c < 3; ++c) {
+          a[2 + 2 * c] = fix32(c0 * v[c]);
+          a[3 + 2 * c] = fix32(c1 * v[c]);
+        }
+      } else {
+        const double wp = (w.s.id[p] & kIdCR) ? ph.w_cr : ph.w_th;
+        const double f = (double)w.s.f[p];
+        const double c0 = wp * (1.0 - f), c1 = wp * f;
+        const double v[3] = {(double)w.s.v[p], (double)w.s.v[w.cap + p],
+                             (double)w.s.v[2 * w.cap + p]};
+        a[0] = (long long)fix(c0);
+        a[1] = (long long)fix(c1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          a[2 + 2 * c] = (long long)fix(c0 * v[c]);
+          a[3 + 2 * c] = (long long)fix(c1 * v[c]);
+        }
       }
     }
     bool big = false;
@@ -1341,7 +1369,8 @@ void forward_step(fs_window* w, Win<T>& r, int n, int k) {
                                                       push_const<T>(w->ph), n, np, w->ninj[n],
                                                       w->first_id[n], ib);
   const int np1 = w->np_at[n + 1];
-  if (np1 > 0) k_win_deposit<T><<<blocks(np1), kBlock, 0, w->st>>>(r, w->g, w->ph, np1);
+  if (np1 > 0) k_win_deposit<T><<<blocks(np1), kBlock, 0, w->st>>>(r, w->g, w->ph, push_const<T>(w->ph),
+                                                        np1);
   k_win_fields<T><<<tiles(w->g.nx), kTbThreads, fields_smem(w->p.n_sub, sizeof(T)), w->st>>>(
       r, w->g, w->ph, field_const<T>(w->ph), w->p.n_sub, r.Bx, tn, tu, tr, tB);
   std::swap(r.B, r.Bx);  // the step's B went to the other buffer
@@ -1394,7 +1423,8 @@ int do_forward(fs_window* w, const double* theta, double* loss) {
                                                           amps + M, M);
   cudaMemsetAsync(r.q, 0, 8 * 4 * (size_t)w->g.nxn, w->st);
   const int np0 = w->np_at[0];
-  if (np0 > 0) k_win_deposit<T><<<blocks(np0), kBlock, 0, w->st>>>(r, w->g, w->ph, np0);
+  if (np0 > 0) k_win_deposit<T><<<blocks(np0), kBlock, 0, w->st>>>(r, w->g, w->ph, push_const<T>(w->ph),
+                                                        np0);
   k_win_moments<T><<<blocks(w->g.nxn), kBlock, 0, w->st>>>(r, w->g, w->ph);
   k_ohm<T, 1><<<blocks(w->g.nxn), kBlock, 0, w->st>>>(r.B, r.n, r.u, nullptr, r.E, r.Bb,
                                                        nullptr, w->g, w->ph);
