@@ -49,7 +49,7 @@ struct Win {
   double *lB, *lBx;            // of B [3][nx] (and the buffer the next one goes to)
   double *lE, *lBb;            // of E, Bbar [3][nxn]
   double *lNm, *lUm;           // of the moments that E^n used [nxn], [3][nxn]
-  double *lNr, *lJ;            // of the deposit sums (raw density, current)
+  T *lNr, *lJ;                 // of the deposit sums (raw density, current), run precision
   double* grad;                // d loss / d theta [M + 2]
 };
 
@@ -492,16 +492,16 @@ __device__ __forceinline__ void curl_adj_point(const double Pc[4], const double 
 template <typename T>
 __device__ __forceinline__ void moments_adj_node(int i, const T* nN, const T* uN,
                                                  const T* nraw, double ln, const double lu[3],
-                                                 double* lNr, double* lJ, const Geo& g,
+                                                 T* lNr, T* lJ, const Geo& g,
                                                  const Phys& ph) {
   const int nxn = g.nxn;
   const double sc = (i == 0 || i == g.nx) ? 2.0 : 1.0;
   const double n = (double)nN[i];
   for (int c = 0; c < 3; ++c) {
-    lJ[c * nxn + i] = lu[c] / n * sc;
+    lJ[c * nxn + i] = (T)(lu[c] / n * sc);
     ln -= lu[c] * (double)uN[c * nxn + i] / n;
   }
-  lNr[i] = ((double)nraw[i] < ph.n_floor) ? 0.0 : ln * sc;
+  lNr[i] = (T)(((double)nraw[i] < ph.n_floor) ? 0.0 : ln * sc);
 }
 
 // ------------------------------------------------ blocked field kernels
@@ -912,19 +912,21 @@ __device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const S
       w.lv[p] = w.lv[cap + p] = w.lv[2 * cap + p] = (T)0;
       return -1;
     }
-    // ---- deposit at the state after the step
+    // ---- deposit at the state after the step (in the run's precision)
     const uint32_t id = w.s.id[p];
-    const double wp = (id & kIdCR) ? ph.w_cr : ph.w_th;
-    const double f1 = (double)t1.f[p];
-    const double v1[3] = {(double)t1.v[p], (double)t1.v[cap + p], (double)t1.v[2 * cap + p]};
-    double lf1 = (double)w.lf[p];
-    double lv[3] = {(double)w.lv[p], (double)w.lv[cap + p], (double)w.lv[2 * cap + p]};
+    A wp;
+    if constexpr (sizeof(T) == 4) wp = (id & kIdCR) ? pc.wcr : pc.wth;
+    else wp = (id & kIdCR) ? ph.w_cr : ph.w_th;
+    const A f1 = t1.f[p];
+    const A v1[3] = {t1.v[p], t1.v[cap + p], t1.v[2 * cap + p]};
+    A lf1 = w.lf[p];
+    A lv[3] = {w.lv[p], w.lv[cap + p], w.lv[2 * cap + p]};
     {
-      double dj = w.lNr[c1 + 1] - w.lNr[c1];
+      A dj = w.lNr[c1 + 1] - w.lNr[c1];
       for (int c = 0; c < 3; ++c) {
-        const double ja = w.lJ[c * nxn + c1], jb = w.lJ[c * nxn + c1 + 1];
+        const A ja = w.lJ[c * nxn + c1], jb = w.lJ[c * nxn + c1 + 1];
         dj += (jb - ja) * v1[c];
-        lv[c] += wp * ((1.0 - f1) * ja + f1 * jb);
+        lv[c] += wp * (((A)1 - f1) * ja + f1 * jb);
       }
       lf1 += wp * dj;
     }
@@ -937,10 +939,10 @@ __device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const S
         const double dmu = (1.0 - s1) / pv;
         const double dsn = (sn > 0.0) ? -mu * dmu / sn : 0.0;
         const double dvx = pv * dmu - 1.0, dvy = pv * dsn * U[1], dvz = pv * dsn * U[2];
-        gucr += lv[0] * dvx + lv[1] * dvy + lv[2] * dvz;
+        gucr += (double)lv[0] * dvx + (double)lv[1] * dvy + (double)lv[2] * dvz;
         const double ix = floor(X);
         if (ix >= 0.0 && ix < (double)g.nx)  // placement not clamped
-          gucr += lf1 * U[3] * dvx * ph.dtdx;
+          gucr += (double)lf1 * U[3] * dvx * ph.dtdx;
       }
       w.lf[p] = (T)0;
       w.lv[p] = w.lv[cap + p] = w.lv[2 * cap + p] = (T)0;
@@ -984,10 +986,11 @@ __device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const S
       const double gf = (Xo + av) / av;
       const double fraw = gf * vnx * ph.dtdx;
       double Lx = lv[0], Ly = lv[1], Lz = lv[2];
+      const double lf1d = lf1;
       double lXo = 0.0, lav = 0.0;
       if (fraw >= 0.0 && fraw < 1.0) {
-        Lx += lf1 * gf * ph.dtdx;
-        const double lgf = lf1 * vnx * ph.dtdx;
+        Lx += lf1d * gf * ph.dtdx;
+        const double lgf = lf1d * vnx * ph.dtdx;
         lXo = lgf / av;
         lav = -lgf * Xo / (av * av);
       }
@@ -1005,10 +1008,10 @@ __device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const S
       lvp[2] = (A)(Lw * vp[2] / wv);
       lf0 = (A)lXo;
     } else {
-      lvp[0] = (A)(lv[0] + lf1 * ph.dtdx);
-      lvp[1] = (A)lv[1];
-      lvp[2] = (A)lv[2];
-      lf0 = (A)lf1;
+      lvp[0] = lv[0] + lf1 * pc.dtdx;
+      lvp[1] = lv[1];
+      lvp[2] = lv[2];
+      lf0 = lf1;
     }
     // ---- Boris adjoint: v+ = q + em, q = vm + p x s, p = vm + vm x t,
     //      s = (2 / (1 + t.t)) t, t = hdt B, vm = v + em, em = hdt E
@@ -1294,8 +1297,8 @@ Win<T> win_ptrs(fs_window* w) {
   r.lBb = (double*)tka(fb);
   r.lNm = (double*)tka(fb);
   r.lUm = (double*)tka(fb);
-  r.lNr = (double*)tka(fb);
-  r.lJ = (double*)tka(fb);
+  r.lNr = (T*)tka(fb);
+  r.lJ = (T*)tka(fb);
   r.grad = (double*)(w->base + w->o_params) + 2 * w->M;
   return r;
 }
