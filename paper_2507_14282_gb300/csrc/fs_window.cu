@@ -1068,15 +1068,30 @@ __device__ __forceinline__ int particle_adj_slot(int p, const Win<T>& w, const S
   }
 }
 
+// An FP32 value as an FP64 one (exact) by integer operations on its bit
+// pattern (the conversion instruction runs on GB300's narrow FP64 pipe):
+// sign kept, exponent rebiased, significand shifted into place; zero and
+// subnormals (below 2^-126) give zero, infinities and NaN stay so.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)s);
+  const unsigned long long ed = (e == 0xFFu) ? 0x7FFull : (unsigned long long)(e + 896u);
+  const unsigned long long m = (unsigned long long)(b & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(s | (ed << 52) | m));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 // Adds one slot's shares (out of particle_adj_slot) to lE, lBb at c0, c0 + 1.
 template <typename T>
 __device__ __forceinline__ void add_node_shares(const Win<T>& w, int nxn, int c0, const T a[12]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    atomicAdd(&w.lE[c * nxn + c0], (double)a[4 * c]);
-    atomicAdd(&w.lE[c * nxn + c0 + 1], (double)a[4 * c + 1]);
-    atomicAdd(&w.lBb[c * nxn + c0], (double)a[4 * c + 2]);
-    atomicAdd(&w.lBb[c * nxn + c0 + 1], (double)a[4 * c + 3]);
+    atomicAdd(&w.lE[c * nxn + c0], widen(a[4 * c]));
+    atomicAdd(&w.lE[c * nxn + c0 + 1], widen(a[4 * c + 1]));
+    atomicAdd(&w.lBb[c * nxn + c0], widen(a[4 * c + 2]));
+    atomicAdd(&w.lBb[c * nxn + c0 + 1], widen(a[4 * c + 3]));
   }
 }
 // Adjoint of one step for every slot p < np1 (slots alive at the end of the
@@ -1120,11 +1135,16 @@ __global__ void __launch_bounds__(kBlock, 4)
     }
     if (c0 >= 0) add_node_shares<T>(w, nxn, c0, a);
   }
-  gu2 = warp_sum_d(gu2);
-  gucr = warp_sum_d(gucr);
-  if ((threadIdx.x & 31) == 0) {
-    if (gucr != 0.0) atomicAdd(&w.grad[M], gucr);
-    if (gu2 != 0.0) atomicAdd(&w.grad[M + 1], gu2);
+  // only slots that were returned or injected add to these: most warps have
+  // none (tested on the bit patterns, off the FP64 pipe)
+  const bool any = __double_as_longlong(gu2) != 0 || __double_as_longlong(gucr) != 0;
+  if (__any_sync(0xffffffffu, any)) {
+    gu2 = warp_sum_d(gu2);
+    gucr = warp_sum_d(gucr);
+    if ((threadIdx.x & 31) == 0) {
+      if (gucr != 0.0) atomicAdd(&w.grad[M], gucr);
+      if (gu2 != 0.0) atomicAdd(&w.grad[M + 1], gu2);
+    }
   }
 }
 
