@@ -98,3 +98,13 @@ def test_window_query_sizes_and_rejections(fs):
     assert q(c_light=50.0)[0] == -1          # no relativistic ions
     assert q(bc_x=fs.FS_BC_PERIODIC)[0] == -1
     assert q(steps=0)[0] == -1 and q(ckpt=0)[0] == -1 and q(n=-1)[0] == -1
+
+
+def test_fp64_fma_rate_rejects_bad_arguments(fs):
+    # checked before any CUDA call, so this runs without a GPU
+    import ctypes as C
+    out = C.c_double()
+    L = fs.lib()
+    assert L.fs_fp64_fma_rate(0, None, C.byref(out)) == -1  # FS_EINVAL
+    assert L.fs_fp64_fma_rate((1 << 24) + 1, None, C.byref(out)) == -1  # FS_EINVAL
+    assert L.fs_fp64_fma_rate(16, None, None) == -1  # FS_EINVAL
