@@ -423,9 +423,10 @@ __global__ void __launch_bounds__(kBlock) k_win_loss(const T* B, Geo g, Phys ph,
 
 // ---------------------------------------------------------------- adjoint
 // Adjoint of Ohm's law at one node of the 1D grid with n, u frozen. In: the
-// centre fields Bm, Bp of the node's two cells (clamped at the walls), the
-// density n at the node and np, nm at its neighbours (mirrored at the walls),
-// u at the node and the adjoint (lex, ley, lez) of E there. Out: the
+// centre fields Bm, Bp of the node's two cells (clamped at the walls), 1/n
+// at the node (in) and the pressure term pgx = -T_e (n(i+1) - n(i-1))/(2 dx)
+// (neighbours mirrored at the walls; both fixed while n is), u at the node
+// and the adjoint (lex, ley, lez) of E there. Out: the
 // adjoints of Bbar_y, Bbar_z, dB_y/dx, dB_z/dx at the node (P), that of n at
 // the node (ln), the weight lp of n at the right neighbour (its negative at
 // the left one: the pressure term's two-point difference) and the adjoint
@@ -436,9 +437,9 @@ struct OhmAdj {
   double P[4], ln, lp, lu[3];
 };
 __device__ __forceinline__ OhmAdj ohm_adj_point(const double Bm[3], const double Bp[3],
-                                                double n, double np, double nm,
-                                                const double u[3], double lex, double ley,
-                                                double lez, const Phys& ph) {
+                                                double in, double pgx, const double u[3],
+                                                double lex, double ley, double lez,
+                                                const Phys& ph) {
   const double idx = ph.idx, te = ph.te, jcr = ph.jcr, eta = ph.eta;
   const double bbx = 0.5 * (Bm[0] + Bp[0]);
   const double bby = 0.5 * (Bm[1] + Bp[1]);
@@ -446,7 +447,6 @@ __device__ __forceinline__ OhmAdj ohm_adj_point(const double Bm[3], const double
   const double dby = (Bp[1] - Bm[1]) * idx;
   const double dbz = (Bp[2] - Bm[2]) * idx;
   const double ux = u[0], uy = u[1], uz = u[2];
-  const double in = 1.0 / n;
   OhmAdj r;
   r.P[0] = lex * (-dby * in + uz) + lez * (-jcr * in - ux);
   r.P[1] = lex * (-dbz * in - uy) + ley * (jcr * in + ux);
@@ -455,7 +455,6 @@ __device__ __forceinline__ OhmAdj ohm_adj_point(const double Bm[3], const double
   const double cax = -dbz * bbz - dby * bby;
   const double cay = dby * bbx + jcr * bbz;
   const double caz = -jcr * bby + dbz * bbx;
-  const double pgx = -(te * ((np - nm) * ph.hdx));
   r.ln = -(lex * (pgx + cax) + ley * cay + lez * caz) * in * in;
   r.lp = -lex * in * te * ph.hdx;
   r.lu[0] = ley * bbz - lez * bby;
@@ -594,7 +593,7 @@ inline size_t fields_smem(int n_sub, size_t tsz) {
 }
 inline size_t rk4_adj_smem(int n_sub, size_t tsz) {
   const size_t L = kTbCells + 2 * halo_rk4_adj(n_sub), Ln = L + 1;
-  return tsz * (9 * L + 7 * Ln) + 8 * ((12 * (size_t)n_sub + 12) * L + 11 * Ln);
+  return tsz * (9 * L + 7 * Ln) + 8 * ((12 * (size_t)n_sub + 12) * L + 12 * Ln);
 }
 
 // One step's moments (and their tape) from the deposit sums, B's tape, the
@@ -702,7 +701,9 @@ __global__ void __launch_bounds__(kTbThreads)
   double* lU = lN + Ln;             // [3][Ln]
   double* lnS = lU + 3 * Ln;        // [Ln]
   double* lpS = lnS + Ln;           // [Ln]
-  T* sB = (T*)(lpS + Ln);           // [3][L]
+  double* sIn = lpS + Ln;           // [Ln] 1/n at M^{n+1}
+  double* sPg = sIn + Ln;           // [Ln] its pressure term
+  T* sB = (T*)(sPg + Ln);           // [3][L]
   T* sBs = sB + 3 * L;
   T* sK = sBs + 3 * L;
   T* sE = sK + 3 * L;               // [3][Ln]
@@ -728,6 +729,13 @@ __global__ void __launch_bounds__(kTbThreads)
     }
   }
   __syncthreads();
+  // n is frozen at M^{n+1}: 1/n and the pressure term once per node (first
+  // read in 2., many barriers later)
+  for (int i = t0; i < Ln; i += nt) {
+    const int gi = t.lo + i;
+    sIn[i] = 1.0 / (double)sn[i];
+    sPg[i] = -(ph.te * (((double)sn[t.node(gi + 1)] - (double)sn[t.node(gi - 1)]) * ph.hdx));
+  }
   // 1.
   for (int sub = 0; sub < ns; ++sub) {
     for (int stage = 1; stage <= 4; ++stage) {
@@ -770,8 +778,7 @@ __global__ void __launch_bounds__(kTbThreads)
         const double Bm[3] = {y[cm], y[L + cm], y[2 * L + cm]};
         const double Bp[3] = {y[cp], y[L + cp], y[2 * L + cp]};
         const double u[3] = {(double)su[i], (double)su[Ln + i], (double)su[2 * Ln + i]};
-        const OhmAdj r = ohm_adj_point(Bm, Bp, (double)sn[i], (double)sn[t.node(gi + 1)],
-                                       (double)sn[t.node(gi - 1)], u, 0.0, (gz - gzm) * idx,
+        const OhmAdj r = ohm_adj_point(Bm, Bp, sIn[i], sPg[i], u, 0.0, (gz - gzm) * idx,
                                        (gym - gy) * idx, ph);
 #pragma unroll
         for (int q = 0; q < 4; ++q) P[q * Ln + i] = r.P[q];
@@ -850,8 +857,9 @@ __global__ void __launch_bounds__(kTbThreads)
     const int ipn = (gi + 1 > nx) ? 2 * nx - (gi + 1) : gi + 1;
     const int imn = (gi - 1 < 0) ? -(gi - 1) : gi - 1;
     const double u[3] = {(double)u0[gi], (double)u0[nxn + gi], (double)u0[2 * nxn + gi]};
-    const OhmAdj r = ohm_adj_point(Bm, Bp, (double)n0[gi], (double)n0[ipn], (double)n0[imn], u,
-                                   w.lE[gi], w.lE[nxn + gi], w.lE[2 * nxn + gi], ph);
+    const double pg = -(ph.te * (((double)n0[ipn] - (double)n0[imn]) * ph.hdx));
+    const OhmAdj r = ohm_adj_point(Bm, Bp, 1.0 / (double)n0[gi], pg, u, w.lE[gi],
+                                   w.lE[nxn + gi], w.lE[2 * nxn + gi], ph);
     P[0][k] = r.P[0] + w.lBb[nxn + gi];
     P[1][k] = r.P[1] + w.lBb[2 * nxn + gi];
     P[2][k] = r.P[2];
