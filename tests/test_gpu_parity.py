@@ -106,6 +106,19 @@ def test_fp64_1d_ragged_field_tiles_bit_exact(fs, nx, n_sub):
         assert_state_equal(gpu, ref, fs)
 
 
+@pytest.mark.parametrize("nx", [3, 8])
+def test_fp64_1d_grid_smaller_than_a_field_tile_bit_exact(fs, nx):
+    # the whole grid inside one 64-cell field tile and its halo: both walls
+    # in the same tile
+    cfg = W.scaled(W.CONFIG_1D, nx=nx, ppc=8, tile_x=min(nx, 4))
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ref = O.Oracle(**{k: v for k, v in cfg.items() if k != "tile_x"})
+    for chunk in (1, 9):
+        gpu.step(chunk)
+        ref.step(chunk)
+        assert_state_equal(gpu, ref, fs)
+
+
 @pytest.mark.parametrize("tile", [(4, 2), (8, 4), (16, 1), (2, 8)])
 def test_fp64_2d_bit_exact_several_tiles(fs, tile):
     cfg = W.scaled(W.CONFIG_2D, nx=64, ny=16, ppc=8, mach_a=10.0, theta_bn_deg=20.0,
@@ -393,18 +406,24 @@ def test_inject_round_trip(fs, prec, with_ids):
 
 
 # ---------------------------------------------------------------- FP32
-@pytest.mark.parametrize("dim", [1, 2, "2-ragged"])
+@pytest.mark.parametrize("dim", [1, 2, "2-ragged", "2-tiny", "2-odd"])
 def test_fp32_fields_within_tolerance(fs, dim):
     if dim == 1:
         cfg = W.scaled(W.CONFIG_1D, nx=256)
     elif dim == 2:
         cfg = W.scaled(W.CONFIG_2D_FP32, nx=64, ny=16, ppc=16)
+    elif dim == "2-tiny":
+        # the whole box in one 32 x 16-cell field tile, rows repeated by the
+        # periodic halo
+        cfg = W.scaled(W.CONFIG_2D_FP32, nx=5, ny=3, ppc=16)
+    elif dim == "2-odd":
+        cfg = W.scaled(W.CONFIG_2D_FP32, nx=33, ny=17, ppc=16, tile_x=3, tile_y=1)
     else:
         # the 2D field advance runs on 32 x 16-cell tiles: partial tiles in
         # x and y, three substeps (halo 4, then 5 in the last)
         cfg = W.scaled(W.CONFIG_2D_FP32, nx=72, ny=20, ppc=16, n_sub=3)
     gpu = fs.FauxShock(precision=fs.FS_FP32, **cfg)
-    ref = O.Oracle(**cfg)
+    ref = O.Oracle(**{k: v for k, v in cfg.items() if k not in ("tile_x", "tile_y")})
     gpu.step(1)
     ref.step(1)
     for gw, ow in GRIDS:
