@@ -98,6 +98,13 @@ def test_window_query_sizes_and_rejections(fs):
     assert q(c_light=50.0)[0] == -1          # no relativistic ions
     assert q(bc_x=fs.FS_BC_PERIODIC)[0] == -1
     assert q(steps=0)[0] == -1 and q(ckpt=0)[0] == -1 and q(n=-1)[0] == -1
+    # the reverse sweep keeps a tile's RK4 stage inputs in shared memory (at
+    # most 227 KB a CTA): FP64 up to 9 substeps, FP32 up to 10
+    assert q(precision=fs.FS_FP64, n_sub=9)[0] == 0
+    assert q(precision=fs.FS_FP64, n_sub=10)[0] == -1
+    assert q(precision=fs.FS_FP32, n_sub=10)[0] == 0
+    assert q(precision=fs.FS_FP32, n_sub=11)[0] == -1
+    assert q(n_sub=0)[0] == -1
 
 
 def test_fp64_fma_rate_rejects_bad_arguments(fs):
