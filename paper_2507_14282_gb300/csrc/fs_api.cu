@@ -401,20 +401,23 @@ void release_events(fs_handle* h) {
 }  // namespace
 
 namespace {
-// Runs f(lo, hi) over [0, n) in slices on up to 16 host threads.
+// Runs f(lo, hi) over [0, n) in slices on up to 16 host threads. If a
+// thread cannot be started, the slices it would have taken run on the
+// calling thread (no exception leaves this function).
 template <typename F>
 void parallel_slices(long long n, F f) {
   const unsigned hw = std::thread::hardware_concurrency();
   long long nt = std::min<long long>(hw ? hw : 1, 16);
   nt = std::max<long long>(1, std::min<long long>(nt, n / (1 << 16)));
-  if (nt == 1) {
-    f(0LL, n);
-    return;
-  }
   std::vector<std::thread> th;
-  th.reserve((size_t)nt);
-  for (long long k = 0; k < nt; ++k)
-    th.emplace_back(f, n * k / nt, n * (k + 1) / nt);
+  long long k = 1;  // slice 0 runs here
+  try {
+    th.reserve((size_t)nt);
+    for (; k < nt; ++k) th.emplace_back(f, n * k / nt, n * (k + 1) / nt);
+  } catch (...) {
+  }
+  f(0LL, n / nt);
+  for (long long r = k; r < nt; ++r) f(n * r / nt, n * (r + 1) / nt);
   for (auto& x : th) x.join();
 }
 

@@ -3,7 +3,9 @@
 // fs_f64.cu (the latter compiled with -fmad=false).
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "fs_push.cuh"
 #include "fs_spectra.cuh"
@@ -20,26 +22,37 @@ inline int grid_for(long long n, int block = kBlock) {
 template <typename T, int DIM, int CH, int NS, bool REL>
 cudaError_t launch_push(Sim* s, int in, long long step) {
   const PushLayout<T, DIM> L(s->g.TX, s->g.TY, CH, NS);
-  static size_t attr_bytes = 0;  // largest dynamic shared memory enabled so far
+  // per kernel instance: the largest dynamic shared memory enabled so far and
+  // the occupancy at the last size asked for (host threads may share them)
+  static std::mutex mu;
+  static size_t attr_bytes = 0;
   static size_t occ_bytes = 0;
-  static int occ_blocks = 1, n_sm = 0;
-  if (L.bytes > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_push<T, DIM, CH, NS, REL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)L.bytes);
-    if (e != cudaSuccess) return e;
-    attr_bytes = L.bytes;
-  }
-  if (L.bytes != occ_bytes) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, k_push<T, DIM, CH, NS, REL>,
-                                                        kBlock, L.bytes);
-    if (e != cudaSuccess) return e;
-    if (occ_blocks < 1) return cudaErrorInvalidConfiguration;
-    occ_bytes = L.bytes;
+  static int occ_blocks_c = 1, n_sm_c = 0;
+  int occ_blocks, n_sm;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (L.bytes > attr_bytes) {
+      cudaError_t e = cudaFuncSetAttribute(k_push<T, DIM, CH, NS, REL>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)L.bytes);
+      if (e != cudaSuccess) return e;
+      attr_bytes = L.bytes;
+    }
+    if (L.bytes != occ_bytes) {
+      int dev = 0, nsm = 0, occ = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push<T, DIM, CH, NS, REL>,
+                                                          kBlock, L.bytes);
+      if (e != cudaSuccess) return e;
+      if (occ < 1) return cudaErrorInvalidConfiguration;
+      n_sm_c = nsm;
+      occ_blocks_c = occ;
+      occ_bytes = L.bytes;
+    }
+    occ_blocks = occ_blocks_c;
+    n_sm = n_sm_c;
   }
   StepArgs a;
   a.g = s->g;
@@ -150,12 +163,12 @@ struct OpsImpl {
     static_assert(sizeof(T) == 4, "the tiled field advance is the FP32 path");
     DevPtrs<T> d = P(s);
     constexpr size_t smem = field_tile_smem<T>();
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr(false);  // set once per process; setting it twice is harmless
+    if (!attr.load()) {
       cudaError_t e = cudaFuncSetAttribute(k_field_substep2<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      attr = true;
+      attr.store(true);
     }
     const dim3 grid((s->g.nx + kFTX - 1) / kFTX, (s->g.ny + kFTY - 1) / kFTY);
     T* src = d.B;
@@ -178,12 +191,16 @@ struct OpsImpl {
   static cudaError_t fields_tiled1(Sim* s) {
     DevPtrs<T> d = P(s);
     const size_t smem = field1_smem<T>(s->p.n_sub);
-    static size_t attr = 0;
-    if (smem > attr) {
+    // the largest size enabled so far; a raise races harmlessly (each caller
+    // sets at least its own size before it launches)
+    static std::atomic<size_t> attr(0);
+    if (smem > attr.load()) {
       cudaError_t e = cudaFuncSetAttribute(k_field_step1<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      attr = smem;
+      size_t cur = attr.load();
+      while (smem > cur && !attr.compare_exchange_weak(cur, smem)) {
+      }
     }
     const int grid = (s->g.nx + kF1 - 1) / kF1;
     k_field_step1<T><<<grid, kF1Threads, smem, s->stream>>>(d.B, d.Bs, d.n, d.u, d.E, d.Bb, d.G,
