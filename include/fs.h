@@ -46,6 +46,7 @@ extern "C" {
 #define FS_ECUDA (-5)         /* a CUDA call or kernel launch failed */
 #define FS_ETIMEOUT (-6)      /* reserved: a bounded device wait ran out */
 #define FS_EUNSTABLE (-7)     /* fs_diag: field integrator beyond its RK4 stability bound */
+#define FS_ENOMEM (-8)        /* a host memory allocation failed */
 
 /* precision of particle and field arithmetic */
 #define FS_FP64 0

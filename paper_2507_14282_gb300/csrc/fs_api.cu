@@ -457,6 +457,7 @@ __global__ void __launch_bounds__(256) k_fp64_fma(double* sink, int iters, doubl
 extern "C" {
 
 int fs_params_default(int dim, fs_params* out) {
+  FS_GUARD_BEGIN
   if (!out || (dim != 1 && dim != 2)) return FS_EINVAL;
   memset(out, 0, sizeof(*out));
   out->dim = dim;
@@ -501,9 +502,11 @@ int fs_params_default(int dim, fs_params* out) {
   out->spec_pmin = 1.0;
   out->spec_pmax = 1.0e4;
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_query(const fs_params* p, fs_sizes* out) {
+  FS_GUARD_BEGIN
   if (!out) return FS_EINVAL;
   Geo g;
   Phys ph;
@@ -518,10 +521,12 @@ int fs_query(const fs_params* p, fs_sizes* out) {
   out->tile_y = g.TY;
   out->nxn = g.nxn;
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_init(const fs_params* p, void* device_mem, size_t device_bytes,
             void* cuda_stream, fs_handle** out) {
+  FS_GUARD_BEGIN
   if (!out) return FS_EINVAL;
   *out = nullptr;
   fs_handle* h = new (std::nothrow) fs_handle();
@@ -600,9 +605,11 @@ int fs_init(const fs_params* p, void* device_mem, size_t device_bytes,
   if (r) { delete h; return r; }
   *out = h;
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_step(fs_handle* h, int nsteps) {
+  FS_GUARD_BEGIN
   if (!h || nsteps < 0) return FS_EINVAL;
   Sim* s = &h->sim;
   if (s->sticky) return s->sticky;
@@ -640,11 +647,13 @@ int fs_step(fs_handle* h, int nsteps) {
     s->steps_direct++;
   }
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_inject(fs_handle* h, long long n, const int* ci, const int* cj,
               const double* fx, const double* fy, const double* vx,
               const double* vy, const double* vz, const unsigned* ids) {
+  FS_GUARD_BEGIN
   if (!h || n < 0) return FS_EINVAL;
   Sim* s = &h->sim;
   if (n == 0) return FS_OK;
@@ -760,9 +769,11 @@ int fs_inject(fs_handle* h, long long n, const int* ci, const int* cj,
   r = redeposit(s);
   if (r) return s->sticky = r;
   return sync_and_check(s);
+  FS_GUARD_END
 }
 
 int fs_load_fields(fs_handle* h, const double* B_host) {
+  FS_GUARD_BEGIN
   if (!h || !B_host) return FS_EINVAL;
   Sim* s = &h->sim;
   int r = sync_and_check(s);
@@ -780,9 +791,11 @@ int fs_load_fields(fs_handle* h, const double* B_host) {
     return s->sticky = FS_ECUDA;
   if (s->ops->ohm_final(s) != cudaSuccess) return s->sticky = FS_ECUDA;
   return sync_and_check(s);
+  FS_GUARD_END
 }
 
 int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes, int dst_on_device) {
+  FS_GUARD_BEGIN
   if (!h || !dst) return FS_EINVAL;
   Sim* s = &h->sim;
   int r = sync_and_check(s);
@@ -864,9 +877,11 @@ int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes, int dst_on_d
       o[q * planes + c] = dbl ? ((double*)tmp.data())[c * npts + q]
                               : (double)((float*)tmp.data())[c * npts + q];
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_num_particles(fs_handle* h, long long* n) {
+  FS_GUARD_BEGIN
   if (!h || !n) return FS_EINVAL;
   Sim* s = &h->sim;
   int r = sync_and_check(s);
@@ -879,11 +894,13 @@ int fs_num_particles(fs_handle* h, long long* n) {
   for (int c : cnt) tot += (c < s->g.tile_cap ? c : s->g.tile_cap);
   *n = tot;
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_get_particles(fs_handle* h, long long cap, int* ci, int* cj, double* fx,
                      double* fy, double* vx, double* vy, double* vz, unsigned* id,
                      long long* n) {
+  FS_GUARD_BEGIN
   if (!h || !n) return FS_EINVAL;
   Sim* s = &h->sim;
   long long tot = 0;
@@ -932,9 +949,11 @@ int fs_get_particles(fs_handle* h, long long cap, int* ci, int* cj, double* fx,
     }
   }
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_diag(fs_handle* h, fs_diag_t* out) {
+  FS_GUARD_BEGIN
   if (!h || !out) return FS_EINVAL;
   Sim* s = &h->sim;
   int r = sync_and_check(s);
@@ -970,9 +989,11 @@ int fs_diag(fs_handle* h, fs_diag_t* out) {
   out->launches = s->launches;
   out->max_z = c.sums[5];
   return out->max_z > FS_RK4_Z_MAX ? FS_EUNSTABLE : FS_OK;
+  FS_GUARD_END
 }
 
 int fs_profile(fs_handle* h, int enable) {
+  FS_GUARD_BEGIN
   if (!h) return FS_EINVAL;
   if (enable) {
     h->profiling = true;
@@ -982,9 +1003,11 @@ int fs_profile(fs_handle* h, int enable) {
   h->profiling = false;
   release_events(h);
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_profile_read(fs_handle* h, double* ms, long long* counts, int nphases) {
+  FS_GUARD_BEGIN
   if (!h || !ms || !counts || nphases < 1 || nphases > FS_NPHASES) return FS_EINVAL;
   Sim* s = &h->sim;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return s->sticky = FS_ECUDA;
@@ -1009,15 +1032,18 @@ int fs_profile_read(fs_handle* h, double* ms, long long* counts, int nphases) {
     h->counts[k] = 0;
   }
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_destroy(fs_handle* h) {
+  FS_GUARD_BEGIN
   if (!h) return FS_EINVAL;
   cudaStreamSynchronize(h->sim.stream);
   release_events(h);
   release_graphs(&h->sim);
   delete h;
   return FS_OK;
+  FS_GUARD_END
 }
 
 
@@ -1126,6 +1152,7 @@ void batch_fail(fs_batch* b, int code) {
 
 int fs_batch_plan(int nruns, const long long* n_particles, const int* ntiles, int ncta_max,
                   int* ncta_out) {
+  FS_GUARD_BEGIN
   if (nruns < 1 || !n_particles || !ntiles || !ncta_out || nruns > ncta_max) return FS_EINVAL;
   long double total = 0;
   for (int r = 0; r < nruns; ++r) {
@@ -1161,17 +1188,21 @@ int fs_batch_plan(int nruns, const long long* n_particles, const int* ntiles, in
     ++sum;
   }
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_batch_query(int nruns, int precision, size_t* table_bytes) {
+  FS_GUARD_BEGIN
   if (nruns < 1 || !table_bytes || (precision != FS_FP32 && precision != FS_FP64))
     return FS_EINVAL;
   *table_bytes = batch_map_offset(nruns, precision) + sizeof(int2) * (size_t)kBatchMaxCtas;
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t table_bytes,
                   fs_batch** out) {
+  FS_GUARD_BEGIN
   if (!runs || nruns < 1 || !table_dev || !out) return FS_EINVAL;
   *out = nullptr;
   for (int r = 0; r < nruns; ++r) {
@@ -1252,9 +1283,11 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
   }
   *out = b;
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_batch_step(fs_batch* b, int nsteps) {
+  FS_GUARD_BEGIN
   if (!b || nsteps < 0) return FS_EINVAL;
   for (fs_handle* h : b->runs)
     if (h->sim.sticky) return h->sim.sticky;
@@ -1288,9 +1321,11 @@ int fs_batch_step(fs_batch* b, int nsteps) {
     }
   }
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_batch_destroy(fs_batch* b) {
+  FS_GUARD_BEGIN
   if (!b) return FS_EINVAL;
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (int p = 0; p < 2; ++p)
@@ -1302,11 +1337,13 @@ int fs_batch_destroy(fs_batch* b) {
   cudaGetLastError();
   delete b;
   return FS_OK;
+  FS_GUARD_END
 }
 
 extern "C" {
 
 int fs_fp64_fma_rate(int iters, void* cuda_stream, double* ops_per_s) {
+  FS_GUARD_BEGIN
   if (!ops_per_s || iters < 1 || iters > (1 << 24)) return FS_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int dev = 0, nsm = 0, occ = 0;
@@ -1333,6 +1370,7 @@ int fs_fp64_fma_rate(int iters, void* cuda_stream, double* ops_per_s) {
   if (!ok) return FS_ECUDA;
   *ops_per_s = (double)grid * 256.0 * kFmaChains * (double)iters / (ms * 1e-3);
   return FS_OK;
+  FS_GUARD_END
 }
 
 const char* fs_strerror(int status) {
@@ -1345,6 +1383,7 @@ const char* fs_strerror(int status) {
     case FS_ECUDA: return "CUDA error";
     case FS_ETIMEOUT: return "device wait timed out";
     case FS_EUNSTABLE: return "field solve unstable";
+    case FS_ENOMEM: return "host memory exhausted";
   }
   return "unknown status";
 }

@@ -1,6 +1,7 @@
 // fs_internal.h -- host-side state shared by the C ABI (fs_api.cu) and the
 // per-precision kernel translation units (fs_f32.cu, fs_f64.cu).
 #pragma once
+#include <new>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -109,6 +110,18 @@ struct DevPtrs {
 // The push's per-step constants in the run's precision, formed on the host:
 // kernel parameters of that type are operands the push reads as they are,
 // with no FP64 conversion on the device.
+// Body guard of every C entry point: no C++ exception leaves the library
+// (a failed host allocation returns FS_ENOMEM, anything else FS_ECUDA).
+#define FS_GUARD_BEGIN try {
+#define FS_GUARD_END                     \
+  }                                      \
+  catch (const std::bad_alloc&) {        \
+    return FS_ENOMEM;                    \
+  }                                      \
+  catch (...) {                          \
+    return FS_ECUDA;                     \
+  }
+
 template <typename T>
 struct PushConst {
   T dtdx, dtdy, hdt;  // dt/dx, dt/dy, dt/2

@@ -1546,18 +1546,21 @@ extern "C" {
 
 int fs_window_query(const fs_params* p, int steps, int ckpt_every, long long n_init,
                     int n_modes, size_t* bytes) {
+  FS_GUARD_BEGIN
   if (!bytes) return FS_EINVAL;
   Geo g;
   Phys ph;
   int cap;
   size_t off[11];
   return window_sizes(p, steps, ckpt_every, n_init, n_modes, &g, &ph, &cap, bytes, off);
+  FS_GUARD_END
 }
 
 int fs_window_init(const fs_params* p, int steps, int ckpt_every, long long n_init,
                    const double* x_init, const double* v_init, int n_modes,
                    const double* mode_phase, int loss_i0, void* dev_buf, size_t bytes,
                    void* cuda_stream, fs_window** out) {
+  FS_GUARD_BEGIN
   if (!out || (n_init > 0 && (!x_init || !v_init)) || (n_modes > 0 && !mode_phase) || !dev_buf)
     return FS_EINVAL;
   *out = nullptr;
@@ -1639,27 +1642,36 @@ int fs_window_init(const fs_params* p, int steps, int ckpt_every, long long n_in
   }
   *out = w;
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_window_forward(fs_window* w, const double* theta, double* loss) {
+  FS_GUARD_BEGIN
   if (!w || !theta || !loss) return FS_EINVAL;
   return w->tsz == 8 ? do_forward<double>(w, theta, loss) : do_forward<float>(w, theta, loss);
+  FS_GUARD_END
 }
 
 int fs_window_backward(fs_window* w, double dloss, double* grad) {
+  FS_GUARD_BEGIN
   if (!w || !grad) return FS_EINVAL;
   return w->tsz == 8 ? do_backward<double>(w, dloss, grad) : do_backward<float>(w, dloss, grad);
+  FS_GUARD_END
 }
 
 int fs_window_counts(fs_window* w, long long* out5) {
+  FS_GUARD_BEGIN
   if (!w || !out5) return FS_EINVAL;
   for (int k = 0; k < 5; ++k) out5[k] = w->counts[k];
   return FS_OK;
+  FS_GUARD_END
 }
 
 int fs_window_destroy(fs_window* w) {
+  FS_GUARD_BEGIN
   delete w;
   return FS_OK;
+  FS_GUARD_END
 }
 
 }  // extern "C"

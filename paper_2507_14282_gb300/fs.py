@@ -25,6 +25,7 @@ FS_PROFILE_B, FS_SPECTRUM_BPERP = 10, 11
 FS_SPECTRUM_P_CR, FS_SPECTRUM_P_ALL = 12, 13
 ID_MASK, ID_CR, ID_RETURNED = 0x3FFFFFFF, 0x40000000, 0x80000000
 FS_EUNSTABLE = -7
+FS_ENOMEM = -8
 FS_RK4_Z_MAX = 2.8284271247461903  # 2 sqrt 2: RK4 on the imaginary axis
 
 

@@ -66,6 +66,7 @@ def test_query_rejects_bad_parameters(fs, bad):
 def test_strerror_names(fs):
     assert fs.strerror(0) == "ok"
     assert "capacity" in fs.strerror(-2)
+    assert "memory" in fs.strerror(fs.FS_ENOMEM)
     assert fs.strerror(-99) == "unknown status"
 
 
