@@ -166,6 +166,46 @@ def test_parallel_mode_dispersion_cold_plasma(k, branch):
     assert slope == pytest.approx(-w, rel=0.01)
 
 
+def _field_only_run(dim, n_sub, dt=0.1, steps=40):
+    # No particles and a density floor of 1: the moments are n = 1, u = 0 at
+    # every node, so a step is n_sub RK4 substeps of the Hall-MHD field
+    # equation dB/dt = -curl E(B) alone. Two modes of a few per cent keep the
+    # nonlinear terms present.
+    nx, ny, dx = (64, 1, 0.5) if dim == 1 else (16, 16, 0.5)
+    sim = O.Oracle(dim=dim, nx=nx, ny=ny, dx=dx, dy=dx, dt=dt, ppc=8, init_plasma=0,
+                   inject_thermal=0, bc_x=O.BC_PERIODIC, mach_a=0.0, beta_i=0.0,
+                   beta_e=0.0, n_floor=1.0, n_sub=n_sub, theta_bn_deg=30.0 * (dim - 1))
+    xc = (np.arange(nx) + 0.5) * dx
+    yc = (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(xc, yc)
+    k = 2 * np.pi / (nx * dx)
+    B = sim.grid(O.GRID_B)
+    if dim == 1:
+        B[0, :, 1] += 1e-2 * np.cos(4 * k * xc) + 5e-3 * np.cos(8 * k * xc + 1.0)
+        B[0, :, 2] += 1e-2 * np.sin(4 * k * xc)
+    else:
+        B[:, :, 1] += 1e-2 * np.sin(k * X)
+        B[:, :, 2] += 1e-2 * np.cos(k * X + 2 * k * Y)
+    sim.set_B(B)
+    sim.step(steps)
+    return sim.grid(O.GRID_B)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_field_integrator_is_fourth_order(dim):
+    # Classical RK4 (the field advance of the hybrid step): over a fixed time,
+    # the error against a run with 256 substeps per step falls by 2^4 = 16 for
+    # each halving of the substep. A stage evaluated at the wrong time or
+    # combined with the wrong weight leaves a consistent but lower-order
+    # scheme (ratios 2, 4 or 8), which the dispersion pins alone could miss.
+    ref = _field_only_run(dim, 256)
+    errs = [float(np.abs(_field_only_run(dim, n) - ref).max()) for n in (1, 2, 4, 8)]
+    assert errs[0] > 1e-8  # well above rounding, the convergence is measurable
+    ratios = [a / b for a, b in zip(errs, errs[1:])]
+    for r in ratios:
+        assert 14.5 < r < 18.5, (errs, ratios)
+
+
 def test_bell_growth_rate_matches_sec31_kmax():
     # Sec. 3.1: J_CR ~ 0.2 n_g v_A gives k_max ~ 0.1/d_i. With the current as
     # a prescribed uniform x-current in Ohm's law, cold linear theory gives
