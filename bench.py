@@ -64,6 +64,10 @@ GRID_WORDS_PER_CELL = 23
 # multiply, fused multiply-add, compare and the reciprocal counted once:
 # gather weights 6 + sums 24, Boris 33, move ~10, deposit 26.
 FP64_OPS_PER_PARTICLE_STEP = 100
+FP64_OPS_SOURCE = "hand count of the written scheme"
+PHASE_TIMING = ("value: the product path (graph replay, no phase events); phases and "
+                "kernel_ms: a second pass of the same run with per-phase CUDA events "
+                "(steps launched directly)")
 # FP64 throughput of GB300: 1.25 TFLOP/s nominal counts an FMA as two; the
 # scheme issues unfused adds and multiplies, one operation per pipe slot.
 # The roofline takes the rate measured on the GPU (fs_fp64_fma_rate), this
@@ -184,8 +188,12 @@ def replica_value(n_mean: float, steps: int, ms_local: float, dist, device="cpu"
 
 
 def timed_run(fs, torch, params: dict, prec, steps: int, warmup: int, dist, device,
-              sample_clocks: bool, local_rank: int):
-    """Device-resident timing of `steps` steps; returns measurements."""
+              sample_clocks: bool, local_rank: int, prof_steps: int):
+    """Device-resident timing of `steps` steps on the product path (fs_step
+    replaying its captured CUDA graph, no per-phase events), then a second,
+    profiled pass of `prof_steps` steps whose per-phase CUDA events (recorded
+    by the library on its stream; the steps launch directly) give the phase
+    and dominant-kernel durations. Returns measurements."""
     sim = fs.FauxShock(device=device, precision=prec, **params)
     stream = sim.stream
     sim.step(warmup)
@@ -201,10 +209,6 @@ def timed_run(fs, torch, params: dict, prec, steps: int, warmup: int, dist, devi
         time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    # per-phase events (the fused push kernel among them) are recorded by the
-    # library on the same stream inside the timed region
-    sim.profile(True)
-    sim.profile_read()
     e0.record(stream)
     for _ in range(steps):
         sim.step(1)
@@ -214,17 +218,27 @@ def timed_run(fs, torch, params: dict, prec, steps: int, warmup: int, dist, devi
         dist.barrier()
     clocks = clk.stop() if clk else None
     ms = e0.elapsed_time(e1)
-    phases = sim.profile_read()
-    sim.profile(False)
     d = sim.diag()
     n1 = d["n_particles"]
     launches = d["launches"] - l0
-    # per-launch duration of the dominant kernel (the fused particle step),
-    # measured with events around single launches on the same stream
+    # second pass: per-phase events, the fused particle step among them
+    sim.profile(True)
+    sim.profile_read()
+    e0.record(stream)
+    for _ in range(prof_steps):
+        sim.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = e0.elapsed_time(e1)
+    phases = sim.profile_read()
+    sim.profile(False)
+    n2 = sim.num_particles()
     sizes = sim.sizes
     out = dict(ms_total=ms, n_mean=0.5 * (n0 + n1), launches=launches, clocks=clocks,
                sim=sim, tiles=sizes.tiles, tile=(sizes.tile_x, sizes.tile_y),
-               phases={k: v[0] / max(v[1], 1) for k, v in phases.items()})
+               phases={k: v[0] / max(v[1], 1) for k, v in phases.items()},
+               prof_ms_per_step=ms_prof / max(prof_steps, 1), prof_steps=prof_steps,
+               prof_n_mean=0.5 * (n1 + n2))
     return out
 
 
@@ -247,14 +261,14 @@ def ours(args):
         fp64_peak = FP64_PEAK_OPS
         fp64_src = "derived from nominal FP64 1.25 TFLOP/s (FMA=2)"
     res64 = timed_run(fs, torch, FP64_WORKLOAD, fs.FS_FP64, args.steps, args.warmup, dist,
-                      device, True, local_rank)
+                      device, True, local_rank, args.prof_steps)
     value, t64 = replica_value(res64["n_mean"], args.steps, res64["ms_total"], dist, device)
     ms_step = t64 / args.steps
     pb64 = particle_bytes(8, 2)
     grid_b64 = GRID_WORDS_PER_CELL * 8 / FP64_WORKLOAD["ppc"]
     step_bw64 = res64["n_mean"] * (pb64 + grid_b64) / (ms_step * 1e-3) / 1e9
     kern64 = res64["phases"]["push"]
-    achieved_ops = res64["n_mean"] * FP64_OPS_PER_PARTICLE_STEP / (kern64 * 1e-3) / 1e12
+    achieved_ops = res64["prof_n_mean"] * FP64_OPS_PER_PARTICLE_STEP / (kern64 * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_push<double,2>",
                 "achieved": achieved_ops, "peak": fp64_peak / 1e12,
                 "unit": "TFLOP/s (FP64 ops)",
@@ -263,11 +277,16 @@ def ours(args):
                 "traffic": traffic_per_launch("fp64", res64["n_mean"]),
                 "traffic_unit": "bytes per launch",
                 "kernel_ms": kern64,
-                "hbm_achieved_gbs": res64["n_mean"] * pb64 / (kern64 * 1e-3) / 1e9,
-                "hbm_peak_gbs": hbm, "hbm_frac": res64["n_mean"] * pb64 / (kern64 * 1e-3) / 1e9 / hbm,
+                "ops_per_particle_step": FP64_OPS_PER_PARTICLE_STEP,
+                "ops_source": FP64_OPS_SOURCE,
+                "hbm_achieved_gbs": res64["prof_n_mean"] * pb64 / (kern64 * 1e-3) / 1e9,
+                "hbm_peak_gbs": hbm,
+                "hbm_frac": res64["prof_n_mean"] * pb64 / (kern64 * 1e-3) / 1e9 / hbm,
                 "peak_source": fp64_src,
                 "step_hbm_frac": step_bw64 / hbm,
-                "phases_ms": res64["phases"]}
+                "phases_ms": res64["phases"],
+                "timing": PHASE_TIMING,
+                "profiled_ms_per_step": res64["prof_ms_per_step"]}
     gpu_launches = res64["launches"]
     res64["sim"].close()
     del res64["sim"]
@@ -276,13 +295,13 @@ def ours(args):
     fp32 = None
     if not args.skip_fp32:
         res32 = timed_run(fs, torch, FP32_WORKLOAD, fs.FS_FP32, args.steps32, args.warmup,
-                          dist, device, False, local_rank)
+                          dist, device, False, local_rank, args.prof_steps)
         v32, t32 = replica_value(res32["n_mean"], args.steps32, res32["ms_total"], dist, device)
         ms32 = t32 / args.steps32
         pb32 = particle_bytes(4, 2)
         gb32 = GRID_WORDS_PER_CELL * 4 / FP32_WORKLOAD["ppc"]
         kern32 = res32["phases"]["push"]
-        ach = res32["n_mean"] * pb32 / (kern32 * 1e-3) / 1e9
+        ach = res32["prof_n_mean"] * pb32 / (kern32 * 1e-3) / 1e9
         fp32 = {"workload": FP32_NAME, "value": v32, "unit": UNIT, "ms_per_step": ms32,
                 "steps": args.steps32, "n_particles": res32["n_mean"],
                 "bytes_per_particle_step": pb32 + gb32,
@@ -292,12 +311,15 @@ def ours(args):
                              "traffic": traffic_per_launch("fp32", res32["n_mean"]),
                              "traffic_unit": "bytes per launch",
                              "kernel_ms": kern32, "peak_source": peak_src},
-                "phases_ms": res32["phases"],
+                "phases_ms": res32["phases"], "timing": PHASE_TIMING,
+                "profiled_ms_per_step": res32["prof_ms_per_step"],
                 "vs_fp64": v32 / value, "gpu_launches": res32["launches"]}
         gpu_launches += res32["launches"]
         res32["sim"].close()
         del res32["sim"]
         torch.cuda.empty_cache()
+        if not args.skip_err:
+            fp32["err_vs_fp64"] = fp32_error_vs_fp64(fs, torch, device)
 
     ens = None
     if not args.skip_ensemble:
@@ -392,6 +414,45 @@ def ensemble(fs, torch, args, hbm, peak_src):
                               "peak_source": peak_src},
             "tiles": {k: v for k, v in sorted(tuner.cache.items())},
             "tune_s": tune_s, "status_ok": all(x == 0 for x in status)}
+
+
+FIELD_NAMES = ("B", "E", "Bbar", "n", "J", "u")
+
+
+def fp32_error_vs_fp64(fs, torch, device):
+    """Relative L2 error of every field and moment of the FP32 precision form
+    against the same box (8192 x 512 cells, 64 ppc, seed 3) run by the plain
+    FP64 method on the GPU, after 1 and after 100 steps from fresh handles.
+    "rel_l2" divides by the FP64 field's norm; "rel_l2_fluct" by the norm of
+    its departure from the initial uniform state (B0, motional E, n = 1,
+    u = -M_A x), the sharper figure for the fields that stay near it."""
+    import numpy as np
+    whats = (fs.FS_B, fs.FS_E, fs.FS_BBAR, fs.FS_N, fs.FS_J, fs.FS_U)
+    f32 = fs.FauxShock(device=device, precision=fs.FS_FP32, **FP32_WORKLOAD)
+    f64 = fs.FauxShock(device=device, precision=fs.FS_FP64, **FP32_WORKLOAD)
+    g0 = [f64.grid(w) for w in whats]
+    out = {}
+    for label, k in (("after_1_step", 1), ("after_100_steps", 99)):
+        f32.step(k)
+        f64.step(k)
+        a = [f32.grid(w) for w in whats]
+        b = [f64.grid(w) for w in whats]
+        rel = {n: float(np.linalg.norm(x - y) / np.linalg.norm(y))
+               for n, x, y in zip(FIELD_NAMES, a, b)}
+        fl = {n: float(np.linalg.norm(x - y) / max(np.linalg.norm(y - z), 1e-300))
+              for n, x, y, z in zip(FIELD_NAMES, a, b, g0)}
+        d32, d64 = f32.diag(), f64.diag()
+        out[label] = {"rel_l2": rel, "rel_l2_fluct": fl,
+                      "reflected": [d32["reflected"], d64["reflected"]],
+                      "injected": [d32["injected"], d64["injected"]]}
+    f32.close()
+    f64.close()
+    del f32, f64
+    torch.cuda.empty_cache()
+    out["reference"] = ("the same box in FP64 on the GPU (bit-exact to the FP64 oracle "
+                        "in the parity tests)")
+    out["tolerance"] = {"after_1_step": 1e-5, "after_100_steps": 1e-3}
+    return out
 
 
 WINDOW_NAME = ("differentiable window, 1D faux-shock box: 2048 cells, 128 ppc (262k ions), "
@@ -538,10 +599,42 @@ def reference(args):
 
 
 def ncu_case(args):
-    """A small run of the benchmark's kernels for ncu captures: the FP64 or
-    FP32 workload on a smaller grid, init then a few steps, no timing."""
+    """A small run of the benchmark's kernels for ncu captures, no timing:
+    fp64 / fp32: the workload (on a smaller grid with --nx/--ny), init then
+    --steps steps; ensemble: the 64-run batched ensemble (tiles from the
+    autotuner), 3 batched steps then --steps more; window: one forward and
+    one forward + backward of the differentiable window in FP32 (--steps
+    window steps, checkpoints every 20)."""
     import torch
     from paper_2507_14282_gb300 import fs
+    if args.ncu_case == "ensemble":
+        from paper_2507_14282_gb300 import tune
+        from tests.workloads import config4_runs
+        runs = [tune.Autotuner().tile(r) for r in config4_runs(64)]
+        sims = [fs.FauxShock(**r) for r in runs]
+        b = fs.FsBatch(sims)
+        b.step(3)
+        b.step(args.steps)
+        torch.cuda.synchronize()
+        ok = all(s.diag()["status"] == 0 for s in sims)
+        b.close()
+        print(json.dumps({"ncu_case": "ensemble", "runs": len(sims), "steps": 3 + args.steps,
+                          "status_ok": ok}))
+        return
+    if args.ncu_case == "window":
+        from paper_2507_14282_gb300 import window as Wn
+        from tests import window_inputs as WI
+        X, V = WI.plasma(2048, 128)
+        amps, ph = WI.modes()
+        w = Wn.FauxShockWindow(X, V, ph, steps=args.steps, ckpt=20, nx=2048, ny=1, ppc=128,
+                               precision=1, cr_enable=1, fs_mode_thermal=1, p_iso=100.0,
+                               n_cr_ratio=0.01, **WI.COMMON)
+        th = WI.theta(amps)
+        w.forward(th)
+        L, g = w.loss_and_grad(th)
+        w.close()
+        print(json.dumps({"ncu_case": "window", "steps": args.steps, "loss": L}))
+        return
     base = FP64_WORKLOAD if args.ncu_case == "fp64" else FP32_WORKLOAD
     p = dict(base)
     if args.nx:
@@ -560,7 +653,7 @@ def ncu_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--ncu-case", choices=["fp64", "fp32"], default=None,
+    ap.add_argument("--ncu-case", choices=["fp64", "fp32", "ensemble", "window"], default=None,
                     help="run a small case of the benchmark kernels for ncu")
     ap.add_argument("--nx", type=int, default=0)
     ap.add_argument("--ny", type=int, default=0)
@@ -576,6 +669,10 @@ def main():
     ap.add_argument("--ens-steps", type=int, default=50)
     ap.add_argument("--skip-ensemble", action="store_true")
     ap.add_argument("--skip-window", action="store_true")
+    ap.add_argument("--skip-err", action="store_true",
+                    help="skip the FP32-vs-FP64 field error of the precision form")
+    ap.add_argument("--prof-steps", type=int, default=20,
+                    help="steps of the profiled pass that gives the phase timings")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args)

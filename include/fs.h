@@ -44,9 +44,10 @@ extern "C" {
 #define FS_ENAN (-3)          /* non-finite particle motion */
 #define FS_EIDOVERFLOW (-4)   /* more than 2^30 particle ids issued */
 #define FS_ECUDA (-5)         /* a CUDA call or kernel launch failed */
-#define FS_ETIMEOUT (-6)      /* reserved: a bounded device wait ran out */
+#define FS_ETIMEOUT (-6)      /* a bounded device wait ran out */
 #define FS_EUNSTABLE (-7)     /* fs_diag: field integrator beyond its RK4 stability bound */
 #define FS_ENOMEM (-8)        /* a host memory allocation failed */
+#define FS_EBADCELL (-9)      /* a particle found outside its tile (corrupted state) */
 
 /* precision of particle and field arithmetic */
 #define FS_FP64 0
@@ -265,15 +266,21 @@ int fs_profile_read(fs_handle* h, double* ms, long long* counts, int nphases);
      n            [ny][nxn]     ion density at the nodes (after the floor)
      u            [3][ny][nxn]  ion bulk velocity at the nodes
      E_out        [3][ny][nxn]  electric field at the nodes
-   nxn = nx + 1 (faux-shock box) or nx (periodic box). FP64 only.
+   nxn = nx + 1 (faux-shock box) or nx (periodic box). FP64 only. Apart
+   from B_out == B_in, no output may share a byte with another output or an
+   input (FS_EINVAL).
    Returns FS_EINVAL for a NULL pointer, FS_FP32, an invalid parameter set,
-   or a grid whose stage buffers (6 nx ny + 3 nxn ny doubles) exceed the
-   static array; FS_ECUDA when a CUDA call fails. Enqueues on cuda_stream.
-   The first call on a device looks up the array's device address (once per
-   device); make that first call before any stream capture. Every call on a
-   device shares the one array, and it keeps the last call's contents (each
-   call writes the stages before reading them): calls that overlap on the GPU
-   -- on different streams, or from different threads -- race. */
+   overlapping buffers, or a grid whose stage buffers (6 nx ny + 3 nxn ny
+   doubles) exceed the static array; FS_ECUDA when a CUDA call fails.
+   Enqueues on cuda_stream. A call made while cuda_stream is not being
+   captured looks up the array's device address on the current device (a
+   host-side lookup, no synchronisation) and remembers it; a call made during
+   stream capture uses the address remembered from an earlier call on that
+   device, so make the first call on a device before any stream capture (a
+   first call under capture returns FS_EINVAL). Every call on a device
+   shares the one array, and it keeps the last call's contents (each call
+   writes the stages before reading them): calls that overlap on the GPU --
+   on different streams, or from different threads -- race. */
 int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
                              const double* n, const double* u, double* B_out,
                              double* E_out, void* cuda_stream);
@@ -331,6 +338,22 @@ int fs_destroy(fs_handle* h);
 
 /* Name of a status code. */
 const char* fs_strerror(int status);
+
+/* Failure-detection self-test (an addition of this library, with no
+   counterpart in the paper). Every device wait of the particle push is
+   bounded: after a fixed number of tries it gives up, records a timeout bit
+   in the simulation's device status word and returns, and the next
+   synchronising call reports FS_ETIMEOUT, so a lost copy cannot hang the
+   GPU. This call exercises that path on purpose without a fault: it launches
+   one CTA that waits with the same bounded wait, at most `limit` tries
+   (1 <= limit <= 2^20), on an mbarrier that nothing arrives on and no copy
+   targets. The wait runs out, the CTA sets the timeout bit in *status_dev
+   (one int of device memory owned by the caller; the call zeroes it first)
+   and returns with nothing in flight. Synchronises cuda_stream and returns
+   the code of the status word: FS_ETIMEOUT when the wait ran out (the
+   expected result), FS_OK if it completed, FS_EINVAL for a NULL pointer or
+   a limit out of range, FS_ECUDA for a failed launch or copy. */
+int fs_selftest_wait(int limit, int* status_dev, void* cuda_stream);
 
 /* Measurement utility (not part of the method): this GPU's FP64
    fused multiply-add rate, the denominator of the FP64 push's roofline.

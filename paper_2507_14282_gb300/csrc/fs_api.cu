@@ -252,7 +252,8 @@ int status_to_code(int st) {
   if (st & kStatusTimeout) return FS_ETIMEOUT;
   if (st & kStatusNaN) return FS_ENAN;
   if (st & kStatusIdOverflow) return FS_EIDOVERFLOW;
-  if (st & (kStatusCapacity | kStatusBadCell)) return FS_ECAPACITY;
+  if (st & kStatusCapacity) return FS_ECAPACITY;
+  if (st & kStatusBadCell) return FS_EBADCELL;
   return FS_OK;
 }
 
@@ -1373,6 +1374,21 @@ int fs_fp64_fma_rate(int iters, void* cuda_stream, double* ops_per_s) {
   FS_GUARD_END
 }
 
+int fs_selftest_wait(int limit, int* status_dev, void* cuda_stream) {
+  FS_GUARD_BEGIN
+  if (!status_dev || limit < 1 || limit > (1 << 20)) return FS_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int word = 0;
+  if (cudaMemsetAsync(status_dev, 0, sizeof(int), st) != cudaSuccess) return FS_ECUDA;
+  if (launch_wait_selftest(status_dev, limit, st) != cudaSuccess) return FS_ECUDA;
+  if (cudaMemcpyAsync(&word, status_dev, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FS_ECUDA;
+  return status_to_code(word);
+  FS_GUARD_END
+}
+
 const char* fs_strerror(int status) {
   switch (status) {
     case FS_OK: return "ok";
@@ -1384,6 +1400,7 @@ const char* fs_strerror(int status) {
     case FS_ETIMEOUT: return "device wait timed out";
     case FS_EUNSTABLE: return "field solve unstable";
     case FS_ENOMEM: return "host memory exhausted";
+    case FS_EBADCELL: return "particle outside its tile";
   }
   return "unknown status";
 }

@@ -9,4 +9,8 @@ const Ops& ops_f32() {
 size_t push_smem_bytes_f32(int dim, int tx, int ty, int chunk) {
   return push_smem_bytes<float>(dim, tx, ty, chunk);
 }
+cudaError_t launch_wait_selftest(int* status, int limit, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(status, limit);
+  return cudaGetLastError();
+}
 }  // namespace fsx

@@ -31,21 +31,34 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 double* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, not a device address).
-int noalloc_scratch(double** out) {
+// Device address of the scratch array on the current device. The host-side
+// symbol is only a stand-in, not a device address. Outside stream capture
+// the address is looked up on every call (cheap, host-side), so a module
+// loaded again into a new context (after cudaDeviceReset, say) is found at
+// its new address; the last address seen on the device is kept for calls
+// made while `st` is being captured, where the lookup is not made.
+int noalloc_scratch(cudaStream_t st, double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FS_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return FS_EINVAL;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FS_ECUDA;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, fs_noalloc_scratch) != cudaSuccess || !ptr)
       return FS_ECUDA;
     g_scratch_addr[dev] = (double*)ptr;
   }
+  if (!g_scratch_addr[dev]) return FS_EINVAL;  // first call on the device made under capture
   *out = g_scratch_addr[dev];
   return FS_OK;
+}
+
+// [a, a + na) and [b, b + nb) share a byte
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
 }
 
 template <int DIM>
@@ -77,6 +90,7 @@ extern "C" int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
                                         const double* n, const double* u,
                                         double* B_out, double* E_out,
                                         void* cuda_stream) {
+  FS_GUARD_BEGIN
   if (!p || !B_in || !n || !u || !B_out || !E_out) return FS_EINVAL;
   if (p->precision != FS_FP64) return FS_EINVAL;
   fsx::Geo g;
@@ -85,10 +99,24 @@ extern "C" int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
   if (r) return r;
   const size_t nc = (size_t)g.nx * g.ny, nn = (size_t)g.nxn * g.ny;
   if (6 * nc + 3 * nn > kNoAllocScratchDoubles) return FS_EINVAL;
-  double* scr = nullptr;
-  r = noalloc_scratch(&scr);
-  if (r) return r;
+  // the outputs share no byte with each other or with the inputs, except
+  // B_out == B_in exactly (the field advanced in place)
+  const size_t bB = 3 * nc * sizeof(double), bE = 3 * nn * sizeof(double);
+  const size_t bn = nn * sizeof(double), bu = 3 * nn * sizeof(double);
+  if (B_out != B_in && overlaps(B_out, bB, B_in, bB)) return FS_EINVAL;
+  if (overlaps(B_out, bB, n, bn) || overlaps(B_out, bB, u, bu) ||
+      overlaps(B_out, bB, E_out, bE))
+    return FS_EINVAL;
+  if (overlaps(E_out, bE, n, bn) || overlaps(E_out, bE, u, bu) ||
+      overlaps(E_out, bE, B_in, bB))
+    return FS_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // a launch error left by an earlier, unrelated call is cleared here, so the
+  // check after this call's launches reports only its own
+  (void)cudaGetLastError();
+  double* scr = nullptr;
+  r = noalloc_scratch(st, &scr);
+  if (r) return r;
   if (B_out != B_in &&
       cudaMemcpyAsync(B_out, B_in, 3 * nc * sizeof(double), cudaMemcpyDeviceToDevice,
                       st) != cudaSuccess)
@@ -98,4 +126,5 @@ extern "C" int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
   else
     noalloc_launch<2>(g, ph, p->n_sub, B_out, n, u, E_out, scr, st);
   return cudaGetLastError() == cudaSuccess ? FS_OK : FS_ECUDA;
+  FS_GUARD_END
 }

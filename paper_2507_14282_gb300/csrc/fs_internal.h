@@ -187,6 +187,8 @@ const Ops& ops_f64();
 size_t push_smem_bytes_f32(int dim, int tx, int ty, int chunk);
 size_t push_smem_bytes_f64(int dim, int tx, int ty, int chunk);
 int derive_geometry(const fs_params* p, Geo* g, Phys* ph);
+// one CTA of the bounded-wait self-test (k_wait_selftest) on st
+cudaError_t launch_wait_selftest(int* status, int limit, cudaStream_t st);
 
 struct Sim {
   fs_params p;

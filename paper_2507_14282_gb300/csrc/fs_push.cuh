@@ -74,12 +74,28 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// bounded wait: false if the phase did not complete within the limit
+// bounded wait: false if the phase did not complete within `limit` tries
 constexpr int kWaitLimit = 1 << 20;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          int limit = kWaitLimit) {
+  for (int it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Failure-detection self-test: one CTA waits, with the push's bounded wait,
+// on an mbarrier that nothing arrives on and no bulk copy targets. The wait
+// runs out after `limit` tries; the CTA records the timeout bit in *status
+// (as the push does in its counters) and returns with nothing in flight.
+static __global__ void k_wait_selftest(int* status, int limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u, limit);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
 }
 
 struct StepArgs {

@@ -26,6 +26,7 @@ FS_SPECTRUM_P_CR, FS_SPECTRUM_P_ALL = 12, 13
 ID_MASK, ID_CR, ID_RETURNED = 0x3FFFFFFF, 0x40000000, 0x80000000
 FS_EUNSTABLE = -7
 FS_ENOMEM = -8
+FS_ETIMEOUT, FS_ENAN, FS_ECAPACITY, FS_EBADCELL = -6, -3, -2, -9
 FS_RK4_Z_MAX = 2.8284271247461903  # 2 sqrt 2: RK4 on the imaginary axis
 
 
@@ -127,6 +128,7 @@ def lib():
         L.fs_window_counts.argtypes = [V, V]
         L.fs_window_destroy.argtypes = [V]
         L.fs_fp64_fma_rate.argtypes = [C.c_int, V, P(C.c_double)]
+        L.fs_selftest_wait.argtypes = [C.c_int, V, V]
         _lib = L
     return _lib
 
@@ -146,6 +148,19 @@ def fp64_fma_rate(iters: int = 1 << 14, stream=None) -> float:
     _check(lib().fs_fp64_fma_rate(int(iters), C.c_void_p(st.cuda_stream), C.byref(out)),
            "fs_fp64_fma_rate")
     return out.value
+
+
+def selftest_wait(limit: int = 4096, stream=None) -> int:
+    """fs_selftest_wait: one CTA waits with the push's bounded mbarrier wait on
+    a barrier nothing arrives on; returns the status code (FS_ETIMEOUT when
+    the wait ran out, as it should)."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("selftest_wait needs a CUDA device")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    word = torch.zeros(1, dtype=torch.int32, device=st.device)
+    return int(lib().fs_selftest_wait(int(limit), C.c_void_p(word.data_ptr()),
+                                      C.c_void_p(st.cuda_stream)))
 
 
 def _check(code: int, what: str):
@@ -214,9 +229,11 @@ class FauxShock:
 
     # ----------------------------------------------------------- lifecycle
     def close(self):
+        """Releases the handle, then the device buffer (back to torch's cache)."""
         if getattr(self, "_h", None):
             lib().fs_destroy(self._h)
             self._h = None
+        self._mem = None
 
     def __del__(self):
         try:

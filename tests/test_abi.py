@@ -116,3 +116,19 @@ def test_fp64_fma_rate_rejects_bad_arguments(fs):
     assert L.fs_fp64_fma_rate(0, None, C.byref(out)) == -1  # FS_EINVAL
     assert L.fs_fp64_fma_rate((1 << 24) + 1, None, C.byref(out)) == -1  # FS_EINVAL
     assert L.fs_fp64_fma_rate(16, None, None) == -1  # FS_EINVAL
+
+
+def test_every_entry_point_body_is_guarded():
+    # No C++ exception may cross the C ABI: each function fs.h declares is
+    # defined with its body inside FS_GUARD_BEGIN ... FS_GUARD_END (fs_strerror
+    # only returns string literals)
+    csrc = os.path.join(ROOT, "paper_2507_14282_gb300", "csrc")
+    text = "".join(open(os.path.join(csrc, f)).read() for f in sorted(os.listdir(csrc))
+                   if f.endswith(".cu"))
+    for name in declared_symbols():
+        if name == "fs_strerror":
+            continue
+        m = re.search(r"\bint\s+" + name + r"\s*\([^;{]*\)\s*\{", text)
+        assert m, f"{name}: definition not found"
+        body = text[m.end():m.end() + 400]
+        assert body.lstrip().startswith("FS_GUARD_BEGIN"), f"{name} is not guarded"

@@ -1,10 +1,12 @@
 """Batched ensembles on the GPU: independent runs stepped together through
 fs_batch_* (one push launch over every run's CTA group, the rest of each
 run's step in parallel graph branches) give each run the results of stepping
-it alone -- bit-identical in FP64, within the FP32 tolerance in FP32."""
+it alone -- bit-identical in FP64, within the FP32 tolerance in FP32 -- and,
+in FP64, the FP64 CPU oracle's results for the same run bit for bit."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from tests import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -56,13 +58,7 @@ def state(sim, fs):
     return out
 
 
-def run_both(fs, runs, prec, steps):
-    alone = []
-    for r in runs:
-        s = fs.FauxShock(precision=prec, **r)
-        s.step(steps)
-        alone.append(state(s, fs))
-        s.close()
+def run_batched(fs, runs, prec, steps):
     sims = [fs.FauxShock(precision=prec, **r) for r in runs]
     b = fs.FsBatch(sims)
     b.step(1)            # launched directly
@@ -71,7 +67,17 @@ def run_both(fs, runs, prec, steps):
     b.close()
     for s in sims:
         s.close()
-    return alone, batched
+    return batched
+
+
+def run_both(fs, runs, prec, steps):
+    alone = []
+    for r in runs:
+        s = fs.FauxShock(precision=prec, **r)
+        s.step(steps)
+        alone.append(state(s, fs))
+        s.close()
+    return alone, run_batched(fs, runs, prec, steps)
 
 
 @pytest.mark.parametrize("runs", [RUNS_1D, RUNS_2D], ids=["1d", "2d"])
@@ -87,6 +93,46 @@ def test_fp64_batch_is_bit_identical_to_runs_alone(fs, runs):
                 assert np.array_equal(a[k], b[k]), f"run {r}: {k} differs"
             else:
                 assert a[k] == b[k], f"run {r}: {k} {a[k]} != {b[k]}"
+
+
+def oracle_state(params, steps):
+    ref = O.Oracle(**{k: v for k, v in params.items() if k not in ("tile_x", "tile_y")})
+    ref.step(steps)
+    p = ref.particles()
+    o = np.argsort(p["id"], kind="stable")
+    out = {k: v[o] for k, v in p.items()}
+    for what, name in ((O.GRID_B, "B"), (O.GRID_E, "E"), (O.GRID_N, "n"), (O.GRID_J, "J")):
+        out[name] = ref.grid(what)
+    d = ref.diag()
+    for k in ("step", "n_particles", "next_id", "incident", "transmitted", "reflected",
+              "escaped", "injected"):
+        out["diag_" + k] = d[k]
+    out["energy"] = np.array([d["kinetic"], d["magnetic"], d["fs_energy"],
+                              d["removed_energy"]])
+    ref.close()
+    return out
+
+
+@pytest.mark.parametrize("runs", [RUNS_1D, RUNS_2D], ids=["1d", "2d"])
+def test_fp64_batched_runs_equal_the_oracle(fs, runs):
+    # every run of a mixed batch (lengths, ppc, M_A, theta, beta, dt, tile
+    # shapes, a periodic box) stepped in the batch -- the first step launched
+    # directly, the rest replayed from the captured graphs of both buffer
+    # parities -- holds the oracle's state of that run, bit for bit
+    steps = 12
+    batched = run_batched(fs, runs, fs.FS_FP64, steps)
+    for r, (params, b) in enumerate(zip(runs, batched)):
+        ref = oracle_state(params, steps)
+        assert b["diag_status"] == 0
+        for k in ref:
+            if k == "energy":
+                np.testing.assert_allclose(b[k], ref[k], rtol=1e-12, atol=1e-15,
+                                           err_msg=f"run {r} {k}")
+            elif isinstance(ref[k], np.ndarray):
+                assert b[k].shape == ref[k].shape, f"run {r}: {k} shape"
+                assert np.array_equal(b[k], ref[k]), f"run {r}: {k} differs from the oracle"
+            else:
+                assert b[k] == ref[k], f"run {r}: {k} {b[k]} != oracle {ref[k]}"
 
 
 def rel_l2(a, b):

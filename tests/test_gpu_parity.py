@@ -193,6 +193,42 @@ def test_fp32_full_size_precision_form_invariants(fs):
     assert np.isfinite(E).all() and np.isfinite(gpu.grid(fs.FS_B)).all()
     ez = E[:, 50:-50, 2].mean()
     assert ez == pytest.approx(30.0 * np.sin(np.radians(30.0)), rel=0.02)
+    gpu.close()
+
+
+def test_fp32_full_size_precision_form_error_vs_fp64(fs):
+    # The FP32 precision form at full size (8192 x 512 cells, 64 ppc, 268 M
+    # particles, M_A 30, theta 30 deg, seed 3) next to the same box run by
+    # the plain FP64 method on the GPU, which equals the FP64 oracle bit for
+    # bit (the tests above, up to the full 16.8 M-particle FP64 workload).
+    # Relative L2 of every field and moment against the FP64 run: <= 1e-5
+    # after one step, <= 1e-3 after 100 steps; integer bookkeeping exact in
+    # each run and the injected counts equal (both draw them in FP64).
+    import torch
+    torch.cuda.empty_cache()
+    cfg = W.CONFIG_2D_FP32
+    f32 = fs.FauxShock(precision=fs.FS_FP32, **cfg)
+    f64 = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    n0 = 8192 * 512 * 64
+    assert f32.num_particles() == n0 and f64.num_particles() == n0
+    for steps, tol in ((1, 1e-5), (99, 1e-3)):
+        f32.step(steps)
+        f64.step(steps)
+        errs = {gw: rel_l2(f32.grid(gw), f64.grid(gw)) for gw, _ in GRIDS}
+        for gw, e in errs.items():
+            assert e <= tol, (f32.diag()["step"], gw, errs)
+        d32, d64 = f32.diag(), f64.diag()
+        for d in (d32, d64):
+            assert d["status"] == 0
+            assert d["n_particles"] == n0 + d["injected"] - d["transmitted"] - d["escaped"]
+            assert d["incident"] == d["transmitted"] + d["reflected"]
+        assert d32["injected"] == d64["injected"]
+        sd = 4 * np.sqrt(max(d64["reflected"], 1)) + 2
+        assert abs(d32["reflected"] - d64["reflected"]) <= sd
+    f32.close()
+    f64.close()
+    del f32, f64
+    torch.cuda.empty_cache()
 
 
 def test_fp64_multi_chunk_tiles_bit_exact(fs):

@@ -38,11 +38,12 @@ def planes(t):
     return t.permute(2, 0, 1).contiguous()
 
 
+@pytest.mark.parametrize("in_place", [False, True], ids=["separate", "in-place"])
 @pytest.mark.parametrize("cfg", [
     dict(dim=2, nx=64, ny=16, ppc=8, mach_a=10.0, theta_bn_deg=20.0, dt=0.0025, seed=3),
     dict(dim=1, nx=256, ny=1, ppc=16, mach_a=10.0, dt=0.005, seed=5),
 ])
-def test_noalloc_field_advance_matches_step(fs, cfg):
+def test_noalloc_field_advance_matches_step(fs, cfg, in_place):
     import torch
     sim = fs.FauxShock(precision=fs.FS_FP64, **cfg)
     sim.step(3)
@@ -60,7 +61,8 @@ def test_noalloc_field_advance_matches_step(fs, cfg):
         for what, t in ((fs.FS_N, n), (fs.FS_U, u), (fs.FS_B, B1), (fs.FS_E, E1)):
             sim.grid_device(what, t)
         b_in, u_p = planes(B0), planes(u)
-        b_out = torch.full_like(b_in, np.nan)
+        # in place: B_out is B_in, advanced where it lies
+        b_out = b_in if in_place else torch.full_like(b_in, np.nan)
         e_out = torch.full((3, ny, nxn), np.nan, dtype=torch.float64, device=dev)
         rc = fs.lib().fs_field_advance_noalloc(
             C.byref(p), C.c_void_p(b_in.data_ptr()), C.c_void_p(n.data_ptr()),
@@ -83,3 +85,31 @@ def test_noalloc_rejects_grids_beyond_the_static_array(fs):
     assert rc == -1
     p32 = fs.make_params(dim=1, nx=64, ppc=1, precision=fs.FS_FP32)
     assert fs.lib().fs_field_advance_noalloc(C.byref(p32), ptr, ptr, ptr, ptr, ptr, None) == -1
+
+
+def test_noalloc_rejects_overlapping_buffers(fs):
+    import torch
+    # outputs may not share bytes with each other or with the inputs, except
+    # B_out == B_in exactly
+    p = fs.make_params(dim=1, nx=64, ppc=1, precision=fs.FS_FP64)
+    nc, nn = 64, 65
+    buf = torch.zeros(3 * nc + nn + 3 * nn + 3 * nn + 64, dtype=torch.float64, device="cuda")
+    buf[3 * nc:3 * nc + nn] = 1.0  # n = 1: finite fields in the one accepted call
+    base = buf.data_ptr()
+    B = base
+    n = B + 8 * 3 * nc
+    u = n + 8 * nn
+    E = u + 8 * 3 * nn
+
+    def call(b_in, nn_, uu, b_out, e_out):
+        return fs.lib().fs_field_advance_noalloc(
+            C.byref(p), C.c_void_p(b_in), C.c_void_p(nn_), C.c_void_p(uu),
+            C.c_void_p(b_out), C.c_void_p(e_out), None)
+
+    assert call(B, n, u, B, E) == 0          # in place, disjoint otherwise
+    torch.cuda.synchronize()
+    assert call(B, n, u, B + 8, E) == -1     # B_out partly over B_in
+    assert call(B, n, u, n, E) == -1         # B_out over n
+    assert call(B, n, u, B, u + 8) == -1     # E_out over u
+    assert call(B, n, u, B, n) == -1         # E_out over n
+    assert call(B, n, u, B, B) == -1         # E_out over B
