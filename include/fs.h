@@ -170,6 +170,29 @@ typedef struct fs_diag_t {
 #define FS_SPECTRUM_P_CR 12   /* cosmic-ray species */
 #define FS_SPECTRUM_P_ALL 13  /* all particles */
 
+/* Run state beyond the particles and the field, for checkpoint / restart:
+   fs_moments(FS_STATE) copies it out, fs_restore_state() puts it back. The
+   step counter keys the random draws of the faux-shock return and of the
+   inflow (Philox counter = (particle number, step, purpose), Sec. 2 draws);
+   the row accumulators carry each transverse row's fractional inflow
+   particle (ppc u_sh dt / dx per step, Sec. 2's continuous injection) to
+   the next step. With them, a run saved after N steps (fs_get_particles,
+   fs_moments(FS_B), fs_moments(FS_STATE)) and restored into a fresh handle
+   (init_plasma = 0; fs_load_fields, fs_inject with the saved ids,
+   fs_restore_state) continues as the straight run does: in FP64 bit for bit
+   (the deposit sums do not depend on particle order); the energy sums
+   only to FP64 rounding, their later additions being order dependent. */
+typedef struct fs_run_state {
+  long long step;          /* steps taken */
+  long long next_id;       /* next particle number to issue */
+  long long incident, transmitted, reflected, escaped, injected;  /* flux counters */
+  double fs_energy, injected_energy, removed_energy;  /* energy budget sums */
+  int ny;                  /* rows: entries of the accumulators that follow */
+  int reserved;            /* 0 */
+  /* followed in the same buffer by double row_acc[ny] */
+} fs_run_state;
+#define FS_STATE 14       /* fs_run_state then row_acc[ny]: sizeof(fs_run_state) + 8 ny bytes */
+
 typedef struct fs_handle fs_handle;
 typedef struct fs_batch fs_batch;   /* ensemble of handles stepped together */
 
@@ -177,7 +200,11 @@ typedef struct fs_batch fs_batch;   /* ensemble of handles stepped together */
    Returns FS_EINVAL if out is NULL or dim is not 1 or 2. */
 int fs_params_default(int dim, fs_params* out);
 
-/* Validates *p and reports the device buffer size it needs in *out.
+/* Validates *p -- the problem statement of Sec. 2 (box, inflow speed u_sh =
+   M_A, faux-shock parameters r and u2 of Eq. 1) and the run columns of
+   Table 1 (Delta x, Delta t, M_A, theta_Bn, n_cr/n_g, p_iso) -- and reports
+   the device buffer size it needs in *out: the particle buckets (capacity
+   factor x ppc per cell), the grids, the moments and the counters.
    Allocates nothing. Returns FS_EINVAL for an inconsistent parameter set. */
 int fs_query(const fs_params* p, fs_sizes* out);
 
@@ -189,8 +216,11 @@ int fs_query(const fs_params* p, fs_sizes* out);
 int fs_init(const fs_params* p, void* device_mem, size_t device_bytes,
             void* cuda_stream, fs_handle** out);
 
-/* Appends n particles given on the host: cell indices (ci, cj), in-cell
+/* Appends n kinetic ions given on the host (the particle species of the
+   hybrid model, Sec. 2: a test population, a custom upstream, or a saved
+   run being restored): cell indices (ci, cj), in-cell
    offsets (fx, fy) in [0, 1), velocities (vx, vy, vz); fy/cj ignored in 1D.
+   Layout: n entries per array, x = (ci + fx) dx, y = (cj + fy) dy.
    ids: NULL assigns fresh thermal ids; otherwise each id word (bits 0-29
    particle number, bit 30 cosmic ray, bit 31 returned) is kept. Re-deposits
    the moments and recomputes E from the current B. Synchronises.
@@ -200,8 +230,13 @@ int fs_inject(fs_handle* h, long long n, const int* ci, const int* cj,
               const double* fx, const double* fy, const double* vx,
               const double* vy, const double* vz, const unsigned* ids);
 
-/* Replaces B at the cell centres ([ny][nx][3] doubles on the host) and
-   recomputes E and B at the nodes from the current moments. Synchronises. */
+/* Replaces B at the cell centres ([ny][nx][3] doubles on the host, copied
+   before return) -- e.g. seeded transverse modes like the perturbations the
+   Bell instability of Sec. 3.1 grows from, or a saved field -- and
+   recomputes E from Ohm's law with the massless-electron closure of Sec. 2
+   and B at the nodes, from the current moments. Values are not checked:
+   a non-finite B surfaces as FS_ENAN once particles move through it.
+   Synchronises. */
 int fs_load_fields(fs_handle* h, const double* B_host);
 
 /* Advances nsteps particle steps (Sec. 2's boundary, the hybrid step).
@@ -209,11 +244,25 @@ int fs_load_fields(fs_handle* h, const double* B_host);
    synchronising call. */
 int fs_step(fs_handle* h, int nsteps);
 
-/* Copies a grid quantity (what = FS_*) to dst (dst_bytes large enough:
+/* Copies an output (what = FS_*) to dst (dst_bytes large enough:
    doubles, or int64 for the histograms), on the host or (dst_on_device)
-   in device memory. Synchronises. */
+   in device memory, converted to FP64 in either precision: the fields and
+   ion moments of the hybrid model (Sec. 2: B, E, n, J, u), the y-averaged
+   profiles and B lineouts (Sec. 3.1, Fig. 2), the x - p_x phase space
+   (Fig. 1), the perpendicular power spectrum (Fig. 3 caption), the
+   momentum spectra (Fig. 1 bottom panels) and the run state (FS_STATE).
+   FS_EINVAL for an unknown code or a short buffer. Synchronises. */
 int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes,
                int dst_on_device);
+
+/* Restores the run state saved by fs_moments(FS_STATE) from host memory
+   (state, state_bytes >= sizeof(fs_run_state) + 8 ny): the step counter,
+   next particle number, flux counters, energy sums and inflow row
+   accumulators. Particles and field are not touched (fs_inject,
+   fs_load_fields restore them). Synchronises. FS_EINVAL for a NULL or short
+   buffer, a row count other than the handle's, negative counts or a
+   non-finite accumulator. */
+int fs_restore_state(fs_handle* h, const void* state, size_t state_bytes);
 
 /* Number of live particles. Synchronises. */
 int fs_num_particles(fs_handle* h, long long* n);
@@ -226,7 +275,12 @@ int fs_get_particles(fs_handle* h, long long cap, int* ci, int* cj,
                      double* vz, unsigned* id, long long* n);
 
 /* Diagnostics: FP64 energy/momentum sums, int64 faux-shock flux counters
-   (incident = transmitted + reflected), particle count. Synchronises. */
+   (incident = transmitted + reflected: each crossing either passes or is
+   returned with Eq. 1's probability, Sec. 2), the energy the returns add
+   (the downstream-frame kick of Sec. 2), injected and removed energy,
+   particle count, the sticky status bits and the field integrator's
+   stability number. Synchronises; returns the sticky device error, if any,
+   and FS_EUNSTABLE (with *out filled) above the RK4 bound. */
 int fs_diag(fs_handle* h, fs_diag_t* out);
 
 /* Per-phase timing of fs_step with CUDA events on the handle's stream

@@ -804,6 +804,40 @@ int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes, int dst_on_d
   const Geo& g = s->g;
   const bool dbl = (s->p.precision == FS_FP64);
   const size_t Tsz = dbl ? 8 : 4;
+  if (what == FS_STATE) {
+    const size_t need = sizeof(fs_run_state) + 8 * (size_t)g.ny;
+    if (dst_bytes < need) return FS_EINVAL;
+    Counters c;
+    std::vector<char> blob(need);
+    if (cudaMemcpyAsync(&c, s->base + s->L.ctr, sizeof(c), cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(blob.data() + sizeof(fs_run_state), s->base + s->L.acc,
+                        8 * (size_t)g.ny, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+      return s->sticky = FS_ECUDA;
+    r = sync_and_check(s);
+    if (r) return r;
+    fs_run_state st;
+    memset(&st, 0, sizeof st);
+    st.step = s->step;
+    st.next_id = (long long)c.next_id;
+    st.incident = (long long)c.incident;
+    st.transmitted = (long long)c.transmitted;
+    st.reflected = (long long)c.reflected;
+    st.escaped = (long long)c.escaped;
+    st.injected = (long long)c.injected;
+    st.fs_energy = c.fs_energy;
+    st.injected_energy = c.injected_energy;
+    st.removed_energy = c.removed_energy;
+    st.ny = g.ny;
+    memcpy(blob.data(), &st, sizeof st);
+    if (!dst_on_device) {
+      memcpy(dst, blob.data(), need);
+      return FS_OK;
+    }
+    if (cudaMemcpyAsync(dst, blob.data(), need, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+      return s->sticky = FS_ECUDA;
+    return sync_and_check(s);
+  }
   if (what == FS_HIST_XPX || what == FS_HIST_XPX_CR) {
     const size_t need = 8 * (size_t)s->ph.hist_nx * s->ph.hist_np;
     if (dst_bytes < need) return FS_EINVAL;
@@ -878,6 +912,46 @@ int fs_moments(fs_handle* h, int what, void* dst, size_t dst_bytes, int dst_on_d
       o[q * planes + c] = dbl ? ((double*)tmp.data())[c * npts + q]
                               : (double)((float*)tmp.data())[c * npts + q];
   return FS_OK;
+  FS_GUARD_END
+}
+
+int fs_restore_state(fs_handle* h, const void* state, size_t state_bytes) {
+  FS_GUARD_BEGIN
+  if (!h || !state || state_bytes < sizeof(fs_run_state)) return FS_EINVAL;
+  Sim* s = &h->sim;
+  fs_run_state st;
+  memcpy(&st, state, sizeof st);
+  if (st.ny != s->g.ny || state_bytes < sizeof(fs_run_state) + 8 * (size_t)s->g.ny)
+    return FS_EINVAL;
+  if (st.step < 0 || st.next_id < 0 || st.next_id > (long long)kIdMask + 1 || st.incident < 0 ||
+      st.transmitted < 0 || st.reflected < 0 || st.escaped < 0 || st.injected < 0 ||
+      st.incident != st.transmitted + st.reflected)
+    return FS_EINVAL;
+  std::vector<double> acc(s->g.ny);
+  memcpy(acc.data(), (const char*)state + sizeof(fs_run_state), 8 * (size_t)s->g.ny);
+  for (double a : acc)
+    if (!(a >= 0.0 && a < 1.0)) return FS_EINVAL;
+  int r = sync_and_check(s);
+  if (r) return r;
+  Counters c;
+  if (cudaMemcpy(&c, s->base + s->L.ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return s->sticky = FS_ECUDA;
+  c.step = st.step;
+  c.next_id = (unsigned long long)st.next_id;
+  c.incident = (unsigned long long)st.incident;
+  c.transmitted = (unsigned long long)st.transmitted;
+  c.reflected = (unsigned long long)st.reflected;
+  c.escaped = (unsigned long long)st.escaped;
+  c.injected = (unsigned long long)st.injected;
+  c.fs_energy = st.fs_energy;
+  c.injected_energy = st.injected_energy;
+  c.removed_energy = st.removed_energy;
+  if (cudaMemcpy(s->base + s->L.ctr, &c, sizeof(c), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->base + s->L.acc, acc.data(), 8 * acc.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return s->sticky = FS_ECUDA;
+  s->step = st.step;
+  return sync_and_check(s);
   FS_GUARD_END
 }
 

@@ -23,6 +23,7 @@ FS_B, FS_E, FS_BBAR, FS_N, FS_J, FS_U = 0, 1, 2, 3, 4, 5
 FS_PROFILE_N, FS_PROFILE_DB2, FS_HIST_XPX, FS_HIST_XPX_CR = 6, 7, 8, 9
 FS_PROFILE_B, FS_SPECTRUM_BPERP = 10, 11
 FS_SPECTRUM_P_CR, FS_SPECTRUM_P_ALL = 12, 13
+FS_STATE = 14
 ID_MASK, ID_CR, ID_RETURNED = 0x3FFFFFFF, 0x40000000, 0x80000000
 FS_EUNSTABLE = -7
 FS_ENOMEM = -8
@@ -80,6 +81,18 @@ class FsDiag(C.Structure):
     ]
 
 
+class FsRunState(C.Structure):
+    _fields_ = [
+        ("step", C.c_longlong), ("next_id", C.c_longlong),
+        ("incident", C.c_longlong), ("transmitted", C.c_longlong),
+        ("reflected", C.c_longlong), ("escaped", C.c_longlong),
+        ("injected", C.c_longlong),
+        ("fs_energy", C.c_double), ("injected_energy", C.c_double),
+        ("removed_energy", C.c_double),
+        ("ny", C.c_int), ("reserved", C.c_int),
+    ]
+
+
 class FsError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
@@ -107,6 +120,7 @@ def lib():
         L.fs_step.argtypes = [V, C.c_int]
         L.fs_moments.argtypes = [V, C.c_int, V, C.c_size_t, C.c_int]
         L.fs_num_particles.argtypes = [V, P(C.c_longlong)]
+        L.fs_restore_state.argtypes = [V, V, C.c_size_t]
         L.fs_get_particles.argtypes = [V, C.c_longlong] + [V] * 8 + [P(C.c_longlong)]
         L.fs_diag.argtypes = [V, P(FsDiag)]
         L.fs_destroy.argtypes = [V]
@@ -333,6 +347,48 @@ class FauxShock:
     def load_fields(self, B: np.ndarray):
         b = np.ascontiguousarray(B, dtype=np.float64).reshape(self.ny, self.nx, 3)
         _check(lib().fs_load_fields(self._h, _ptr(b)), "fs_load_fields")
+
+    # ----------------------------------------------------------- checkpoint
+    def run_state(self) -> np.ndarray:
+        """fs_moments(FS_STATE): the run state beyond particles and field
+        (step, next id, flux counters, energy sums, inflow accumulators) as
+        raw bytes; fields(blob) decodes them."""
+        blob = np.zeros(C.sizeof(FsRunState) + 8 * self.ny, dtype=np.uint8)
+        _check(lib().fs_moments(self._h, FS_STATE, _ptr(blob), blob.nbytes, 0), "fs_moments")
+        return blob
+
+    @staticmethod
+    def run_state_fields(blob: np.ndarray) -> dict:
+        st = FsRunState.from_buffer_copy(blob[:C.sizeof(FsRunState)].tobytes())
+        out = {name: getattr(st, name) for name, _ in FsRunState._fields_}
+        out["row_acc"] = blob[C.sizeof(FsRunState):].view(np.float64).copy()
+        return out
+
+    def restore_state(self, blob: np.ndarray):
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(lib().fs_restore_state(self._h, _ptr(b), b.nbytes), "fs_restore_state")
+
+    def checkpoint(self) -> dict:
+        """Everything a restart needs: the particles (with ids), B at the
+        cell centres and the run state."""
+        return {"particles": self.particles(), "B": self.grid(FS_B),
+                "state": self.run_state()}
+
+    @classmethod
+    def restart(cls, ckpt: dict, device: str = "cuda:0", stream=None, **params):
+        """A fresh handle with the same parameters holding a checkpoint: no
+        initial plasma, then the field, the particles with their ids and the
+        run state (fs_load_fields, fs_inject, fs_restore_state)."""
+        params = dict(params)
+        params["init_plasma"] = 0
+        sim = cls(device=device, stream=stream, **params)
+        sim.load_fields(ckpt["B"])
+        p = ckpt["particles"]
+        if len(p["id"]):
+            sim.inject(p["ci"], p["cj"], p["fx"], p["fy"], p["vx"], p["vy"], p["vz"],
+                       ids=p["id"])
+        sim.restore_state(ckpt["state"])
+        return sim
 
 
 def batch_plan(n_particles, ntiles, ncta_max: int) -> list:

@@ -132,3 +132,9 @@ def test_every_entry_point_body_is_guarded():
         assert m, f"{name}: definition not found"
         body = text[m.end():m.end() + 400]
         assert body.lstrip().startswith("FS_GUARD_BEGIN"), f"{name} is not guarded"
+
+
+def test_restore_state_rejects_null_arguments(fs):
+    # checked before any CUDA call
+    L = fs.lib()
+    assert L.fs_restore_state(None, None, 0) == -1
