@@ -60,11 +60,13 @@ def particle_bytes(prec_bytes: int, dim: int) -> int:
 # Grid traffic per cell per step on a single pass (moments write + read 8
 # words, B read + write 6, E write 3, E + Bbar read by the gather 6).
 GRID_WORDS_PER_CELL = 23
-# FP64 operations of the written scheme per particle-step in 2D, each add,
-# multiply, fused multiply-add, compare and the reciprocal counted once:
-# gather weights 6 + sums 24, Boris 33, move ~10, deposit 26.
-FP64_OPS_PER_PARTICLE_STEP = 100
-FP64_OPS_SOURCE = "hand count of the written scheme"
+# FP64-pipe operations of the FP64 push per particle-step in 2D, from ncu
+# (sm__thread_inst_executed_pipe_fp64_pred_on.sum over the particles of one
+# launch of the 1024 x 256-cell case: 408.2 M / 4 194 771; DADD + DMUL + DFMA
+# alone give 96.9); an FMA is one pipe operation, like the denominator.
+FP64_OPS_PER_PARTICLE_STEP = 97.3
+FP64_OPS_SOURCE = ("ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum / particles, "
+                   "1024x256-cell case of the FP64 workload")
 PHASE_TIMING = ("value: the product path (graph replay, no phase events); phases and "
                 "kernel_ms: a second pass of the same run with per-phase CUDA events "
                 "(steps launched directly)")
@@ -80,10 +82,12 @@ FP64_PEAK_OPS = 0.625e12
 # by the particles of a launch; valid only while the kernel sources are the
 # ones the counters were taken on (their hash below), else reported as null.
 PUSH_TRAFFIC = {"fp32": (504.478208e6 + 448.012288e6) / 16779950,
-                "fp64": (224.012032e6 + 175.387904e6) / 4194771}
+                "fp64": (224.020480e6 + 175.140352e6) / 4194771}
 PUSH_SOURCES = ("paper_2507_14282_gb300/csrc/fs_push.cuh",
                 "paper_2507_14282_gb300/csrc/fs_engine.cuh")
-PUSH_SOURCES_SHA1 = "0140520203da97907f67449d38658cb21bdfe49e"
+# hash of PUSH_SOURCES when each precision's counters were taken
+PUSH_SOURCES_SHA1 = {"fp32": "0140520203da97907f67449d38658cb21bdfe49e",
+                     "fp64": "9f0aa318431fb5cb7e16104ebd5bbb9f5d734e6e"}
 
 
 def push_sources_sha1() -> str:
@@ -96,7 +100,7 @@ def push_sources_sha1() -> str:
 
 
 def traffic_per_launch(prec: str, n: float):
-    if push_sources_sha1() != PUSH_SOURCES_SHA1:
+    if push_sources_sha1() != PUSH_SOURCES_SHA1[prec]:
         return None
     return PUSH_TRAFFIC[prec] * n
 
