@@ -345,10 +345,15 @@ int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
    precision and dimension, created on one CUDA stream -- with one push
    launch per step: each run gets a group of persistent CTAs about
    proportional to its particles (a (run, tile) work list, each run's
-   pointers, geometry and physics read from a device table), and the rest of
-   every run's step (movers, injection, moments, field advance) runs in
-   parallel branches of one CUDA graph. Each run's results are those of
-   fs_step on that handle alone (bit-identical in FP64).
+   pointers, geometry and physics read from a device table). When every run
+   is 1D with x walls (the one-launch field advance), the rest of the step --
+   movers, injection, moments, field advance, step counter -- is one launch
+   per kernel over all runs too (each block works for one run, found from
+   per-run block prefixes in the table): about seven launches per step
+   whatever the number of runs. Otherwise each run's remaining kernels run in
+   parallel branches. Either way the step is captured as a CUDA graph. Each
+   run's results are those of fs_step on that handle alone (bit-identical in
+   FP64).
 
    fs_batch_plan: host-only planner of the CTA groups. Runs of
    n_particles[r] particles in ntiles[r] tiles share ncta_max CTAs:

@@ -1142,6 +1142,26 @@ size_t batch_rec_bytes(int precision) {
 size_t batch_map_offset(int nruns, int precision) {
   return up(2 * (size_t)nruns * batch_rec_bytes(precision), kAlign);
 }
+// the block prefixes of the batched step tail (movers, moments, field tiles)
+size_t batch_pre_offset(int nruns, int precision) {
+  return up(batch_map_offset(nruns, precision) + sizeof(int2) * (size_t)kBatchMaxCtas, kAlign);
+}
+size_t batch_table_bytes(int nruns, int precision) {
+  return batch_pre_offset(nruns, precision) + 3 * sizeof(int) * ((size_t)nruns + 1);
+}
+// blocks of the per-run step kernels the batched tail replaces (as step_rest
+// and the 1D field launcher size them)
+int movers_blocks(const Sim& s) { return std::min((s.g.ntiles + 7) / 8, 152 * 16); }
+int moments_blocks(const Sim& s) {
+  const long long nn = (long long)s.g.nxn * s.g.ny;
+  return (int)std::max(1LL, std::min((nn + 255) / 256, 152LL * 16));
+}
+int field1_blocks(const Sim& s) { return (s.g.nx + 63) / 64; }
+// runs whose whole step tail the batched kernels cover: 1D boxes with x
+// walls and the one-launch field advance
+bool tail_batchable(const Sim& s) {
+  return s.g.dim == 1 && s.g.bc_x != FS_BC_PERIODIC && s.p.n_sub <= 16;
+}
 }  // namespace
 
 struct fs_batch {
@@ -1161,6 +1181,10 @@ struct fs_batch {
   int rel = 0;  // some run has relativistic ions (c > 0)
   const Ops* ops = nullptr;
   int parity = 0;  // steps taken, mod 2
+  bool tail_batched = false;  // the step tail runs as one launch per kernel
+  int nblk[3] = {0, 0, 0};    // blocks of the batched movers, moments, field tiles
+  int n_sub_max = 1;
+  int* pre = nullptr;         // their block prefixes in the table
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graphs_ready = false;
   int steps_direct = 0;
@@ -1174,6 +1198,9 @@ cudaError_t batch_enqueue(fs_batch* b, int p, cudaStream_t st) {
   cudaError_t e = b->ops->push_batch(b->dim, b->rel, b->table + (size_t)p * nr * b->rec, b->map,
                                      b->ncta, b->smem, st);
   if (e != cudaSuccess) return e;
+  if (b->tail_batched)
+    return b->ops->batch_rest(b->table + (size_t)p * nr * b->rec, b->pre, nr, b->nblk,
+                              b->n_sub_max, st);
   if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
   const int K = (int)b->branch.size();
   for (int k = 0; k < K; ++k)
@@ -1270,7 +1297,7 @@ int fs_batch_query(int nruns, int precision, size_t* table_bytes) {
   FS_GUARD_BEGIN
   if (nruns < 1 || !table_bytes || (precision != FS_FP32 && precision != FS_FP64))
     return FS_EINVAL;
-  *table_bytes = batch_map_offset(nruns, precision) + sizeof(int2) * (size_t)kBatchMaxCtas;
+  *table_bytes = batch_table_bytes(nruns, precision);
   return FS_OK;
   FS_GUARD_END
 }
@@ -1326,8 +1353,11 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
   b->rec = batch_rec_bytes(s0.p.precision);
   b->table = (char*)table_dev;
   b->map = (int2*)(b->table + batch_map_offset(nruns, s0.p.precision));
+  b->pre = (int*)(b->table + batch_pre_offset(nruns, s0.p.precision));
   std::vector<char> host(need, 0);
   std::vector<int2> map;
+  std::vector<int> pre(3 * ((size_t)nruns + 1), 0);
+  b->tail_batched = true;
   for (int r = 0; r < nruns; ++r) {
     const Sim& s = runs[r]->sim;
     b->cur0.push_back(s.cur);
@@ -1335,10 +1365,19 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
       ops->fill_batch_run(&s, (s.cur + p) & 1, ncta[r],
                           host.data() + ((size_t)p * nruns + r) * b->rec);
     for (int k = 0; k < ncta[r]; ++k) map.push_back(make_int2(r, k));
+    b->tail_batched = b->tail_batched && tail_batchable(s);
+    b->n_sub_max = std::max(b->n_sub_max, s.p.n_sub);
+    const int n1 = nruns + 1;
+    pre[r + 1] = pre[r] + movers_blocks(s);
+    pre[n1 + r + 1] = pre[n1 + r] + moments_blocks(s);
+    pre[2 * n1 + r + 1] = pre[2 * n1 + r] + field1_blocks(s);
   }
+  for (int k = 0; k < 3; ++k) b->nblk[k] = pre[(size_t)k * (nruns + 1) + nruns];
   b->ncta = (int)map.size();
   memcpy(host.data() + batch_map_offset(nruns, s0.p.precision), map.data(),
          sizeof(int2) * map.size());
+  memcpy(host.data() + batch_pre_offset(nruns, s0.p.precision), pre.data(),
+         sizeof(int) * pre.size());
   bool ok = cudaMemcpyAsync(table_dev, host.data(), need, cudaMemcpyHostToDevice, b->stream) ==
                 cudaSuccess &&
             cudaStreamSynchronize(b->stream) == cudaSuccess;

@@ -250,13 +250,15 @@ __device__ __forceinline__ bool fs_return(double& vx, double& vy, double& vz,
 // ------------------------------------------------------------------------
 // k_movers: append each leaver to its destination tile's bucket.
 // ------------------------------------------------------------------------
+// Block blk of nblk: one warp per source tile, its leavers go to their
+// destination tiles.
 template <typename T, int DIM>
-__global__ void k_movers(DevPtrs<T> d, Geo g, int out) {
-  // one warp per source tile: its leavers go to their destination tiles
+__device__ __forceinline__ void movers_body(const DevPtrs<T>& d, const Geo& g, int out, int blk,
+                                            int nblk) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const Parts<T> PO = d.P[out];
-  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < g.ntiles; t += gridDim.x * wpb) {
+  for (int t = blk * wpb + (threadIdx.x >> 5); t < g.ntiles; t += nblk * wpb) {
     const int nm = d.mcnt[t];
     const int mb = t * g.mover_per_tile;
     for (int k = lane; k < nm; k += 32) {
@@ -280,6 +282,11 @@ __global__ void k_movers(DevPtrs<T> d, Geo g, int out) {
       PO.id[gi] = d.M.id[src];
     }
   }
+}
+
+template <typename T, int DIM>
+__global__ void k_movers(DevPtrs<T> d, Geo g, int out) {
+  movers_body<T, DIM>(d, g, out, blockIdx.x, gridDim.x);
 }
 
 // Deposit of one particle into the far accumulators (global atomics).
@@ -353,8 +360,9 @@ __device__ __forceinline__ void place_new(const DevPtrs<T>& d, const Geo& g,
 // count; a scan over rows gives each row's first id. k_inject_gen: one thread
 // per (row, slot) draws the particle.
 // ------------------------------------------------------------------------
-static __global__ void k_inject_count(double* acc, int* rowcnt, int* rowoff, int ny,
-                               double rate, int per_row_mult) {
+// The whole block (any multiple of 32 threads up to 1024) counts every row.
+__device__ __forceinline__ void inject_count_body(double* acc, int* rowcnt, int* rowoff, int ny,
+                                                  double rate, int per_row_mult) {
   __shared__ int wsum[32];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -397,18 +405,19 @@ static __global__ void k_inject_count(double* acc, int* rowcnt, int* rowoff, int
   if (threadIdx.x == 0) rowoff[ny] = carry;
 }
 
+static __global__ void k_inject_count(double* acc, int* rowcnt, int* rowoff, int ny,
+                                      double rate, int per_row_mult) {
+  inject_count_body(acc, rowcnt, rowoff, ny, rate, per_row_mult);
+}
+
+// New particle k of row j (thermal at x = L, then the cosmic rays at x = 0),
+// ids from `first` (next_id before this step's injection) in (row, slot)
+// order; counts and energy added to the caller's l_inj, l_e.
 template <typename T, int DIM>
-__global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
-                             const int* rowcnt, const int* rowoff, int maxk) {
-  const long long step = d.ctr->step;
-  const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = gidx / maxk, k = gidx % maxk;
-  __shared__ unsigned long long s_first;
-  if (threadIdx.x == 0) s_first = d.ctr->next_id;
-  __syncthreads();
-  const unsigned long long first = s_first;
-  long long l_inj = 0;
-  double l_e = 0.0;
+__device__ __forceinline__ void inject_one(const DevPtrs<T>& d, const Geo& g, const Phys& ph,
+                                           int buf, const int* rowcnt, const int* rowoff, int j,
+                                           int k, unsigned long long first, long long step,
+                                           long long& l_inj, double& l_e) {
   if (j < g.ny) {
     const int n = rowcnt[j];
     if (k < n) {
@@ -494,10 +503,56 @@ __global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
       }
     }
   }
+}
+
+template <typename T, int DIM>
+__global__ void k_inject_gen(DevPtrs<T> d, Geo g, Phys ph, int buf,
+                             const int* rowcnt, const int* rowoff, int maxk) {
+  const long long step = d.ctr->step;
+  const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = gidx / maxk, k = gidx % maxk;
+  __shared__ unsigned long long s_first;
+  if (threadIdx.x == 0) s_first = d.ctr->next_id;
+  __syncthreads();
+  const unsigned long long first = s_first;
+  long long l_inj = 0;
+  double l_e = 0.0;
+  inject_one<T, DIM>(d, g, ph, buf, rowcnt, rowoff, j, k, first, step, l_inj, l_e);
   if (l_inj) {
     atomicAdd(&d.ctr->injected, (unsigned long long)l_inj);
     atomicAdd(&d.ctr->injected_energy, l_e);
   }
+}
+
+// The injection of one run by one whole block: the row counts (as
+// k_inject_count), every (row, slot) draw (as k_inject_gen) and the id
+// commit (as k_inject_commit), with block barriers between them.
+template <typename T, int DIM>
+__device__ __forceinline__ void inject_run_block(const DevPtrs<T>& d, const Geo& g,
+                                                 const Phys& ph, int buf) {
+  const int mult = (ph.inject_thermal ? 1 : 0) + (ph.cr_enable ? 1 : 0);
+  int* rowcnt = d.inj;
+  int* rowoff = rowcnt + g.ny;
+  inject_count_body(d.acc, rowcnt, rowoff, g.ny, ph.rate, mult);
+  __shared__ unsigned long long s_first;
+  __shared__ long long s_step;
+  if (threadIdx.x == 0) {
+    s_first = d.ctr->next_id;
+    s_step = d.ctr->step;
+  }
+  __syncthreads();
+  const int maxk = (int)ph.rate + 2;
+  long long l_inj = 0;
+  double l_e = 0.0;
+  for (int gidx = threadIdx.x; gidx < g.ny * maxk; gidx += blockDim.x)
+    inject_one<T, DIM>(d, g, ph, buf, rowcnt, rowoff, gidx / maxk, gidx % maxk, s_first,
+                       s_step, l_inj, l_e);
+  if (l_inj) {
+    atomicAdd(&d.ctr->injected, (unsigned long long)l_inj);
+    atomicAdd(&d.ctr->injected_energy, l_e);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) d.ctr->next_id += rowoff[g.ny];
 }
 
 // end of a step: advance the device step counter
@@ -518,12 +573,12 @@ static __global__ void k_inject_commit(Counters* ctr, const int* rowoff, int ny)
 // the density floor and u = J / n.
 // ------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
+__device__ __forceinline__ void moments_body(const DevPtrs<T>& d, const Geo& g, const Phys& ph,
+                                             int blk, int nblk) {
   using A = typename Num<T>::acc;
   const int nn = g.nxn * g.ny;
   const int AX = g.TX + 3, AY = (DIM == 2) ? g.TY + 3 : 1, NA = AX * AY;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nn;
-       q += gridDim.x * blockDim.x) {
+  for (int q = blk * blockDim.x + threadIdx.x; q < nn; q += nblk * blockDim.x) {
     const int i = q % g.nxn, j = q / g.nxn;
     // candidate tile columns / rows (distinct): a tile's accumulator spans
     // nodes i0 - 1 .. i0 + TX + 1, so tiles home - 2 .. home + 1 can cover i
@@ -604,6 +659,11 @@ __global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) farw[(size_t)c * nn + q] = (A)0;
   }
+}
+
+template <typename T, int DIM>
+__global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
+  moments_body<T, DIM>(d, g, ph, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------------
@@ -870,6 +930,12 @@ inline FieldConst<T> field_const(const Phys& ph) {
   return FieldConst<T>{(T)ph.idx, (T)ph.hdx, (T)ph.hdy, (T)ph.te, (T)ph.jcr,
                        (T)ph.eta, (T)ph.h,   (T)ph.hh,  (T)ph.h6, ph.eta != 0.0 ? 1 : 0};
 }
+// the same on the device (IEEE conversions round alike on host and device)
+template <typename T>
+__device__ __forceinline__ FieldConst<T> field_const_dev(const Phys& ph) {
+  return FieldConst<T>{(T)ph.idx, (T)ph.hdx, (T)ph.hdy, (T)ph.te, (T)ph.jcr,
+                       (T)ph.eta, (T)ph.h,   (T)ph.hh,  (T)ph.h6, ph.eta != 0.0 ? 1 : 0};
+}
 
 // ------------------------------------------------------------------------
 // The whole field advance of a 1D step with x walls (n_sub RK4 substeps,
@@ -893,15 +959,18 @@ inline size_t field1_smem(int n_sub) {
   return sizeof(T) * (9 * L + 7 * (L + 1));
 }
 
+// Tile blk of the 1D field advance (the body of k_field_step1); smem is the
+// block's dynamic shared memory (field1_smem(n_sub) bytes).
 template <typename T>
-__global__ void __launch_bounds__(kF1Threads)
-    k_field_step1(const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ nN,
-                  const T* __restrict__ uN, T* __restrict__ Eo, T* __restrict__ Bbo,
-                  T* __restrict__ G, Geo g, Phys ph, FieldConst<T> fc, int n_sub) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void field_step1_body(const T* __restrict__ Bin, T* __restrict__ Bout,
+                                                 const T* __restrict__ nN,
+                                                 const T* __restrict__ uN, T* __restrict__ Eo,
+                                                 T* __restrict__ Bbo, T* __restrict__ G,
+                                                 const Geo& g, const FieldConst<T>& fc,
+                                                 int n_sub, int blk, unsigned char* smem) {
   const int nx = g.nx, nxn = g.nxn, t0 = threadIdx.x, nt = blockDim.x;
   const int H = field1_halo(n_sub);
-  const int c0 = blockIdx.x * kF1, c1 = min(nx, c0 + kF1);
+  const int c0 = blk * kF1, c1 = min(nx, c0 + kF1);
   const int lo = max(0, c0 - H), L = min(nx, c1 + H) - lo, Ln = L + 1;
   T* sB = (T*)smem;
   T* sBs = sB + 3 * L;
@@ -983,6 +1052,15 @@ __global__ void __launch_bounds__(kF1Threads)
       const int gi = lo + a;
       if (gi >= c0 && gi < c1) Bout[c * nx + gi] = sB[c * L + a];
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kF1Threads)
+    k_field_step1(const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ nN,
+                  const T* __restrict__ uN, T* __restrict__ Eo, T* __restrict__ Bbo,
+                  T* __restrict__ G, Geo g, Phys ph, FieldConst<T> fc, int n_sub) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  field_step1_body<T>(Bin, Bout, nN, uN, Eo, Bbo, G, g, fc, n_sub, blockIdx.x, smem);
 }
 
 // ------------------------------------------------------------------------

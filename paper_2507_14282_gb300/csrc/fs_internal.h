@@ -143,7 +143,7 @@ struct alignas(16) BatchRun {
   PushConst<T> pc;
   int in, out;  // particle buffers read and written this step
   int ncta;     // CTAs of the run's group
-  int pad;
+  int n_sub;    // RK4 field substeps per step
 };
 static_assert(sizeof(BatchRun<float>) % 16 == 0 && sizeof(BatchRun<double>) % 16 == 0,
               "batch records must tile the table at their own size");
@@ -168,6 +168,11 @@ struct Ops {
   cudaError_t (*batch_setup)(int dim, int rel, size_t smem, int* occ);
   cudaError_t (*push_batch)(int dim, int rel, const void* runs, const int2* cta_map,
                             int ncta, size_t smem, cudaStream_t st);
+  // the rest of a batched step in one launch per kernel over every run (1D
+  // runs with x walls): pre holds three block prefixes over the runs (movers,
+  // moments, field tiles; nruns + 1 entries each), nblk their totals
+  cudaError_t (*batch_rest)(const void* runs, const int* pre, int nruns, const int* nblk,
+                            int n_sub_max, cudaStream_t st);
   cudaError_t (*fields)(Sim*);
   cudaError_t (*insert_staged)(Sim*, int buf, int n, bool from_movers);
   cudaError_t (*diag)(Sim*, int buf);

@@ -299,7 +299,7 @@ struct OpsImpl {
     r.in = in;
     r.out = 1 - in;
     r.ncta = ncta;
-    r.pad = 0;
+    r.n_sub = s->p.n_sub;
     memcpy(dst, &r, sizeof r);
   }
   static size_t batch_smem(int dim, int tx, int ty) {
@@ -344,6 +344,30 @@ struct OpsImpl {
       push_batch_launch<true>(dim, r, cta_map, ncta, smem, st);
     else
       push_batch_launch<false>(dim, r, cta_map, ncta, smem, st);
+    return cudaGetLastError();
+  }
+
+  // the rest of a batched step over every run (all 1D with x walls)
+  static cudaError_t batch_rest(const void* runs, const int* pre, int nruns, const int* nblk,
+                                int n_sub_max, cudaStream_t st) {
+    const BatchRun<T>* r = (const BatchRun<T>*)runs;
+    const size_t fsm = field1_smem<T>(n_sub_max);
+    static std::atomic<size_t> attr(0);  // the largest size enabled so far
+    if (fsm > attr.load()) {
+      cudaError_t e = cudaFuncSetAttribute(k_field1_batch<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+      if (e != cudaSuccess) return e;
+      size_t cur = attr.load();
+      while (fsm > cur && !attr.compare_exchange_weak(cur, fsm)) {
+      }
+    }
+    const int n1 = nruns + 1;
+    k_movers_batch<T, 1><<<nblk[0], kBlock, 0, st>>>(r, pre, nruns);
+    k_inject_batch<T, 1><<<nruns, kBlock, 0, st>>>(r, nruns);
+    k_moments_batch<T, 1><<<nblk[1], kBlock, 0, st>>>(r, pre + n1, nruns);
+    k_field1_batch<T><<<nblk[2], kF1Threads, fsm, st>>>(r, pre + 2 * n1, nruns);
+    k_copyB_batch<T><<<nblk[2], kF1Threads, 0, st>>>(r, pre + 2 * n1, nruns);
+    k_step_end_batch<T><<<(nruns + 63) / 64, 64, 0, st>>>(r, nruns);
     return cudaGetLastError();
   }
 
@@ -480,6 +504,7 @@ struct OpsImpl {
     o.batch_smem = batch_smem;
     o.batch_setup = batch_setup;
     o.push_batch = push_batch;
+    o.batch_rest = batch_rest;
     o.profile_B = profile_B;
     o.spectrum_bperp = spectrum_bperp;
     o.spectrum_p = spectrum_p;

@@ -966,4 +966,92 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
   push_run<T, DIM, CH, NS, REL>(R.d, R.g, R.ph, R.pc, R.in, R.out, cm.y, R.ncta, sm);
 }
 
+// ---------------------------------------------------------------- batched step tail
+// The rest of a batched step (movers, injection, moments, the 1D tiled field
+// advance, the step counter) as one launch per kernel over every run of the
+// batch: block b belongs to the run r with pre[r] <= b < pre[r + 1] and works
+// as block b - pre[r] of that run's own launch; the run's record is copied
+// into shared memory first. Same bodies, so the same results, as the per-run
+// kernels.
+__device__ __forceinline__ int batch_run_of(const int* pre, int nruns, int b) {
+  int lo = 0, hi = nruns;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ int load_batch_run(const BatchRun<T>* runs, const int* pre, int nruns,
+                                              BatchRun<T>& R) {
+  __shared__ int s_run;
+  if (threadIdx.x == 0) s_run = pre ? batch_run_of(pre, nruns, blockIdx.x) : (int)blockIdx.x;
+  __syncthreads();
+  const int r = s_run;
+  const int* src = reinterpret_cast<const int*>(runs + r);
+  int* dst = reinterpret_cast<int*>(&R);
+  for (int k = threadIdx.x; k < (int)(sizeof(BatchRun<T>) / 4); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  return r;
+}
+
+template <typename T, int DIM>
+__global__ void k_movers_batch(const BatchRun<T>* __restrict__ runs, const int* __restrict__ pre,
+                               int nruns) {
+  __shared__ __align__(16) BatchRun<T> R;
+  const int r = load_batch_run<T>(runs, pre, nruns, R);
+  movers_body<T, DIM>(R.d, R.g, R.out, blockIdx.x - pre[r], pre[r + 1] - pre[r]);
+}
+
+// one block per run
+template <typename T, int DIM>
+__global__ void k_inject_batch(const BatchRun<T>* __restrict__ runs, int nruns) {
+  __shared__ __align__(16) BatchRun<T> R;
+  load_batch_run<T>(runs, nullptr, nruns, R);
+  if (R.g.bc_x == FS_BC_FAUXSHOCK && (R.ph.inject_thermal || R.ph.cr_enable))
+    inject_run_block<T, DIM>(R.d, R.g, R.ph, R.out);
+}
+
+template <typename T, int DIM>
+__global__ void k_moments_batch(const BatchRun<T>* __restrict__ runs,
+                                const int* __restrict__ pre, int nruns) {
+  __shared__ __align__(16) BatchRun<T> R;
+  const int r = load_batch_run<T>(runs, pre, nruns, R);
+  moments_body<T, DIM>(R.d, R.g, R.ph, blockIdx.x - pre[r], pre[r + 1] - pre[r]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kF1Threads)
+    k_field1_batch(const BatchRun<T>* __restrict__ runs, const int* __restrict__ pre,
+                   int nruns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) BatchRun<T> R;
+  const int r = load_batch_run<T>(runs, pre, nruns, R);
+  const FieldConst<T> fc = field_const_dev<T>(R.ph);
+  field_step1_body<T>(R.d.B, R.d.Bs, R.d.n, R.d.u, R.d.E, R.d.Bb, R.d.G, R.g, fc, R.n_sub,
+                      blockIdx.x - pre[r], smem);
+}
+
+// the new B back from the stage buffer: tile b's cells, as the per-run copy
+template <typename T>
+__global__ void __launch_bounds__(kF1Threads)
+    k_copyB_batch(const BatchRun<T>* __restrict__ runs, const int* __restrict__ pre,
+                  int nruns) {
+  __shared__ __align__(16) BatchRun<T> R;
+  const int r = load_batch_run<T>(runs, pre, nruns, R);
+  const int nx = R.g.nx, c0 = (blockIdx.x - pre[r]) * kF1, c1 = min(nx, c0 + kF1);
+  for (int k = threadIdx.x; k < 3 * kF1; k += blockDim.x) {
+    const int c = k / kF1, i = c0 + k % kF1;
+    if (i < c1) R.d.B[c * nx + i] = R.d.Bs[c * nx + i];
+  }
+}
+
+template <typename T>
+__global__ void k_step_end_batch(const BatchRun<T>* __restrict__ runs, int nruns) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x)
+    runs[r].d.ctr->step += 1;
+}
+
 }  // namespace fsx

@@ -35,6 +35,9 @@ RUNS_1D = [
     dict(dim=1, nx=64, ppc=32, mach_a=8.0, theta_bn_deg=10.0, beta_i=1.0, beta_e=1.0,
          dt=0.004, seed=15, bc_x=1),
 ]
+# every run 1D with x walls: the batch runs the whole step tail (movers,
+# injection, moments, field advance, step counter) as one launch per kernel
+RUNS_1D_WALLS = [r for r in RUNS_1D if r.get("bc_x", 0) == 0]
 RUNS_2D = [
     dict(dim=2, nx=64, ny=16, ppc=8, mach_a=10.0, theta_bn_deg=20.0, dt=0.0025, seed=21),
     dict(dim=2, nx=32, ny=8, ppc=16, mach_a=25.0, theta_bn_deg=0.0, dt=0.002, seed=22,
@@ -80,7 +83,8 @@ def run_both(fs, runs, prec, steps):
     return alone, run_batched(fs, runs, prec, steps)
 
 
-@pytest.mark.parametrize("runs", [RUNS_1D, RUNS_2D], ids=["1d", "2d"])
+@pytest.mark.parametrize("runs", [RUNS_1D, RUNS_1D_WALLS, RUNS_2D],
+                         ids=["1d", "1d-walls", "2d"])
 def test_fp64_batch_is_bit_identical_to_runs_alone(fs, runs):
     alone, batched = run_both(fs, runs, fs.FS_FP64, 12)
     for r, (a, b) in enumerate(zip(alone, batched)):
@@ -113,7 +117,8 @@ def oracle_state(params, steps):
     return out
 
 
-@pytest.mark.parametrize("runs", [RUNS_1D, RUNS_2D], ids=["1d", "2d"])
+@pytest.mark.parametrize("runs", [RUNS_1D, RUNS_1D_WALLS, RUNS_2D],
+                         ids=["1d", "1d-walls", "2d"])
 def test_fp64_batched_runs_equal_the_oracle(fs, runs):
     # every run of a mixed batch (lengths, ppc, M_A, theta, beta, dt, tile
     # shapes, a periodic box) stepped in the batch -- the first step launched
@@ -139,8 +144,9 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(a), 1e-30))
 
 
-def test_fp32_batch_matches_runs_alone(fs):
-    alone, batched = run_both(fs, RUNS_1D, fs.FS_FP32, 6)
+@pytest.mark.parametrize("runs", [RUNS_1D, RUNS_1D_WALLS], ids=["1d", "1d-walls"])
+def test_fp32_batch_matches_runs_alone(fs, runs):
+    alone, batched = run_both(fs, runs, fs.FS_FP32, 6)
     for r, (a, b) in enumerate(zip(alone, batched)):
         assert a["diag_status"] == 0 and b["diag_status"] == 0
         for k in ("diag_step", "diag_injected", "diag_next_id"):
