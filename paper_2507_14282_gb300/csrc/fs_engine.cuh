@@ -261,12 +261,22 @@ __device__ __forceinline__ void movers_body(const DevPtrs<T>& d, const Geo& g, i
   for (int t = blk * wpb + (threadIdx.x >> 5); t < g.ntiles; t += nblk * wpb) {
     const int nm = d.mcnt[t];
     const int mb = t * g.mover_per_tile;
-    for (int k = lane; k < nm; k += 32) {
+    for (int k0 = 0; k0 < nm; k0 += 32) {  // nm is the same for the whole warp
+      const int k = k0 + lane;
+      const bool act = k < nm;
       const int src = mb + k;
-      const int cell = d.M.cell[src];
+      const int cell = act ? d.M.cell[src] : 0;
       const int i = cell & 0xFFFF, j = cell >> 16;
-      const int dt = (j / g.TY) * g.ntx + i / g.TX;
-      const int slot = atomicAdd(&d.cnt[out][dt], 1);
+      const int dt = act ? (j / g.TY) * g.ntx + i / g.TX : -1;
+      // lanes bound for the same tile take consecutive slots after one
+      // atomic by the lowest of them (a tile's leavers go to a few tiles)
+      const unsigned peers = __match_any_sync(0xffffffffu, dt);
+      const int leader = __ffs(peers) - 1;
+      int base = 0;
+      if (act && lane == leader) base = atomicAdd(&d.cnt[out][dt], __popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (!act) continue;
+      const int slot = base + __popc(peers & ((1u << lane) - 1u));
       if (slot >= g.tile_cap) {
         atomicSub(&d.cnt[out][dt], 1);
         atomicOr(&d.ctr->status, kStatusCapacity);
