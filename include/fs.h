@@ -113,6 +113,13 @@ typedef struct fs_params {
                               v, and p_iso is the CRs' momentum */
   int spec_np;             /* momentum spectrum n(p) (FS_SPECTRUM_P_*): bins of */
   double spec_pmin, spec_pmax; /* |u| between log-spaced edges pmin..pmax */
+  /* launch shape of the particle push (a tuning choice; results do not
+     depend on it in FP64): */
+  int push_chunk;          /* particles per shared-memory chunk: 0 (library
+                              choice), 512 (three stages in FP32) or 640 (two
+                              stages; FP32 only) */
+  int push_ctas_per_sm;    /* persistent CTAs per SM: 0 (as many as fit) or a
+                              cap >= 1 */
 } fs_params;
 
 /* sizes reported by fs_query */
@@ -351,7 +358,9 @@ int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
    per kernel over all runs too (each block works for one run, found from
    per-run block prefixes in the table): about seven launches per step
    whatever the number of runs. Otherwise each run's remaining kernels run in
-   parallel branches. Either way the step is captured as a CUDA graph. Each
+   parallel branches. Either way the step is captured as a CUDA graph. The
+   push's launch shape is the runs' push_chunk and push_ctas_per_sm when all
+   runs agree on them, else the library's choice. Each
    run's results are those of fs_step on that handle alone (bit-identical in
    FP64).
 

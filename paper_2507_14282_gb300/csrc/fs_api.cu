@@ -29,8 +29,16 @@ size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool divides(int a, int b) { return a > 0 && b % a == 0; }
 
 // The push's shared memory for a tx x ty tile fits one CTA.
+// The push's chunk: the caller's choice, else 640 particles in FP32 (a
+// 512-particle mean tile in one chunk) unless the mean tile holds at most
+// 256, and 512 in FP64 (two CTAs per SM with its wider particles).
+int push_chunk_of(const fs_params* p, int tx, int ty) {
+  if (p->push_chunk) return p->push_chunk;
+  return (p->precision == FS_FP32 && (long long)tx * ty * p->ppc > 256) ? 640 : 512;
+}
+
 bool push_tile_fits(const fs_params* p, int tx, int ty) {
-  const int chunk = (p->precision == FS_FP32 && (long long)tx * ty * p->ppc > 256) ? 640 : 512;
+  const int chunk = push_chunk_of(p, tx, ty);
   const size_t smem = (p->precision == FS_FP64) ? push_smem_bytes_f64(p->dim, tx, ty, chunk)
                                                 : push_smem_bytes_f32(p->dim, tx, ty, chunk);
   return smem <= 227 * 1024 - 1024;
@@ -102,6 +110,10 @@ int validate(const fs_params* p) {
   if (p->c_light > 0 && !(p->mach_a < p->c_light)) return FS_EINVAL;
   if (p->spec_np < 1 || !(p->spec_pmin > 0) || !(p->spec_pmax > p->spec_pmin)) return FS_EINVAL;
   if (p->mach_a < 0) return FS_EINVAL;
+  if (p->push_chunk != 0 && p->push_chunk != 512 &&
+      !(p->push_chunk == 640 && p->precision == FS_FP32))
+    return FS_EINVAL;
+  if (p->push_ctas_per_sm < 0) return FS_EINVAL;
   return FS_OK;
 }
 
@@ -142,10 +154,8 @@ int derive(const fs_params* p, Geo* g, Phys* ph, Layout* L) {
   g->mover_per_tile = (int)mpt;
   g->mover_cap = (int)(mpt * g->ntiles);
   g->staging_cap = 1 << 16;
-  // shared-memory chunk: FP32 takes 640 particles (a 512-particle mean tile
-  // in one chunk) unless the mean tile holds at most 256; FP64 takes 512
-  // (two CTAs per SM with its wider particles)
-  g->chunk = (p->precision == FS_FP32 && cells_per_tile * p->ppc > 256) ? 640 : 512;
+  g->chunk = push_chunk_of(p, tx, ty);
+  g->push_ctas = p->push_ctas_per_sm;
   g->na = (tx + 3) * (p->dim == 2 ? ty + 3 : 1);
   g->nk = (tx + 2) * (p->dim == 2 ? ty + 2 : 1) + 2;
   const size_t smem = (p->precision == FS_FP64)
@@ -1179,6 +1189,7 @@ struct fs_batch {
   size_t smem = 0;
   int dim = 1;
   int rel = 0;  // some run has relativistic ions (c > 0)
+  int chunk = 0;  // the batch push's chunk (0: the large chunk)
   const Ops* ops = nullptr;
   int parity = 0;  // steps taken, mod 2
   bool tail_batched = false;  // the step tail runs as one launch per kernel
@@ -1195,8 +1206,8 @@ namespace {
 // one launch, then each run's remaining kernels on its branch.
 cudaError_t batch_enqueue(fs_batch* b, int p, cudaStream_t st) {
   const int nr = (int)b->runs.size();
-  cudaError_t e = b->ops->push_batch(b->dim, b->rel, b->table + (size_t)p * nr * b->rec, b->map,
-                                     b->ncta, b->smem, st);
+  cudaError_t e = b->ops->push_batch(b->dim, b->rel, b->chunk, b->table + (size_t)p * nr * b->rec,
+                                     b->map, b->ncta, b->smem, st);
   if (e != cudaSuccess) return e;
   if (b->tail_batched)
     return b->ops->batch_rest(b->table + (size_t)p * nr * b->rec, b->pre, nr, b->nblk,
@@ -1323,16 +1334,24 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
   const Ops* ops = s0.ops;
   size_t smem = 0;
   int rel = 0;
+  // launch shape: every run's push_chunk and CTA cap when they agree, else
+  // the library's choice
+  int chunk = s0.p.push_chunk, cap = s0.p.push_ctas_per_sm;
+  for (int r = 1; r < nruns; ++r) {
+    if (runs[r]->sim.p.push_chunk != chunk) chunk = 0;
+    if (runs[r]->sim.p.push_ctas_per_sm != cap) cap = 0;
+  }
   for (int r = 0; r < nruns; ++r) {
-    smem = std::max(smem, ops->batch_smem(s0.g.dim, runs[r]->sim.g.TX, runs[r]->sim.g.TY));
+    smem = std::max(smem, ops->batch_smem(s0.g.dim, runs[r]->sim.g.TX, runs[r]->sim.g.TY, chunk));
     if (runs[r]->sim.ph.c2inv > 0.0) rel = 1;
   }
   if (smem > 227 * 1024 - 2048) return FS_EINVAL;
   int dev = 0, nsm = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      ops->batch_setup(s0.g.dim, rel, smem, &occ) != cudaSuccess || occ < 1)
+      ops->batch_setup(s0.g.dim, rel, chunk, smem, &occ) != cudaSuccess || occ < 1)
     return FS_ECUDA;
+  if (cap > 0) occ = std::min(occ, cap);
   const int ncta_max = std::min(nsm * occ, kBatchMaxCtas);
   std::vector<long long> np(nruns);
   std::vector<int> nt(nruns), ncta(nruns);
@@ -1349,6 +1368,7 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
   b->ops = ops;
   b->dim = s0.g.dim;
   b->rel = rel;
+  b->chunk = chunk;
   b->smem = smem;
   b->rec = batch_rec_bytes(s0.p.precision);
   b->table = (char*)table_dev;

@@ -61,6 +61,7 @@ struct Geo {
   int staging_cap;          // host-injection staging slots
   int na;                   // accumulator nodes per tile: (TX+3)*(TY+3) or TX+3
   int nk;                   // sort keys per tile
+  int push_ctas;            // cap on the push's persistent CTAs per SM (0: none)
 };
 
 // Constants derived once on the host from fs_params (FP64; kernels cast).
@@ -163,11 +164,13 @@ struct Ops {
   // batched ensembles (k_push_batch)
   size_t (*batch_run_bytes)();
   void (*fill_batch_run)(const Sim*, int in_buf, int ncta, void* dst);
-  size_t (*batch_smem)(int dim, int tx, int ty);
+  // chunk: the batch's push chunk (every run's push_chunk when they agree,
+  // else 0: the large chunk)
+  size_t (*batch_smem)(int dim, int tx, int ty, int chunk);
   // rel: the push variant with the relativistic terms (some run has c > 0)
-  cudaError_t (*batch_setup)(int dim, int rel, size_t smem, int* occ);
-  cudaError_t (*push_batch)(int dim, int rel, const void* runs, const int2* cta_map,
-                            int ncta, size_t smem, cudaStream_t st);
+  cudaError_t (*batch_setup)(int dim, int rel, int chunk, size_t smem, int* occ);
+  cudaError_t (*push_batch)(int dim, int rel, int chunk, const void* runs,
+                            const int2* cta_map, int ncta, size_t smem, cudaStream_t st);
   // the rest of a batched step in one launch per kernel over every run (1D
   // runs with x walls): pre holds three block prefixes over the runs (movers,
   // moments, field tiles; nruns + 1 entries each), nblk their totals

@@ -60,7 +60,8 @@ cudaError_t launch_push(Sim* s, int in, long long step) {
   a.in = in;
   a.out = 1 - in;
   a.step = step;
-  const long long want = (long long)n_sm * occ_blocks;
+  const int per_sm = s->g.push_ctas > 0 ? std::min(occ_blocks, s->g.push_ctas) : occ_blocks;
+  const long long want = (long long)n_sm * per_sm;
   const int grid = (int)std::min<long long>(want, s->g.ntiles);
   k_push<T, DIM, CH, NS, REL><<<grid, kBlock, L.bytes, s->stream>>>(s->ptrs<T>(), a,
                                                                     push_const<T>(s->ph));
@@ -302,48 +303,64 @@ struct OpsImpl {
     r.n_sub = s->p.n_sub;
     memcpy(dst, &r, sizeof r);
   }
-  static size_t batch_smem(int dim, int tx, int ty) {
+  // chunk: 0 or the large chunk (PushShape::kChunkLarge, its stages), or
+  // the small chunk (kChunkSmall, its stages) for every run of the batch
+  static bool batch_small(int chunk) {
     using S = PushShape<T>;
-    return dim == 1 ? PushLayout<T, 1>(tx, ty, S::kChunkLarge, S::kStagesLarge).bytes
-                    : PushLayout<T, 2>(tx, ty, S::kChunkLarge, S::kStagesLarge).bytes;
+    return chunk == S::kChunkSmall && S::kChunkSmall != S::kChunkLarge;
   }
-  template <int DIM, bool REL>
-  static cudaError_t batch_kernel_setup(size_t smem, int* occ) {
+  static size_t batch_smem(int dim, int tx, int ty, int chunk) {
     using S = PushShape<T>;
-    auto kern = k_push_batch<T, DIM, S::kChunkLarge, S::kStagesLarge, REL>;
+    const int ch = batch_small(chunk) ? S::kChunkSmall : S::kChunkLarge;
+    const int ns = batch_small(chunk) ? S::kStagesSmall : S::kStagesLarge;
+    return dim == 1 ? PushLayout<T, 1>(tx, ty, ch, ns).bytes
+                    : PushLayout<T, 2>(tx, ty, ch, ns).bytes;
+  }
+  template <int DIM, int CH, int NS, bool REL>
+  static cudaError_t batch_kernel_setup(size_t smem, int* occ) {
+    auto kern = k_push_batch<T, DIM, CH, NS, REL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess && occ)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, kBlock, smem);
     return e;
   }
+  template <int CH, int NS>
+  static cudaError_t batch_setup_shape(int dim, int rel, size_t smem, int* occ) {
+    if (rel)
+      return dim == 1 ? batch_kernel_setup<1, CH, NS, true>(smem, occ)
+                      : batch_kernel_setup<2, CH, NS, true>(smem, occ);
+    return dim == 1 ? batch_kernel_setup<1, CH, NS, false>(smem, occ)
+                    : batch_kernel_setup<2, CH, NS, false>(smem, occ);
+  }
   // sets the shared-memory attribute; occ (optional): CTAs per SM. rel: the
   // variant with the relativistic terms (some run has a finite c).
-  static cudaError_t batch_setup(int dim, int rel, size_t smem, int* occ) {
-    if (rel)
-      return dim == 1 ? batch_kernel_setup<1, true>(smem, occ)
-                      : batch_kernel_setup<2, true>(smem, occ);
-    return dim == 1 ? batch_kernel_setup<1, false>(smem, occ)
-                    : batch_kernel_setup<2, false>(smem, occ);
+  static cudaError_t batch_setup(int dim, int rel, int chunk, size_t smem, int* occ) {
+    using S = PushShape<T>;
+    if (batch_small(chunk))
+      return batch_setup_shape<S::kChunkSmall, S::kStagesSmall>(dim, rel, smem, occ);
+    return batch_setup_shape<S::kChunkLarge, S::kStagesLarge>(dim, rel, smem, occ);
   }
-  template <bool REL>
+  template <int CH, int NS, bool REL>
   static void push_batch_launch(int dim, const BatchRun<T>* r, const int2* cta_map, int ncta,
                                 size_t smem, cudaStream_t st) {
-    using S = PushShape<T>;
     if (dim == 1)
-      k_push_batch<T, 1, S::kChunkLarge, S::kStagesLarge, REL>
-          <<<ncta, kBlock, smem, st>>>(r, cta_map);
+      k_push_batch<T, 1, CH, NS, REL><<<ncta, kBlock, smem, st>>>(r, cta_map);
     else
-      k_push_batch<T, 2, S::kChunkLarge, S::kStagesLarge, REL>
-          <<<ncta, kBlock, smem, st>>>(r, cta_map);
+      k_push_batch<T, 2, CH, NS, REL><<<ncta, kBlock, smem, st>>>(r, cta_map);
   }
-  static cudaError_t push_batch(int dim, int rel, const void* runs, const int2* cta_map,
-                                int ncta, size_t smem, cudaStream_t st) {
+  static cudaError_t push_batch(int dim, int rel, int chunk, const void* runs,
+                                const int2* cta_map, int ncta, size_t smem, cudaStream_t st) {
+    using S = PushShape<T>;
     const BatchRun<T>* r = (const BatchRun<T>*)runs;
-    if (rel)
-      push_batch_launch<true>(dim, r, cta_map, ncta, smem, st);
-    else
-      push_batch_launch<false>(dim, r, cta_map, ncta, smem, st);
+    const bool sm = batch_small(chunk);
+    if (rel) {
+      if (sm) push_batch_launch<S::kChunkSmall, S::kStagesSmall, true>(dim, r, cta_map, ncta, smem, st);
+      else push_batch_launch<S::kChunkLarge, S::kStagesLarge, true>(dim, r, cta_map, ncta, smem, st);
+    } else {
+      if (sm) push_batch_launch<S::kChunkSmall, S::kStagesSmall, false>(dim, r, cta_map, ncta, smem, st);
+      else push_batch_launch<S::kChunkLarge, S::kStagesLarge, false>(dim, r, cta_map, ncta, smem, st);
+    }
     return cudaGetLastError();
   }
 

@@ -54,6 +54,7 @@ class FsParams(C.Structure):
         ("use_graph", C.c_int),
         ("c_light", C.c_double),
         ("spec_np", C.c_int), ("spec_pmin", C.c_double), ("spec_pmax", C.c_double),
+        ("push_chunk", C.c_int), ("push_ctas_per_sm", C.c_int),
     ]
 
 

@@ -54,6 +54,7 @@ def test_query_scales_with_capacity(fs):
     dict(fs_mode_thermal=9), dict(n_floor=0.0), dict(capacity_factor=0.5),
     dict(cr_enable=1, p_iso=1.0, mach_a=10.0), dict(hist_pmin=5.0, hist_pmax=1.0),
     dict(nx=70000), dict(tile_x=3, nx=512),
+    dict(push_chunk=700), dict(push_chunk=640), dict(push_ctas_per_sm=-1),
 ])
 def test_query_rejects_bad_parameters(fs, bad):
     kw = dict(dim=1, nx=512, ppc=8)
@@ -138,3 +139,11 @@ def test_restore_state_rejects_null_arguments(fs):
     # checked before any CUDA call
     L = fs.lib()
     assert L.fs_restore_state(None, None, 0) == -1
+
+
+def test_query_accepts_push_launch_shapes(fs):
+    # FP32 takes 512- or 640-particle chunks, FP64 512; any CTA cap >= 0
+    for prec, chunk in ((fs.FS_FP32, 512), (fs.FS_FP32, 640), (fs.FS_FP64, 512)):
+        s = fs.query(dim=2, nx=256, ny=64, ppc=64, precision=prec, push_chunk=chunk,
+                     push_ctas_per_sm=2)
+        assert s.device_bytes > 0

@@ -90,3 +90,18 @@ def test_tile_rule():
     assert tune.tile_for(2048, 256, 512) == 2
     assert tune.tile_for(5792, 128, 512) == 4   # 5792 = 2^5 * 181
     assert tune.tile_for(5792, 32, 1024) == 32
+
+
+def test_tuner_2d_candidates_and_launch_shapes():
+    from paper_2507_14282_gb300 import tune, fs
+    c = tune.tile_candidates_2d(1024, 64, 64)
+    assert (4, 2) in c and (8, 1) in c and (2, 4) in c
+    for tx, ty in c:
+        assert 1024 % tx == 0 and 64 % ty == 0 and tx >= 2
+        assert 128 <= tx * ty * 64 <= 1024
+    counts = [tx * ty for tx, ty in c]
+    assert counts == sorted(counts)
+    # a box whose sides admit no shape in range gives none
+    assert tune.tile_candidates_2d(7, 1, 1000) == []
+    assert (0, 0) in tune.launch_shapes(fs.FS_FP32) and (640, 0) in tune.launch_shapes(fs.FS_FP32)
+    assert all(c in (0, 512) for c, _ in tune.launch_shapes(fs.FS_FP64))

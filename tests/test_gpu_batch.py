@@ -175,6 +175,32 @@ def test_config4_ensemble_steps_with_autotuned_tiles(fs):
     b.close()
 
 
+def test_autotuner_2d_class_and_launch_shapes(fs):
+    # a 2D class: tile shapes, then launch shapes on the winner; the tuned
+    # parameters make a valid run, and a batch of such runs equals the oracle
+    from oracle import oracle as O
+    from paper_2507_14282_gb300 import tune
+    tuner = tune.Autotuner(probe_particles=1 << 18, warm=2, steps=3)
+    base = dict(dim=2, nx=128, ny=32, ppc=16, mach_a=10.0, theta_bn_deg=20.0, dt=0.0025,
+                seed=31, precision=fs.FS_FP64)
+    t = tuner.tile(base)
+    assert t["nx"] % t["tile_x"] == 0 and t["ny"] % t["tile_y"] == 0
+    assert t["push_chunk"] in (0, 512) and t["push_ctas_per_sm"] in (0, 1)
+    assert any("tile" in e for e in tuner.log) and any("push_chunk" in e for e in tuner.log)
+    runs = [dict(t, seed=31 + k) for k in range(3)]
+    sims = [fs.FauxShock(**r) for r in runs]
+    b = fs.FsBatch(sims)
+    b.step(6)
+    for r, s in zip(runs, sims):
+        ref = O.Oracle(**{k: v for k, v in r.items()
+                          if k not in ("tile_x", "tile_y", "push_chunk", "push_ctas_per_sm",
+                                       "precision")})
+        ref.step(6)
+        assert np.array_equal(s.grid(fs.FS_B), ref.grid(O.GRID_B))
+        assert s.diag()["n_particles"] == ref.diag()["n_particles"]
+    b.close()
+
+
 def test_batch_rejects_mixed_precision(fs):
     a = fs.FauxShock(precision=fs.FS_FP64, **RUNS_1D[0])
     c = fs.FauxShock(precision=fs.FS_FP32, **RUNS_1D[1])

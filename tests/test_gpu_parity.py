@@ -231,6 +231,30 @@ def test_fp32_full_size_precision_form_error_vs_fp64(fs):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("chunk,ctas", [(512, 1), (512, 2)])
+def test_fp64_push_launch_shapes_bit_exact(fs, chunk, ctas):
+    # the launch shape is a tuning choice: FP64 results stay the oracle's
+    cfg = W.scaled(W.CONFIG_2D, nx=64, ny=16, ppc=16, mach_a=10.0, theta_bn_deg=20.0)
+    gpu = fs.FauxShock(precision=fs.FS_FP64, push_chunk=chunk, push_ctas_per_sm=ctas, **cfg)
+    ref = O.Oracle(**cfg)
+    gpu.step(12)
+    ref.step(12)
+    assert_state_equal(gpu, ref, fs)
+
+
+@pytest.mark.parametrize("chunk,ctas", [(512, 0), (640, 2), (512, 2)])
+def test_fp32_push_launch_shapes_within_tolerance(fs, chunk, ctas):
+    cfg = W.scaled(W.CONFIG_2D_FP32, nx=64, ny=16)
+    gpu = fs.FauxShock(precision=fs.FS_FP32, push_chunk=chunk, push_ctas_per_sm=ctas, **cfg)
+    ref = O.Oracle(**cfg)
+    gpu.step(20)
+    ref.step(20)
+    for gw, ow in GRIDS:
+        assert rel_l2(gpu.grid(gw), ref.grid(ow)) <= 1e-3, gw
+    d = gpu.diag()
+    assert d["status"] == 0 and d["injected"] == ref.diag()["injected"]
+
+
 def test_fp64_multi_chunk_tiles_bit_exact(fs):
     # 128 cells x 32 ppc = 4096 particles per tile: several shared-memory chunks
     cfg = W.scaled(W.CONFIG_1D, nx=256, tile_x=128)
