@@ -115,14 +115,14 @@ def central_difference(w, th, k, L, rel_h):
 # particle crosses a cell face, and a returned ion's re-placement and path
 # move with u2 and u_cr. A difference interval must be narrower than the
 # spacing of the kinks it crosses and wider than rounding: for the kick u2
-# that is h = 1e-6 u2 (1e-5 already straddles kinks and moves the quotient
-# by 0.4 %, 1e-8 is rounding-limited); the modes take h = 1e-5 |a_m|.
-@pytest.mark.parametrize("k,rel_h", [(0, 1e-5), (7, 1e-5), (15, 1e-5), (17, 1e-6)])
+# that is h = 1e-6 u2 (1e-4 straddles kinks and moves the quotient by 2 %,
+# 1e-5 by 0.4 %); the modes take h = 1e-5 |a_m| (an h sweep from 1e-4 to
+# 1e-6 |a_m| on GB300 gave agreement within 2e-5 for every mode).
+@pytest.mark.parametrize("k,rel_h", [(m, 1e-5) for m in range(16)] + [(17, 1e-6)])
 def test_full_window_gradient_matches_central_differences(full_fp64, k, rel_h):
     w, th, L, g = full_fp64
     fd = central_difference(w, th, k, L, rel_h)
-    atol = 1e-6 * np.abs(g[:16]).max() if k < 16 else 0.0
-    assert g[k] == pytest.approx(fd, rel=1e-3, abs=atol), (k, g[k], fd)
+    assert g[k] == pytest.approx(fd, rel=1e-3), (k, g[k], fd)
 
 
 def test_cosmic_ray_drift_gradient_matches_central_differences(full_fp64_100, full_fp64):
@@ -134,20 +134,47 @@ def test_cosmic_ray_drift_gradient_matches_central_differences(full_fp64_100, fu
     w, th, L, g = full_fp64_100
     fd = central_difference(w, th, 16, L, 1e-6)
     assert g[16] == pytest.approx(fd, rel=1e-3), (g[16], fd)
+    # 200 steps, h swept over 1e-6 and 1e-7 |u_cr| (a sweep from 1e-4 down
+    # on GB300 gave quotients from -4.5 % to +0.8 % of the adjoint): each
+    # quotient within 2 % and the adjoint between them
     w, th, L, g = full_fp64
-    fd = central_difference(w, th, 16, L, 1e-6)
-    assert g[16] == pytest.approx(fd, rel=2e-2), (g[16], fd)
+    fds = [central_difference(w, th, 16, L, rh) for rh in (1e-6, 1e-7)]
+    for fd in fds:
+        assert g[16] == pytest.approx(fd, rel=2e-2), (g[16], fds)
+    assert min(fds) <= g[16] <= max(fds), (g[16], fds)
 
 
 def test_fp32_window_gradient_tracks_fp64(fsw, full_fp64):
+    # the full window (200 steps): the FP32 forward makes one faux-shock
+    # return decision differently from the FP64 run (893 against 891 returns)
+    # and its gradient follows its own trajectory: modes within 1e-3 of the
+    # FP64 gradient (2.7e-4 on GB300), the kick within 2 % (0.7 %)
     _, th, L64, g64 = full_fp64
     w, _ = gpu_window(fsw, 2048, 128, 200, 20, precision=1)
     L32, g32 = w.loss_and_grad(th)
     assert L32 == pytest.approx(L64, rel=1e-3)
     gm = np.abs(g64[:16]).max()
-    assert np.abs(g32[:16] - g64[:16]).max() <= 2e-2 * gm
-    assert g32[17] == pytest.approx(g64[17], rel=5e-2)
+    assert np.abs(g32[:16] - g64[:16]).max() <= 1e-3 * gm
+    assert g32[17] == pytest.approx(g64[17], rel=2e-2)
     w.close()
+
+
+def test_fp32_window_gradient_equals_fp64_while_the_decisions_agree(fsw):
+    # over 20 steps both forwards take the same faux-shock decisions (counts
+    # equal): the FP32 adjoint then gives the FP64 gradient to 1e-4 in every
+    # component (about 1e-8 for the modes and 1e-5 for u_cr and u2 on GB300)
+    w64, th = gpu_window(fsw, 2048, 128, 20, 20, precision=0)
+    w32, _ = gpu_window(fsw, 2048, 128, 20, 20, precision=1)
+    L64, g64 = w64.loss_and_grad(th)
+    L32, g32 = w32.loss_and_grad(th)
+    assert w32.counts() == w64.counts()
+    assert L32 == pytest.approx(L64, rel=1e-6)
+    gm = np.abs(g64[:16]).max()
+    assert np.abs(g32[:16] - g64[:16]).max() <= 1e-4 * gm
+    assert g32[16] == pytest.approx(g64[16], rel=1e-4)
+    assert g32[17] == pytest.approx(g64[17], rel=1e-4)
+    w64.close()
+    w32.close()
 
 
 @pytest.mark.parametrize("nx,n_sub", [(40, 2), (72, 1), (88, 3)])
