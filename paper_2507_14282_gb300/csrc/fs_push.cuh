@@ -181,6 +181,18 @@ struct PushLayout {
 // exclusive scan of n ints by one warp (lanes of warp w); out[n] = total
 __device__ __forceinline__ void warp_scan_excl(const int* in, int* out, int n,
                                                int lane) {
+  if (n <= 32) {  // one value per lane
+    const int s = lane < n ? in[lane] : 0;
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane < n) out[lane] = inc - s;
+    if (lane == 31) out[n] = inc;
+    return;
+  }
   const int per = (n + 31) / 32;
   const int b = lane * per, e = min(b + per, n);
   int s = 0;
