@@ -652,13 +652,14 @@ __device__ __forceinline__ void drain_stages(unsigned char* sm, const PushLayout
 
 // The push of one run by one CTA of a group of G CTAs (rank cta in the
 // group): tiles cta, cta + G, ... of the run; sm is the dynamic shared memory.
-template <typename T, int DIM, int CH, int NS, bool REL>
+// TXC, TYC: the tile shape as compile-time constants (0: the run's g.TX, g.TY)
+template <typename T, int DIM, int CH, int NS, bool REL, int TXC = 0, int TYC = 0>
 __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, const Phys& ph,
                                          const PushConst<T>& pc, int in, int out, int cta,
                                          int G, unsigned char* sm) {
   using A = typename Num<T>::acc;
   constexpr int PPT = (CH + kBlock - 1) / kBlock;
-  const PushLayout<T, DIM> L(g.TX, g.TY, CH, NS);
+  const PushLayout<T, DIM> L(TXC ? TXC : g.TX, TXC ? TYC : g.TY, CH, NS);
   const int TX = L.TX, TY = L.TY, EX = L.EX, EY = L.EY, NE = L.NE, NINT = L.NINT,
             NK = L.NK, NA = L.NA, AX = L.AX;
   uint64_t* bar = (uint64_t*)(sm + L.bar);
@@ -952,12 +953,14 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
 }
 
 
-// REL: compiled with the relativistic terms (used when c2inv > 0).
-template <typename T, int DIM, int CH, int NS, bool REL>
+// REL: compiled with the relativistic terms (used when c2inv > 0). TXC, TYC:
+// a tile shape compiled in (0: any shape, read from the geometry).
+template <typename T, int DIM, int CH, int NS, bool REL, int TXC = 0, int TYC = 0>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
     k_push(DevPtrs<T> d, StepArgs a, PushConst<T> pc) {
   extern __shared__ __align__(128) unsigned char sm[];
-  push_run<T, DIM, CH, NS, REL>(d, a.g, a.ph, pc, a.in, a.out, blockIdx.x, gridDim.x, sm);
+  push_run<T, DIM, CH, NS, REL, TXC, TYC>(d, a.g, a.ph, pc, a.in, a.out, blockIdx.x, gridDim.x,
+                                          sm);
 }
 
 // Batched push of an ensemble of independent runs in one persistent launch:
