@@ -1090,7 +1090,10 @@ __global__ void __launch_bounds__(kF1Threads)
 // Bin's cells). With `fin`, also Ohm's E and Bbar at the owned nodes from
 // the new B (Eo, Bbo, and the packed gather block G with its ghost row), as
 // the step's final k_ohm does. Same per-element arithmetic as ohm_node /
-// faraday_cell (2D).
+// faraday_cell (2D). Boxes that are a whole number of tiles (x and y) run
+// the interior tile columns 1 .. gx - 2 (full tiles whose halo lies inside
+// the box) as one launch with the tile's local sizes compiled in, and the
+// two wall columns as a second launch of the general form.
 constexpr int kFTX = 32, kFTY = 16, kFH = 5;  // owned cells; halo of the last substep
 constexpr int kFLX = kFTX + 2 * kFH, kFLY = kFTY + 2 * kFH;
 constexpr int kFNPT = ((kFLX + 1) * (kFLY + 1) + kBlock - 1) / kBlock;  // nodes per thread
@@ -1120,18 +1123,28 @@ struct TileWalk {
   }
 };
 
-template <typename T>
+// FINC: -1 / -2 (fin from the argument) or the compile-time fin of an interior
+// tile launch (a full tile whose halo lies inside the box: its local sizes
+// are constants); bx0: the first tile column of the launch (blockIdx.x + bx0)
+template <typename T, int FINC>
 __global__ void __launch_bounds__(kBlock)
     k_field_substep2(const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ nN,
                      const T* __restrict__ uN, T* __restrict__ Eo, T* __restrict__ Bbo,
-                     T* __restrict__ G, Geo g, Phys ph, FieldConst<T> fc, int fin) {
+                     T* __restrict__ G, Geo g, Phys ph, FieldConst<T> fc, int fin_arg, int bx0,
+                     int bx_last) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const int fin = FINC >= 0 ? FINC : fin_arg;
   const int nx = g.nx, ny = g.ny, nxn = g.nxn;
   const int nc = nx * ny, nn = nxn * ny;
   const int H = fin ? kFH : kFH - 1;  // four stages need 4 cells, the final Ohm one more
-  const int cx0 = blockIdx.x * kFTX, cx1 = min(nx, cx0 + kFTX);
-  const int cy0 = blockIdx.y * kFTY, cy1 = min(ny, cy0 + kFTY);
-  const int lx0 = max(0, cx0 - H), LX = min(nx, cx1 + H) - lx0;  // local cell columns
+  // interior launch: columns bx0 ..; edge launch (FINC -1): columns 0 and
+  // bx_last; FINC -2: every column, general sizes
+  const int bx = (FINC >= 0) ? (int)blockIdx.x + bx0
+                 : (FINC == -1 ? (blockIdx.x == 0 ? 0 : bx_last) : (int)blockIdx.x);
+  const int cx0 = bx * kFTX, cx1 = (FINC >= 0) ? cx0 + kFTX : min(nx, cx0 + kFTX);
+  const int cy0 = blockIdx.y * kFTY, cy1 = (FINC >= 0) ? cy0 + kFTY : min(ny, cy0 + kFTY);
+  const int lx0 = (FINC >= 0) ? cx0 - H : max(0, cx0 - H);
+  const int LX = (FINC >= 0) ? kFTX + 2 * H : min(nx, cx1 + H) - lx0;  // local cell columns
   const int ly0 = cy0 - H, LY = (cy1 - cy0) + 2 * H;             // local rows (unwrapped)
   const int NX = LX + 1, NC = LX * LY, NN = NX * (LY + 1);        // nodes: NX x (LY + 1)
   T* sB = (T*)smem;

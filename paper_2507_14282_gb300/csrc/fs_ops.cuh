@@ -174,19 +174,41 @@ struct OpsImpl {
     constexpr size_t smem = field_tile_smem<T>();
     static std::atomic<bool> attr(false);  // set once per process; setting it twice is harmless
     if (!attr.load()) {
-      cudaError_t e = cudaFuncSetAttribute(k_field_substep2<T>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
+      for (auto k : {k_field_substep2<T, -2>, k_field_substep2<T, -1>, k_field_substep2<T, 0>,
+                     k_field_substep2<T, 1>}) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+      }
       attr.store(true);
     }
-    const dim3 grid((s->g.nx + kFTX - 1) / kFTX, (s->g.ny + kFTY - 1) / kFTY);
+    const int gx = (s->g.nx + kFTX - 1) / kFTX, gy = (s->g.ny + kFTY - 1) / kFTY;
+    // interior tile columns (full, halo inside the box): 1 .. gx - 2 when the
+    // box is a whole number of tiles and rows; the rest take the general form
+    const bool split = gx >= 3 && s->g.nx % kFTX == 0 && s->g.ny % kFTY == 0 &&
+                       kFTX >= kFH;
     T* src = d.B;
     T* dst = d.Bs;
+    const FieldConst<T> fc = field_const<T>(s->ph);
     for (int sub = 0; sub < s->p.n_sub; ++sub) {
       const int fin = (sub + 1 == s->p.n_sub) ? 1 : 0;
-      k_field_substep2<T><<<grid, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb, d.G,
-                                                            s->g, s->ph, field_const<T>(s->ph),
-                                                            fin);
+      if (split) {
+        const dim3 gi(gx - 2, gy), ge(2, gy);
+        if (fin)
+          k_field_substep2<T, 1><<<gi, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
+                                                                d.G, s->g, s->ph, fc, fin, 1, 0);
+        else
+          k_field_substep2<T, 0><<<gi, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
+                                                                d.G, s->g, s->ph, fc, fin, 1, 0);
+        k_field_substep2<T, -1><<<ge, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
+                                                               d.G, s->g, s->ph, fc, fin, 0,
+                                                               gx - 1);
+      } else {
+        const dim3 grid(gx, gy);
+        // every column: the general form
+        k_field_substep2<T, -2><<<grid, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
+                                                                 d.G, s->g, s->ph, fc, fin, 0, 0);
+      }
       std::swap(src, dst);
     }
     if (src != d.B)  // odd n_sub: the field ended in the stage buffer

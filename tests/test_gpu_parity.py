@@ -466,12 +466,16 @@ def test_inject_round_trip(fs, prec, with_ids):
 
 
 # ---------------------------------------------------------------- FP32
-@pytest.mark.parametrize("dim", [1, 2, "2-ragged", "2-tiny", "2-odd"])
+@pytest.mark.parametrize("dim", [1, 2, "2-ragged", "2-tiny", "2-odd", "2-interior"])
 def test_fp32_fields_within_tolerance(fs, dim):
     if dim == 1:
         cfg = W.scaled(W.CONFIG_1D, nx=256)
     elif dim == 2:
         cfg = W.scaled(W.CONFIG_2D_FP32, nx=64, ny=16, ppc=16)
+    elif dim == "2-interior":
+        # a whole number of 32 x 16-cell field tiles, four columns: the two
+        # interior columns take the launch with the tile sizes compiled in
+        cfg = W.scaled(W.CONFIG_2D_FP32, nx=128, ny=32, ppc=16)
     elif dim == "2-tiny":
         # the whole box in one 32 x 16-cell field tile, rows repeated by the
         # periodic halo
