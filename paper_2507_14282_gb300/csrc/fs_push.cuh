@@ -554,7 +554,9 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
   // no particle of the tile can reach a box edge by a one-cell shift
   const int inner =
       i0 >= 1 && i0 + L.TX < g.nx && (DIM == 1 || (j0 >= 1 && j0 + L.TY < g.ny));
-  desc[2 * b + 1] = make_int4(i0, j0, inner, d.tile_base[c.x]);
+  // a tile's bucket starts at tile x capacity (fixed at set-up)
+  const int tbase = c.x * g.tile_cap;
+  desc[2 * b + 1] = make_int4(i0, j0, inner, tbase);
   if (c.z <= 0) return;
   const size_t bo = (size_t)b * L.bstride;
   mbar_arrive_expect_tx(bar, L.chunk_bytes(c.z));
@@ -562,7 +564,7 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
   for (int ly = 0; ly < L.NFY; ++ly)
     bulk_g2s(sm + L.F[0] + bo + (size_t)ly * row,
              d.G + ((size_t)(j0 + ly) * (g.nx + 1) + i0) * 8, row, bar);
-  const size_t first = (size_t)d.tile_base[c.x] + c.y;
+  const size_t first = (size_t)tbase + c.y;
   const uint32_t m4 = (uint32_t)((c.z + 3) & ~3);
   bulk_g2s(sm + L.cell[0] + bo, PI.cell + first, 4 * m4, bar);
   bulk_g2s(sm + L.ox[0] + bo, PI.ox + first, sizeof(T) * m4, bar);
