@@ -1139,6 +1139,7 @@ int fs_destroy(fs_handle* h) {
 
 namespace {
 constexpr int kBatchMaxCtas = 4096;  // CTA map entries the table holds
+constexpr int kBatchOversubscribe = 4;  // batched-push CTAs per resident CTA slot
 #ifndef FS_BATCH_BRANCHES
 #define FS_BATCH_BRANCHES 32
 #endif
@@ -1352,7 +1353,10 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
       ops->batch_setup(s0.g.dim, rel, chunk, smem, &occ) != cudaSuccess || occ < 1)
     return FS_ECUDA;
   if (cap > 0) occ = std::min(occ, cap);
-  const int ncta_max = std::min(nsm * occ, kBatchMaxCtas);
+  // four CTAs per resident slot: the runs' groups are whole CTAs, and with
+  // more, smaller CTAs than fit at once the hardware starts a waiting CTA
+  // wherever one finishes, which evens out the groups' unequal loads
+  const int ncta_max = std::min(nsm * occ * kBatchOversubscribe, kBatchMaxCtas);
   std::vector<long long> np(nruns);
   std::vector<int> nt(nruns), ncta(nruns);
   for (int r = 0; r < nruns; ++r) {
