@@ -350,9 +350,11 @@ int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
    per run; the batch is an execution schedule, not a different method).
    A batch steps several handles -- faux-shock runs of any size, one
    precision and dimension, created on one CUDA stream -- with one push
-   launch per step: each run gets a group of persistent CTAs about
-   proportional to its particles (a (run, tile) work list, each run's
-   pointers, geometry and physics read from a device table). When every run
+   launch per step for each class of runs (1D FP32 runs of tile width 4, 8
+   or 16 cells each form a class with that width compiled in; all other runs
+   one class): each run gets a group of CTAs about proportional to its
+   particles (a (run, tile) work list, each run's pointers, geometry and
+   physics read from a device table). When every run
    is 1D with x walls (the one-launch field advance), the rest of the step --
    movers, injection, moments, field advance, step counter -- is one launch
    per kernel over all runs too (each block works for one run, found from

@@ -1138,7 +1138,7 @@ int fs_destroy(fs_handle* h) {
 // (definitions keep the C linkage of their declarations in fs.h)
 
 namespace {
-constexpr int kBatchMaxCtas = 4096;  // CTA map entries the table holds
+constexpr int kBatchMaxCtas = 16384;  // CTA map entries the table holds
 constexpr int kBatchOversubscribe = 4;  // batched-push CTAs per resident CTA slot
 #ifndef FS_BATCH_BRANCHES
 #define FS_BATCH_BRANCHES 32
@@ -1188,6 +1188,10 @@ struct fs_batch {
   int2* map = nullptr;
   int ncta = 0;
   size_t smem = 0;
+  // one push launch per class of runs: its tile width (0: any), its CTAs'
+  // range of the map, its shared memory
+  struct Class { int txc, map0, ncta; size_t smem; };
+  std::vector<Class> classes;
   int dim = 1;
   int rel = 0;  // some run has relativistic ions (c > 0)
   int chunk = 0;  // the batch push's chunk (0: the large chunk)
@@ -1207,9 +1211,12 @@ namespace {
 // one launch, then each run's remaining kernels on its branch.
 cudaError_t batch_enqueue(fs_batch* b, int p, cudaStream_t st) {
   const int nr = (int)b->runs.size();
-  cudaError_t e = b->ops->push_batch(b->dim, b->rel, b->chunk, b->table + (size_t)p * nr * b->rec,
-                                     b->map, b->ncta, b->smem, st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  for (const auto& c : b->classes) {
+    e = b->ops->push_batch(b->dim, b->rel, b->chunk, c.txc, b->table + (size_t)p * nr * b->rec,
+                           b->map + c.map0, c.ncta, c.smem, st);
+    if (e != cudaSuccess) return e;
+  }
   if (b->tail_batched)
     return b->ops->batch_rest(b->table + (size_t)p * nr * b->rec, b->pre, nr, b->nblk,
                               b->n_sub_max, st);
@@ -1347,25 +1354,58 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
     if (runs[r]->sim.ph.c2inv > 0.0) rel = 1;
   }
   if (smem > 227 * 1024 - 2048) return FS_EINVAL;
-  int dev = 0, nsm = 0, occ = 0;
+  int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      ops->batch_setup(s0.g.dim, rel, chunk, smem, &occ) != cudaSuccess || occ < 1)
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return FS_ECUDA;
-  if (cap > 0) occ = std::min(occ, cap);
-  // four CTAs per resident slot: the runs' groups are whole CTAs, and with
-  // more, smaller CTAs than fit at once the hardware starts a waiting CTA
-  // wherever one finishes, which evens out the groups' unequal loads
-  const int ncta_max = std::min(nsm * occ * kBatchOversubscribe, kBatchMaxCtas);
   std::vector<long long> np(nruns);
-  std::vector<int> nt(nruns), ncta(nruns);
+  std::vector<int> nt(nruns), ncta(nruns), cls(nruns);
   for (int r = 0; r < nruns; ++r) {
     const int rc = fs_num_particles(runs[r], &np[r]);  // synchronises
     if (rc) return rc;
     nt[r] = runs[r]->sim.g.ntiles;
   }
-  int rc = fs_batch_plan(nruns, np.data(), nt.data(), ncta_max, ncta.data());
-  if (rc) return rc;
+  // classes: runs of one compiled-in tile width each, the rest together; one
+  // push launch per class after another, each planned over the whole GPU
+  std::vector<int> widths;  // class c's width (0: any)
+  for (int r = 0; r < nruns; ++r) {
+    const int tx = runs[r]->sim.g.TX;
+    const int w = (s0.g.dim == 1 && s0.p.precision == FS_FP32 && !rel && chunk != 512 &&
+                   (tx == 4 || tx == 8 || tx == 16)) ? tx : 0;
+    int c = -1;
+    for (size_t k = 0; k < widths.size(); ++k) if (widths[k] == w) c = (int)k;
+    if (c < 0) { c = (int)widths.size(); widths.push_back(w); }
+    cls[r] = c;
+  }
+  std::vector<fs_batch::Class> classes;
+  int map_used = 0;
+  for (size_t c = 0; c < widths.size(); ++c) {
+    std::vector<int> idx;
+    size_t sm_c = 0;
+    for (int r = 0; r < nruns; ++r)
+      if (cls[r] == (int)c) {
+        idx.push_back(r);
+        sm_c = std::max(sm_c, ops->batch_smem(s0.g.dim, runs[r]->sim.g.TX, runs[r]->sim.g.TY, chunk));
+      }
+    int occ = 0;
+    if (ops->batch_setup(s0.g.dim, rel, chunk, widths[c], sm_c, &occ) != cudaSuccess || occ < 1)
+      return FS_ECUDA;
+    if (cap > 0) occ = std::min(occ, cap);
+    // four CTAs per resident slot: the runs' groups are whole CTAs, and with
+    // more, smaller CTAs than fit at once the hardware starts a waiting CTA
+    // wherever one finishes, which evens out the groups' unequal loads
+    const int ncta_max = std::min(nsm * occ * kBatchOversubscribe,
+                                  kBatchMaxCtas / (int)widths.size());
+    std::vector<long long> npc;
+    std::vector<int> ntc, nc(idx.size());
+    for (int r : idx) { npc.push_back(np[r]); ntc.push_back(nt[r]); }
+    const int rc = fs_batch_plan((int)idx.size(), npc.data(), ntc.data(), ncta_max, nc.data());
+    if (rc) return rc;
+    int tot = 0;
+    for (size_t k = 0; k < idx.size(); ++k) { ncta[idx[k]] = nc[k]; tot += nc[k]; }
+    classes.push_back({widths[c], map_used, tot, sm_c});
+    map_used += tot;
+  }
   fs_batch* b = new fs_batch();
   b->runs.assign(runs, runs + nruns);
   b->stream = s0.stream;
@@ -1374,6 +1414,7 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
   b->rel = rel;
   b->chunk = chunk;
   b->smem = smem;
+  b->classes = classes;
   b->rec = batch_rec_bytes(s0.p.precision);
   b->table = (char*)table_dev;
   b->map = (int2*)(b->table + batch_map_offset(nruns, s0.p.precision));
@@ -1388,7 +1429,7 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
     for (int p = 0; p < 2; ++p)
       ops->fill_batch_run(&s, (s.cur + p) & 1, ncta[r],
                           host.data() + ((size_t)p * nruns + r) * b->rec);
-    for (int k = 0; k < ncta[r]; ++k) map.push_back(make_int2(r, k));
+
     b->tail_batched = b->tail_batched && tail_batchable(s);
     b->n_sub_max = std::max(b->n_sub_max, s.p.n_sub);
     const int n1 = nruns + 1;
@@ -1397,6 +1438,10 @@ int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev, size_t tab
     pre[2 * n1 + r + 1] = pre[2 * n1 + r] + field1_blocks(s);
   }
   for (int k = 0; k < 3; ++k) b->nblk[k] = pre[(size_t)k * (nruns + 1) + nruns];
+  for (size_t c = 0; c < classes.size(); ++c)  // the map in class order
+    for (int r = 0; r < nruns; ++r)
+      if (cls[r] == (int)c)
+        for (int k = 0; k < ncta[r]; ++k) map.push_back(make_int2(r, k));
   b->ncta = (int)map.size();
   memcpy(host.data() + batch_map_offset(nruns, s0.p.precision), map.data(),
          sizeof(int2) * map.size());

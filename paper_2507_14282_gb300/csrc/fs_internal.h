@@ -168,8 +168,10 @@ struct Ops {
   // else 0: the large chunk)
   size_t (*batch_smem)(int dim, int tx, int ty, int chunk);
   // rel: the push variant with the relativistic terms (some run has c > 0)
-  cudaError_t (*batch_setup)(int dim, int rel, int chunk, size_t smem, int* occ);
-  cudaError_t (*push_batch)(int dim, int rel, int chunk, const void* runs,
+  // txc: the tile width of every run of the launch (1D FP32 widths 4, 8, 16
+  // have a kernel with the width compiled in; else 0)
+  cudaError_t (*batch_setup)(int dim, int rel, int chunk, int txc, size_t smem, int* occ);
+  cudaError_t (*push_batch)(int dim, int rel, int chunk, int txc, const void* runs,
                             const int2* cta_map, int ncta, size_t smem, cudaStream_t st);
   // the rest of a batched step in one launch per kernel over every run (1D
   // runs with x walls): pre holds three block prefixes over the runs (movers,

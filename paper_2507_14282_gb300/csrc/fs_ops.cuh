@@ -346,9 +346,9 @@ struct OpsImpl {
     return dim == 1 ? PushLayout<T, 1>(tx, ty, ch, ns).bytes
                     : PushLayout<T, 2>(tx, ty, ch, ns).bytes;
   }
-  template <int DIM, int CH, int NS, bool REL>
+  template <int DIM, int CH, int NS, bool REL, int TXC = 0>
   static cudaError_t batch_kernel_setup(size_t smem, int* occ) {
-    auto kern = k_push_batch<T, DIM, CH, NS, REL>;
+    auto kern = k_push_batch<T, DIM, CH, NS, REL, TXC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess && occ)
@@ -365,8 +365,19 @@ struct OpsImpl {
   }
   // sets the shared-memory attribute; occ (optional): CTAs per SM. rel: the
   // variant with the relativistic terms (some run has a finite c).
-  static cudaError_t batch_setup(int dim, int rel, int chunk, size_t smem, int* occ) {
+  // the 1D FP32 tile widths compiled into their own batched push
+  static bool batch_width_compiled(int dim, int rel, int chunk, int txc) {
+    return sizeof(T) == 4 && dim == 1 && !rel && !batch_small(chunk) &&
+           (txc == 4 || txc == 8 || txc == 16);
+  }
+  static cudaError_t batch_setup(int dim, int rel, int chunk, int txc, size_t smem, int* occ) {
     using S = PushShape<T>;
+    if (batch_width_compiled(dim, rel, chunk, txc)) {
+      constexpr int CH = S::kChunkLarge, NS = S::kStagesLarge;
+      if (txc == 4) return batch_kernel_setup<1, CH, NS, false, 4>(smem, occ);
+      if (txc == 8) return batch_kernel_setup<1, CH, NS, false, 8>(smem, occ);
+      return batch_kernel_setup<1, CH, NS, false, 16>(smem, occ);
+    }
     if (batch_small(chunk))
       return batch_setup_shape<S::kChunkSmall, S::kStagesSmall>(dim, rel, smem, occ);
     return batch_setup_shape<S::kChunkLarge, S::kStagesLarge>(dim, rel, smem, occ);
@@ -379,10 +390,17 @@ struct OpsImpl {
     else
       k_push_batch<T, 2, CH, NS, REL><<<ncta, kBlock, smem, st>>>(r, cta_map);
   }
-  static cudaError_t push_batch(int dim, int rel, int chunk, const void* runs,
+  static cudaError_t push_batch(int dim, int rel, int chunk, int txc, const void* runs,
                                 const int2* cta_map, int ncta, size_t smem, cudaStream_t st) {
     using S = PushShape<T>;
     const BatchRun<T>* r = (const BatchRun<T>*)runs;
+    if (batch_width_compiled(dim, rel, chunk, txc)) {
+      constexpr int CH = S::kChunkLarge, NS = S::kStagesLarge;
+      if (txc == 4) k_push_batch<T, 1, CH, NS, false, 4><<<ncta, kBlock, smem, st>>>(r, cta_map);
+      else if (txc == 8) k_push_batch<T, 1, CH, NS, false, 8><<<ncta, kBlock, smem, st>>>(r, cta_map);
+      else k_push_batch<T, 1, CH, NS, false, 16><<<ncta, kBlock, smem, st>>>(r, cta_map);
+      return cudaGetLastError();
+    }
     const bool sm = batch_small(chunk);
     if (rel) {
       if (sm) push_batch_launch<S::kChunkSmall, S::kStagesSmall, true>(dim, r, cta_map, ncta, smem, st);

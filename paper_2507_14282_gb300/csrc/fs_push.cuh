@@ -969,7 +969,8 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
 // CTA b works on run cta_map[b].x as rank cta_map[b].y of that run's group of
 // runs[run].ncta CTAs; the run's pointers, geometry and physics come from the
 // device table, copied once into shared memory.
-template <typename T, int DIM, int CH, int NS, bool REL>
+// TXC: the tile width of every run the launch serves, compiled in (0: any)
+template <typename T, int DIM, int CH, int NS, bool REL, int TXC = 0>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
     k_push_batch(const BatchRun<T>* __restrict__ runs, const int2* __restrict__ cta_map) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -980,7 +981,8 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
   int* dst = reinterpret_cast<int*>(&R);
   for (int k = threadIdx.x; k < (int)(sizeof(BatchRun<T>) / 4); k += kBlock) dst[k] = src[k];
   __syncthreads();
-  push_run<T, DIM, CH, NS, REL>(R.d, R.g, R.ph, R.pc, R.in, R.out, cm.y, R.ncta, sm);
+  push_run<T, DIM, CH, NS, REL, TXC, (TXC ? 1 : 0)>(R.d, R.g, R.ph, R.pc, R.in, R.out, cm.y,
+                                                      R.ncta, sm);
 }
 
 // ---------------------------------------------------------------- batched step tail
