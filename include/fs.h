@@ -384,9 +384,10 @@ int fs_batch_query(int nruns, int precision, size_t* table_bytes);
 /* Creates a batch over runs[0..nruns-1]. The handles are not owned: each
    stays valid, and is not stepped on its own, until fs_batch_destroy.
    Synchronises the stream and sizes the CTA groups from the current
-   particle counts (four CTAs per CTA slot the GPU holds at once, at most
-   4096). FS_EINVAL: NULL arguments, handles of mixed precision, dimension or
-   stream, a table smaller than fs_batch_query's size, or more runs than
+   particle counts (for each class of runs, four CTAs per CTA slot the GPU
+   holds at once, at most 16384 over all classes). FS_EINVAL: NULL
+   arguments, handles of mixed precision, dimension or stream, a table
+   smaller than fs_batch_query's size, or more runs in a class than its
    CTAs; a handle's sticky error is returned as it is. */
 int fs_batch_init(fs_handle* const* runs, int nruns, void* table_dev,
                   size_t table_bytes, fs_batch** out);
