@@ -258,14 +258,26 @@ __device__ __forceinline__ void movers_body(const DevPtrs<T>& d, const Geo& g, i
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const Parts<T> PO = d.P[out];
-  for (int t = blk * wpb + (threadIdx.x >> 5); t < g.ntiles; t += nblk * wpb) {
-    const int nm = d.mcnt[t];
+  const int stride = nblk * wpb;
+  int t = blk * wpb + (threadIdx.x >> 5);
+  int nm_next = t < g.ntiles ? d.mcnt[t] : 0;
+  for (; t < g.ntiles; t += stride) {
+    const int nm = nm_next;  // the next tile's count is loaded a tile ahead
+    nm_next = t + stride < g.ntiles ? d.mcnt[t + stride] : 0;
     const int mb = t * g.mover_per_tile;
     for (int k0 = 0; k0 < nm; k0 += 32) {  // nm is the same for the whole warp
       const int k = k0 + lane;
       const bool act = k < nm;
       const int src = mb + k;
+      // the whole record is loaded before the slot is known, so that its
+      // loads overlap the slot atomic
       const int cell = act ? d.M.cell[src] : 0;
+      const T ox = act ? d.M.ox[src] : (T)0;
+      const T oy = (DIM == 2 && act) ? d.M.oy[src] : (T)0;
+      const T vx = act ? d.M.vx[src] : (T)0;
+      const T vy = act ? d.M.vy[src] : (T)0;
+      const T vz = act ? d.M.vz[src] : (T)0;
+      const uint32_t id = act ? d.M.id[src] : 0u;
       const int i = cell & 0xFFFF, j = cell >> 16;
       const int dt = act ? (j / g.TY) * g.ntx + i / g.TX : -1;
       // lanes bound for the same tile take consecutive slots after one
@@ -282,14 +294,14 @@ __device__ __forceinline__ void movers_body(const DevPtrs<T>& d, const Geo& g, i
         atomicOr(&d.ctr->status, kStatusCapacity);
         continue;
       }
-      const int gi = d.tile_base[dt] + slot;
+      const int gi = dt * g.tile_cap + slot;  // a tile's bucket starts at tile x capacity
       PO.cell[gi] = cell;
-      PO.ox[gi] = d.M.ox[src];
-      if (DIM == 2) PO.oy[gi] = d.M.oy[src];
-      PO.vx[gi] = d.M.vx[src];
-      PO.vy[gi] = d.M.vy[src];
-      PO.vz[gi] = d.M.vz[src];
-      PO.id[gi] = d.M.id[src];
+      PO.ox[gi] = ox;
+      if (DIM == 2) PO.oy[gi] = oy;
+      PO.vx[gi] = vx;
+      PO.vy[gi] = vy;
+      PO.vz[gi] = vz;
+      PO.id[gi] = id;
     }
   }
 }
@@ -348,7 +360,7 @@ __device__ __forceinline__ void place_new(const DevPtrs<T>& d, const Geo& g,
     atomicOr(&d.ctr->status, kStatusCapacity);
     return;
   }
-  const int gi = d.tile_base[t] + slot;
+  const int gi = t * g.tile_cap + slot;  // a tile's bucket starts at tile x capacity
   const Parts<T> P = d.P[buf];
   P.cell[gi] = (j << 16) | i;
   P.ox[gi] = fx;
