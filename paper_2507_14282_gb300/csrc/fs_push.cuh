@@ -115,7 +115,7 @@ struct PushLayout {
   // stage 0's regions; stage b sits b * bstride bytes further
   size_t F[1], cell[1], ox[1], oy[1], vx[1], vy[1], vz[1], id[1];
   size_t sW, sV, sF, scell, sid;  // key-sorted buffer
-  size_t acc, kc, wk, e2k, k2e, desc, bar, pf, tally, bytes;
+  size_t acc, kc, wk, e2k, k2e, desc, bar, pf, tally, pst, dq, bytes;
   size_t bstride;  // distance between two chunk buffers
   __host__ __device__ static size_t take(size_t& o, size_t n) {
     o = (o + 15) / 16 * 16;
@@ -166,6 +166,8 @@ struct PushLayout {
     acc = take(o, sizeof(typename Num<T>::acc) * 2 * 4 * NA);  // two tiles in flight
     kc = take(o, sizeof(int) * 2 * NK);                         // two chunks in flight
     wk = take(o, sizeof(int) * kWarps * (NK + 1));              // key offsets per warp
+    pst = take(o, sizeof(int) * (NK + 1));  // first deposit piece of each key
+    dq = take(o, sizeof(int) * 2);          // deposit piece counters, two chunks
     e2k = take(o, sizeof(uint16_t) * NE);
     k2e = take(o, sizeof(int) * NE);
     bytes = (o + 127) / 128 * 128;
@@ -642,6 +644,42 @@ __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, 
   }
 }
 
+// Deposit of a key-sorted chunk in pieces: key k's particles [wk[k], wk[k+1])
+// form ceil(n / kPiece) pieces of at most kPiece, numbered from pst[k]. Warp w
+// takes piece w, then the next unclaimed piece from the counter *q until none
+// is left, so that warps which reach the deposit early take more of it. A
+// piece is one team reduction: whole keys (cells) where they are not large,
+// since the reduction, not the particle count, sets most of a piece's cost.
+constexpr int kPiece = 160;
+template <typename T, int DIM, bool REL>
+__device__ __forceinline__ void deposit_pieces(typename Num<T>::acc* ACC, int NA, int AX, int NE,
+                                               const int* wk, const int* pst, const int* k2e,
+                                               const T* W, const T* V, int* q, int warp,
+                                               int lane) {
+  constexpr int PS = kPiece;
+  const int np = pst[NE];
+  int gi = warp;
+  while (gi < np) {
+    int k = -1;
+    for (int kb = 0; kb < NE; kb += 32) {
+      const int kk = kb + lane;
+      const unsigned h =
+          __ballot_sync(0xffffffffu, kk < NE && pst[kk] <= gi && gi < pst[kk + 1]);
+      if (h) {
+        k = kb + __ffs(h) - 1;
+        break;
+      }
+    }
+    if (k < 0) break;
+    const int b0 = wk[k] + (gi - pst[k]) * PS;
+    const int b1 = min(b0 + PS, wk[k + 1]);
+    team_deposit<T, DIM, REL>(ACC, NA, AX, k2e[k], b0, b1, W, V, lane);
+    int nx = 0;
+    if (lane == 0) nx = atomicAdd(q, 1);
+    gi = kWarps + __shfl_sync(0xffffffffu, nx, 0);
+  }
+}
+
 // Every stage holds a chunk not yet consumed.
 template <typename T, int DIM>
 __device__ __forceinline__ void drain_stages(unsigned char* sm, const PushLayout<T, DIM>& L,
@@ -703,6 +741,9 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
   }
   for (int k = tid; k < 2 * 4 * NA; k += kBlock) ACC0[k] = (A)0;
   for (int k = tid; k < 2 * NK; k += kBlock) kc0[k] = 0;
+  int* pst = (int*)(sm + L.pst);
+  int* dq = (int*)(sm + L.dq);
+  if (tid < 2) dq[tid] = 0;
 
   if (tid == 0) {
     for (int b = 0; b < NS; ++b) mbar_init(&bar[b], 1);
@@ -733,11 +774,23 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
   int tiles_seen = 0, tpar = 0;  // accumulator buffer of the current tile
   int pend = -1, pend_par = 0;   // tile whose partial is written next chunk
   int status = 0;
+  int dpar = -1;  // accumulator buffer of the chunk whose deposit is pending (-1: none)
+  int* oc = (int*)(sm + L.scell);
+  uint32_t* oid = (uint32_t*)(sm + L.sid);
+  T* oW = (T*)(sm + L.sW);
+  T* oV = (T*)(sm + L.sV);
+  T* oF = (T*)(sm + L.sF);
 
   int b = 0;
   for (int ci = 0;; ++ci, b = (b + 1 == NS) ? 0 : b + 1) {
     const int4 c = desc[2 * b];
-    if (c.x >= g.ntiles) break;
+    if (c.x >= g.ntiles) {
+      // the last chunk's deposit
+      if (dpar >= 0)
+        deposit_pieces<T, DIM, REL>(ACC0 + dpar * 4 * NA, NA, AX, NE, wk, pst, k2e, oW, oV,
+                                    dq + ((ci - 1) & 1), warp, lane);
+      break;
+    }
     const int i0 = desc[2 * b + 1].x, j0 = desc[2 * b + 1].y;
     const bool inner = desc[2 * b + 1].z != 0;
     const int t = c.x, m = c.z;
@@ -801,6 +854,11 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       base = __shfl_sync(0xffffffffu, base, leader);
       rk[r] = base + __popc(peers & ((1u << lane) - 1u));
     }
+    // ---- the previous chunk's deposit, after this chunk's push: warps that
+    //      finished their push early take more of it
+    if (dpar >= 0)
+      deposit_pieces<T, DIM, REL>(ACC0 + dpar * 4 * NA, NA, AX, NE, wk, pst, k2e, oW, oV,
+                                  dq + ((ci - 1) & 1), warp, lane);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(&d.ctr->status, kStatusTimeout);
@@ -820,15 +878,29 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       pend = -1;
     }
     for (int q = tid; q < NK; q += kBlock) kc0[((ci + 1) & 1) * NK + q] = 0;
+    if (tid == 0) dq[ci & 1] = 0;
     const int tbase = desc[2 * b + 1].w;  // read before the stage is refilled
     // ---- key offsets (each warp its own copy); copy into key order
     warp_scan_excl(kc, wk, NK, lane);
     __syncwarp();
-    int* oc = (int*)(sm + L.scell);
-    uint32_t* oid = (uint32_t*)(sm + L.sid);
-    T* oW = (T*)(sm + L.sW);
-    T* oV = (T*)(sm + L.sV);
-    T* oF = (T*)(sm + L.sF);
+    if (warp == kWarps - 1) {  // the deposit's pieces per key
+      constexpr int PS = kPiece;
+      int carry = 0;
+      for (int kb = 0; kb < NE; kb += 32) {
+        const int kk = kb + lane;
+        const int n = kk < NE ? wk[kk + 1] - wk[kk] : 0;
+        const int pc = (n + PS - 1) / PS;
+        int inc = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += v;
+        }
+        if (kk < NE) pst[kk] = carry + inc - pc;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) pst[NE] = carry;
+    }
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
       const int key = ky[r];
@@ -900,28 +972,7 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
         d.M.id[gi] = oid[si];
       }
     }
-    // ---- deposit in key order: warp w takes an equal share of the sorted
-    //      deposited range [0, offset of FAR) and each key's part of it
-    {
-      const int nd = wk[NE];
-      const int r0 = (int)(((long long)nd * warp) / kWarps);
-      const int r1 = (int)(((long long)nd * (warp + 1)) / kWarps);
-      // first key whose range reaches past r0
-      int k = 0;
-      for (int kb = 0; kb < NE; kb += 32) {
-        const int kk = kb + lane;
-        const unsigned hit = __ballot_sync(0xffffffffu, kk < NE && wk[kk + 1] > r0);
-        if (hit) {
-          k = kb + __ffs(hit) - 1;
-          break;
-        }
-        k = NE;
-      }
-      for (; k < NE && wk[k] < r1; ++k) {
-        const int b0 = max(wk[k], r0), b1 = min(wk[k + 1], r1);
-        if (b0 < b1) team_deposit<T, DIM, REL>(ACC, NA, AX, k2e[k], b0, b1, oW, oV, lane);
-      }
-    }
+    dpar = tpar;  // deposited after the next chunk's push
     outRun += S;
     movRun += Lv;
     if (c.y + m >= c.w) {
