@@ -645,9 +645,10 @@ __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, 
 }
 
 // Deposit of a key-sorted chunk in pieces: key k's particles [wk[k], wk[k+1])
-// form ceil(n / kPiece) pieces of at most kPiece, numbered from pst[k]. Warp w
-// takes piece w, then the next unclaimed piece from the counter *q until none
-// is left, so that warps which reach the deposit early take more of it. A
+// form ceil(n / kPiece) pieces of at most kPiece, numbered from pst[k]. Warp
+// w > 0 takes piece w - 1, then (and warp 0 from the start) the next
+// unclaimed piece from the counter *q until none is left, so that warps which
+// reach the deposit early take more of it. A
 // piece is one team reduction: whole keys (cells) where they are not large,
 // since the reduction, not the particle count, sets most of a piece's cost.
 constexpr int kPiece = 160;
@@ -658,7 +659,16 @@ __device__ __forceinline__ void deposit_pieces(typename Num<T>::acc* ACC, int NA
                                                int lane) {
   constexpr int PS = kPiece;
   const int np = pst[NE];
-  int gi = warp;
+  // warp 0 (which issues the bulk copies) claims from the start; warp w > 0
+  // takes piece w - 1 first
+  int gi;
+  if (warp == 0) {
+    int nx = 0;
+    if (lane == 0) nx = atomicAdd(q, 1);
+    gi = kWarps - 1 + __shfl_sync(0xffffffffu, nx, 0);
+  } else {
+    gi = warp - 1;
+  }
   while (gi < np) {
     int k = -1;
     for (int kb = 0; kb < NE; kb += 32) {
@@ -676,7 +686,7 @@ __device__ __forceinline__ void deposit_pieces(typename Num<T>::acc* ACC, int NA
     team_deposit<T, DIM, REL>(ACC, NA, AX, k2e[k], b0, b1, W, V, lane);
     int nx = 0;
     if (lane == 0) nx = atomicAdd(q, 1);
-    gi = kWarps + __shfl_sync(0xffffffffu, nx, 0);
+    gi = kWarps - 1 + __shfl_sync(0xffffffffu, nx, 0);
   }
 }
 
