@@ -116,7 +116,7 @@ typedef struct fs_params {
   /* launch shape of the particle push (a tuning choice; results do not
      depend on it in FP64): */
   int push_chunk;          /* particles per shared-memory chunk: 0 (library
-                              choice), 512 (three stages in FP32) or 640 (two
+                              choice), 512 (three stages in FP32) or 576 (two
                               stages; FP32 only) */
   int push_ctas_per_sm;    /* persistent CTAs per SM: 0 (as many as fit) or a
                               cap >= 1 */

@@ -29,12 +29,13 @@ size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool divides(int a, int b) { return a > 0 && b % a == 0; }
 
 // The push's shared memory for a tx x ty tile fits one CTA.
-// The push's chunk: the caller's choice, else 640 particles in FP32 (a
-// 512-particle mean tile in one chunk) unless the mean tile holds at most
-// 256, and 512 in FP64 (two CTAs per SM with its wider particles).
+// The push's chunk: the caller's choice, else 576 particles in FP32 (a
+// 512-particle mean tile in one chunk, four CTAs per SM) unless the mean tile
+// holds at most 256, and 512 in FP64 (two CTAs per SM with its wider
+// particles).
 int push_chunk_of(const fs_params* p, int tx, int ty) {
   if (p->push_chunk) return p->push_chunk;
-  return (p->precision == FS_FP32 && (long long)tx * ty * p->ppc > 256) ? 640 : 512;
+  return (p->precision == FS_FP32 && (long long)tx * ty * p->ppc > 256) ? 576 : 512;
 }
 
 bool push_tile_fits(const fs_params* p, int tx, int ty) {
@@ -111,7 +112,7 @@ int validate(const fs_params* p) {
   if (p->spec_np < 1 || !(p->spec_pmin > 0) || !(p->spec_pmax > p->spec_pmin)) return FS_EINVAL;
   if (p->mach_a < 0) return FS_EINVAL;
   if (p->push_chunk != 0 && p->push_chunk != 512 &&
-      !(p->push_chunk == 640 && p->precision == FS_FP32))
+      !(p->push_chunk == 576 && p->precision == FS_FP32))
     return FS_EINVAL;
   if (p->push_ctas_per_sm < 0) return FS_EINVAL;
   return FS_OK;

@@ -252,56 +252,83 @@ __device__ __forceinline__ bool fs_return(double& vx, double& vy, double& vz,
 // ------------------------------------------------------------------------
 // Block blk of nblk: one warp per source tile, its leavers go to their
 // destination tiles.
+// One leaver record of the mover list.
+template <typename T>
+struct MoverRec {
+  int cell;
+  T ox, oy, vx, vy, vz;
+  uint32_t id;
+};
+template <typename T, int DIM>
+__device__ __forceinline__ MoverRec<T> mover_load(const DevPtrs<T>& d, bool act, int src) {
+  MoverRec<T> r;
+  r.cell = act ? d.M.cell[src] : 0;
+  r.ox = act ? d.M.ox[src] : (T)0;
+  r.oy = (DIM == 2 && act) ? d.M.oy[src] : (T)0;
+  r.vx = act ? d.M.vx[src] : (T)0;
+  r.vy = act ? d.M.vy[src] : (T)0;
+  r.vz = act ? d.M.vz[src] : (T)0;
+  r.id = act ? d.M.id[src] : 0u;
+  return r;
+}
+// destination tile of an active record (-1: none)
+template <typename T>
+__device__ __forceinline__ int mover_dest(const Geo& g, bool act, const MoverRec<T>& r) {
+  const int i = r.cell & 0xFFFF, j = r.cell >> 16;
+  return act ? (j / g.TY) * g.ntx + i / g.TX : -1;
+}
+template <typename T, int DIM>
+__device__ __forceinline__ void mover_store(const DevPtrs<T>& d, const Geo& g, int out, bool act,
+                                            int dt, int slot, const MoverRec<T>& r) {
+  if (!act) return;
+  if (slot >= g.tile_cap) {
+    atomicSub(&d.cnt[out][dt], 1);
+    atomicOr(&d.ctr->status, kStatusCapacity);
+    return;
+  }
+  const Parts<T> PO = d.P[out];
+  const int gi = dt * g.tile_cap + slot;  // a tile's bucket starts at tile x capacity
+  PO.cell[gi] = r.cell;
+  PO.ox[gi] = r.ox;
+  if (DIM == 2) PO.oy[gi] = r.oy;
+  PO.vx[gi] = r.vx;
+  PO.vy[gi] = r.vy;
+  PO.vz[gi] = r.vz;
+  PO.id[gi] = r.id;
+}
+
+// Block blk of nblk: one warp per source tile, its leavers go to their
+// destination tiles; each warp works on two source tiles at a time (their
+// loads and slot atomics in flight together). Lanes bound for the same tile
+// take consecutive slots after one atomic by the lowest of them.
 template <typename T, int DIM>
 __device__ __forceinline__ void movers_body(const DevPtrs<T>& d, const Geo& g, int out, int blk,
                                             int nblk) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  const Parts<T> PO = d.P[out];
   const int stride = nblk * wpb;
-  int t = blk * wpb + (threadIdx.x >> 5);
-  int nm_next = t < g.ntiles ? d.mcnt[t] : 0;
-  for (; t < g.ntiles; t += stride) {
-    const int nm = nm_next;  // the next tile's count is loaded a tile ahead
-    nm_next = t + stride < g.ntiles ? d.mcnt[t + stride] : 0;
-    const int mb = t * g.mover_per_tile;
-    for (int k0 = 0; k0 < nm; k0 += 32) {  // nm is the same for the whole warp
+  const unsigned below = (1u << lane) - 1u;
+  for (int t = blk * wpb + (threadIdx.x >> 5); t < g.ntiles; t += 2 * stride) {
+    const int t2 = t + stride;
+    const int nm1 = d.mcnt[t];
+    const int nm2 = t2 < g.ntiles ? d.mcnt[t2] : 0;
+    const int mb1 = t * g.mover_per_tile, mb2 = t2 * g.mover_per_tile;
+    for (int k0 = 0; k0 < nm1 || k0 < nm2; k0 += 32) {  // counts are warp-uniform
       const int k = k0 + lane;
-      const bool act = k < nm;
-      const int src = mb + k;
-      // the whole record is loaded before the slot is known, so that its
-      // loads overlap the slot atomic
-      const int cell = act ? d.M.cell[src] : 0;
-      const T ox = act ? d.M.ox[src] : (T)0;
-      const T oy = (DIM == 2 && act) ? d.M.oy[src] : (T)0;
-      const T vx = act ? d.M.vx[src] : (T)0;
-      const T vy = act ? d.M.vy[src] : (T)0;
-      const T vz = act ? d.M.vz[src] : (T)0;
-      const uint32_t id = act ? d.M.id[src] : 0u;
-      const int i = cell & 0xFFFF, j = cell >> 16;
-      const int dt = act ? (j / g.TY) * g.ntx + i / g.TX : -1;
-      // lanes bound for the same tile take consecutive slots after one
-      // atomic by the lowest of them (a tile's leavers go to a few tiles)
-      const unsigned peers = __match_any_sync(0xffffffffu, dt);
-      const int leader = __ffs(peers) - 1;
-      int base = 0;
-      if (act && lane == leader) base = atomicAdd(&d.cnt[out][dt], __popc(peers));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (!act) continue;
-      const int slot = base + __popc(peers & ((1u << lane) - 1u));
-      if (slot >= g.tile_cap) {
-        atomicSub(&d.cnt[out][dt], 1);
-        atomicOr(&d.ctr->status, kStatusCapacity);
-        continue;
-      }
-      const int gi = dt * g.tile_cap + slot;  // a tile's bucket starts at tile x capacity
-      PO.cell[gi] = cell;
-      PO.ox[gi] = ox;
-      if (DIM == 2) PO.oy[gi] = oy;
-      PO.vx[gi] = vx;
-      PO.vy[gi] = vy;
-      PO.vz[gi] = vz;
-      PO.id[gi] = id;
+      const bool a1 = k < nm1, a2 = k < nm2;
+      const MoverRec<T> r1 = mover_load<T, DIM>(d, a1, mb1 + k);
+      const MoverRec<T> r2 = mover_load<T, DIM>(d, a2, mb2 + k);
+      const int dt1 = mover_dest(g, a1, r1), dt2 = mover_dest(g, a2, r2);
+      const unsigned p1 = __match_any_sync(0xffffffffu, dt1);
+      const unsigned p2 = __match_any_sync(0xffffffffu, dt2);
+      const int l1 = __ffs(p1) - 1, l2 = __ffs(p2) - 1;
+      int b1 = 0, b2 = 0;
+      if (a1 && lane == l1) b1 = atomicAdd(&d.cnt[out][dt1], __popc(p1));
+      if (a2 && lane == l2) b2 = atomicAdd(&d.cnt[out][dt2], __popc(p2));
+      b1 = __shfl_sync(0xffffffffu, b1, l1);
+      b2 = __shfl_sync(0xffffffffu, b2, l2);
+      mover_store<T, DIM>(d, g, out, a1, dt1, b1 + __popc(p1 & below), r1);
+      mover_store<T, DIM>(d, g, out, a2, dt2, b2 + __popc(p2 & below), r2);
     }
   }
 }

@@ -74,7 +74,7 @@ struct PushShape;
 template <>
 struct PushShape<float> {
   static constexpr int kChunkSmall = 512, kStagesSmall = 3;
-  static constexpr int kChunkLarge = 640, kStagesLarge = 2;
+  static constexpr int kChunkLarge = 576, kStagesLarge = 2;
 };
 template <>
 struct PushShape<double> {

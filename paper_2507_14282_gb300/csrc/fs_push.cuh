@@ -156,7 +156,8 @@ struct PushLayout {
     o += (size_t)(NS - 1) * bstride;
     // the key-sorted copy of the chunk being finished: the four CIC corner
     // weights, {vx, vy, vz, 1/gamma}, {fx, fy}, cell and id per particle
-    sW = take(o, sizeof(T) * 4 * CH);
+    // FP32: no weights (the deposit forms them from the offsets)
+    sW = take(o, sizeof(T) == 4 ? 0 : sizeof(T) * 4 * CH);
     sV = take(o, sizeof(T) * 4 * CH);
     sF = take(o, sizeof(T) * 2 * CH);
     scell = take(o, sizeof(int) * CH);
@@ -586,10 +587,25 @@ __device__ __forceinline__ void issue_chunk(unsigned char* sm, const PushLayout<
 // total in one lane, which adds it to the tile's node accumulator. Each
 // contribution is formed as in the per-particle scheme, so in fixed point
 // the sums do not depend on the order.
-template <typename T, bool REL>
+template <typename T, int DIM, bool REL>
 __device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T* W,
-                                         const T* V, int i, int c) {
-  const T cw = W[4 * i + c];
+                                         const T* V, const T* Fo, const uint32_t* ID,
+                                         T wth, T wcr, int i, int c) {
+  T cw;
+  if constexpr (sizeof(T) == 4) {  // corner weight wp * (gx * gy) from the offsets
+    T f[2];
+    ld2(Fo + 2 * i, f);
+    const T wp = (ID[i] & kIdCR) ? wcr : wth;
+    const T gx = (c & 1) ? f[0] : (T)1 - f[0];
+    if (DIM == 2) {
+      const T gy = (c >> 1) ? f[1] : (T)1 - f[1];
+      cw = wp * (gx * gy);
+    } else {
+      cw = wp * gx;
+    }
+  } else {
+    cw = W[4 * i + c];
+  }
   T v[4];
   ld4(V + 4 * i, v);
   if (REL) {  // relativistic ions: V holds u and 1/gamma
@@ -606,6 +622,7 @@ __device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T
 template <typename T, int DIM, bool REL>
 __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, int AX,
                                              int le, int b0, int b1, const T* W, const T* V,
+                                             const T* Fo, const uint32_t* ID, T wth, T wcr,
                                              int lane) {
   using A_t = typename Num<T>::acc;
   constexpr int NC = (DIM == 2) ? 4 : 2;
@@ -614,10 +631,10 @@ __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, 
   A_t acc[4] = {(A_t)0, (A_t)0, (A_t)0, (A_t)0};
   int i = b0 + s;
   for (; i + SPL < b1; i += 2 * SPL) {  // two particles in flight per lane
-    team_add<T, REL>(acc, W, V, i, c);
-    team_add<T, REL>(acc, W, V, i + SPL, c);
+    team_add<T, DIM, REL>(acc, W, V, Fo, ID, wth, wcr, i, c);
+    team_add<T, DIM, REL>(acc, W, V, Fo, ID, wth, wcr, i + SPL, c);
   }
-  if (i < b1) team_add<T, REL>(acc, W, V, i, c);
+  if (i < b1) team_add<T, DIM, REL>(acc, W, V, Fo, ID, wth, wcr, i, c);
   // two halving levels leave one quantity per lane, the rest add pairs
   {
     const bool up = (s & (SPL / 2)) != 0;
@@ -655,8 +672,9 @@ constexpr int kPiece = 160;
 template <typename T, int DIM, bool REL>
 __device__ __forceinline__ void deposit_pieces(typename Num<T>::acc* ACC, int NA, int AX, int NE,
                                                const int* wk, const int* pst, const int* k2e,
-                                               const T* W, const T* V, int* q, int warp,
-                                               int lane) {
+                                               const T* W, const T* V, const T* Fo,
+                                               const uint32_t* ID, T wth, T wcr, int* q,
+                                               int warp, int lane) {
   constexpr int PS = kPiece;
   const int np = pst[NE];
   // warp 0 (which issues the bulk copies) claims from the start; warp w > 0
@@ -683,7 +701,7 @@ __device__ __forceinline__ void deposit_pieces(typename Num<T>::acc* ACC, int NA
     if (k < 0) break;
     const int b0 = wk[k] + (gi - pst[k]) * PS;
     const int b1 = min(b0 + PS, wk[k + 1]);
-    team_deposit<T, DIM, REL>(ACC, NA, AX, k2e[k], b0, b1, W, V, lane);
+    team_deposit<T, DIM, REL>(ACC, NA, AX, k2e[k], b0, b1, W, V, Fo, ID, wth, wcr, lane);
     int nx = 0;
     if (lane == 0) nx = atomicAdd(q, 1);
     gi = kWarps - 1 + __shfl_sync(0xffffffffu, nx, 0);
@@ -798,7 +816,7 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       // the last chunk's deposit
       if (dpar >= 0)
         deposit_pieces<T, DIM, REL>(ACC0 + dpar * 4 * NA, NA, AX, NE, wk, pst, k2e, oW, oV,
-                                    dq + ((ci - 1) & 1), warp, lane);
+                                    oF, oid, wth, wcr, dq + ((ci - 1) & 1), warp, lane);
       break;
     }
     const int i0 = desc[2 * b + 1].x, j0 = desc[2 * b + 1].y;
@@ -867,8 +885,8 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
     // ---- the previous chunk's deposit, after this chunk's push: warps that
     //      finished their push early take more of it
     if (dpar >= 0)
-      deposit_pieces<T, DIM, REL>(ACC0 + dpar * 4 * NA, NA, AX, NE, wk, pst, k2e, oW, oV,
-                                  dq + ((ci - 1) & 1), warp, lane);
+      deposit_pieces<T, DIM, REL>(ACC0 + dpar * 4 * NA, NA, AX, NE, wk, pst, k2e, oW, oV, oF,
+                                  oid, wth, wcr, dq + ((ci - 1) & 1), warp, lane);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(&d.ctr->status, kStatusTimeout);
@@ -927,12 +945,15 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       st4(oV + 4 * pos, svx[p], svy[p], svz[p],
           rel ? inv_gamma_u(svx[p], svy[p], svz[p], c2inv) : (T)1);
       // corner weights: wp * (gx * gy), corners (0,0) (1,0) (0,1) (1,1)
-      const T gx0 = (T)1 - fx;
-      if (DIM == 2) {
-        const T gy0 = (T)1 - fy;
-        st4(oW + 4 * pos, wp * (gx0 * gy0), wp * (fx * gy0), wp * (gx0 * fy), wp * (fx * fy));
-      } else {
-        st4(oW + 4 * pos, wp * gx0, wp * fx, (T)0, (T)0);
+      // (FP32: formed in the deposit)
+      if constexpr (sizeof(T) == 8) {
+        const T gx0 = (T)1 - fx;
+        if (DIM == 2) {
+          const T gy0 = (T)1 - fy;
+          st4(oW + 4 * pos, wp * (gx0 * gy0), wp * (fx * gy0), wp * (gx0 * fy), wp * (fx * fy));
+        } else {
+          st4(oW + 4 * pos, wp * gx0, wp * fx, (T)0, (T)0);
+        }
       }
     }
     __syncthreads();
@@ -1019,7 +1040,7 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
 // REL: compiled with the relativistic terms (used when c2inv > 0). TXC, TYC:
 // a tile shape compiled in (0: any shape, read from the geometry).
 template <typename T, int DIM, int CH, int NS, bool REL, int TXC = 0, int TYC = 0>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 4 : 2))
     k_push(DevPtrs<T> d, StepArgs a, PushConst<T> pc) {
   extern __shared__ __align__(128) unsigned char sm[];
   push_run<T, DIM, CH, NS, REL, TXC, TYC>(d, a.g, a.ph, pc, a.in, a.out, blockIdx.x, gridDim.x,
@@ -1032,7 +1053,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
 // device table, copied once into shared memory.
 // TXC: the tile width of every run the launch serves, compiled in (0: any)
 template <typename T, int DIM, int CH, int NS, bool REL, int TXC = 0>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 4 : 2))
     k_push_batch(const BatchRun<T>* __restrict__ runs, const int2* __restrict__ cta_map) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(16) BatchRun<T> R;

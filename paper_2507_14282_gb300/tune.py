@@ -4,7 +4,7 @@ sweeps on the GPU and caches the choice per (dimension, ppc, precision).
 A tile's shape sets the push's chunk fill, the share of particles that leave
 the tile (the deposit's halo cells and the mover list) and the number of
 persistent-CTA work items; the launch shape is the shared-memory chunk size
-with its pipeline depth (512 particles in three stages or 640 in two, FP32)
+with its pipeline depth (512 particles in three stages or 576 in two, FP32)
 and the number of persistent CTAs per SM. The tuner times the phases these
 set (push and movers) with the library's own CUDA-event phase timing, in two
 stages: the tile over a set of candidates at the library's default launch
@@ -57,7 +57,7 @@ def launch_shapes(precision: int) -> list:
     is the library's choice."""
     if precision == fs.FS_FP64:
         return [(0, 0), (512, 1)]
-    return [(0, 0), (512, 0), (640, 0), (640, 2), (512, 2)]
+    return [(0, 0), (512, 0), (576, 0), (576, 3), (512, 2)]
 
 
 class Autotuner:

@@ -142,8 +142,8 @@ def test_restore_state_rejects_null_arguments(fs):
 
 
 def test_query_accepts_push_launch_shapes(fs):
-    # FP32 takes 512- or 640-particle chunks, FP64 512; any CTA cap >= 0
-    for prec, chunk in ((fs.FS_FP32, 512), (fs.FS_FP32, 640), (fs.FS_FP64, 512)):
+    # FP32 takes 512- or 576-particle chunks, FP64 512; any CTA cap >= 0
+    for prec, chunk in ((fs.FS_FP32, 512), (fs.FS_FP32, 576), (fs.FS_FP64, 512)):
         s = fs.query(dim=2, nx=256, ny=64, ppc=64, precision=prec, push_chunk=chunk,
                      push_ctas_per_sm=2)
         assert s.device_bytes > 0

@@ -103,5 +103,5 @@ def test_tuner_2d_candidates_and_launch_shapes():
     assert counts == sorted(counts)
     # a box whose sides admit no shape in range gives none
     assert tune.tile_candidates_2d(7, 1, 1000) == []
-    assert (0, 0) in tune.launch_shapes(fs.FS_FP32) and (640, 0) in tune.launch_shapes(fs.FS_FP32)
+    assert (0, 0) in tune.launch_shapes(fs.FS_FP32) and (576, 0) in tune.launch_shapes(fs.FS_FP32)
     assert all(c in (0, 512) for c, _ in tune.launch_shapes(fs.FS_FP64))

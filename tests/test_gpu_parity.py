@@ -242,7 +242,7 @@ def test_fp64_push_launch_shapes_bit_exact(fs, chunk, ctas):
     assert_state_equal(gpu, ref, fs)
 
 
-@pytest.mark.parametrize("chunk,ctas", [(512, 0), (640, 2), (512, 2)])
+@pytest.mark.parametrize("chunk,ctas", [(512, 0), (576, 2), (512, 2)])
 def test_fp32_push_launch_shapes_within_tolerance(fs, chunk, ctas):
     cfg = W.scaled(W.CONFIG_2D_FP32, nx=64, ny=16)
     gpu = fs.FauxShock(precision=fs.FS_FP32, push_chunk=chunk, push_ctas_per_sm=ctas, **cfg)
