@@ -1052,8 +1052,9 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 4 : 2))
 // runs[run].ncta CTAs; the run's pointers, geometry and physics come from the
 // device table, copied once into shared memory.
 // TXC: the tile width of every run the launch serves, compiled in (0: any)
+// Three CTAs per SM in FP32 (at the four of k_push, its register cap spills).
 template <typename T, int DIM, int CH, int NS, bool REL, int TXC = 0>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 4 : 2))
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 3 : 2))
     k_push_batch(const BatchRun<T>* __restrict__ runs, const int2* __restrict__ cta_map) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(16) BatchRun<T> R;
