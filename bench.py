@@ -370,7 +370,7 @@ def ensemble(fs, torch, args, hbm, peak_src):
     with CUDA events, next to the same runs stepped one after another."""
     from paper_2507_14282_gb300 import tune
     from tests.workloads import config4_runs
-    tuner = tune.Autotuner()
+    tuner = tune.Autotuner(widths=fs.FsBatch.COMPILED_WIDTHS)
     t0 = time.perf_counter()
     runs = [tuner.tile(r) for r in config4_runs(64)]
     tune_s = time.perf_counter() - t0
@@ -614,7 +614,7 @@ def ncu_case(args):
     if args.ncu_case == "ensemble":
         from paper_2507_14282_gb300 import tune
         from tests.workloads import config4_runs
-        runs = [tune.Autotuner().tile(r) for r in config4_runs(64)]
+        runs = [tune.Autotuner(widths=fs.FsBatch.COMPILED_WIDTHS).tile(r) for r in config4_runs(64)]
         sims = [fs.FauxShock(**r) for r in runs]
         b = fs.FsBatch(sims)
         b.step(3)

@@ -621,6 +621,30 @@ static __global__ void k_inject_commit(Counters* ctr, const int* rowoff, int ny)
 // wall half-volume correction (x2 at i = 0 and i = nx in the faux-shock box),
 // the density floor and u = J / n.
 // ------------------------------------------------------------------------
+// The node's moments from its sums s (n, Jx, Jy, Jz); clears its far sums.
+template <typename T, int DIM>
+__device__ __forceinline__ void moments_finish(const DevPtrs<T>& d, const Geo& g, const Phys& ph,
+                                               int q, int i, const typename Num<T>::acc (&s)[4]) {
+  using A = typename Num<T>::acc;
+  const int nn = g.nxn * g.ny;
+  T nt = acc_value(s[0]), jxt = acc_value(s[1]), jyt = acc_value(s[2]), jzt = acc_value(s[3]);
+  if (g.bc_x == FS_BC_FAUXSHOCK && (i == 0 || i == g.nx)) {
+    nt = nt * (T)2; jxt = jxt * (T)2; jyt = jyt * (T)2; jzt = jzt * (T)2;
+  }
+  d.J[q] = jxt;
+  d.J[(size_t)nn + q] = jyt;
+  d.J[(size_t)2 * nn + q] = jzt;
+  const T nf = (T)ph.n_floor;
+  if (nt < nf) nt = nf;
+  d.n[q] = nt;
+  d.u[q] = jxt / nt;
+  d.u[(size_t)nn + q] = jyt / nt;
+  d.u[(size_t)2 * nn + q] = jzt / nt;
+  A* farw = (A*)d.far;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) farw[(size_t)c * nn + q] = (A)0;
+}
+
 template <typename T, int DIM>
 __device__ __forceinline__ void moments_body(const DevPtrs<T>& d, const Geo& g, const Phys& ph,
                                              int blk, int nblk) {
@@ -691,28 +715,70 @@ __device__ __forceinline__ void moments_body(const DevPtrs<T>& d, const Geo& g, 
         }
       }
     }
-    T nt = acc_value(s[0]), jxt = acc_value(s[1]), jyt = acc_value(s[2]), jzt = acc_value(s[3]);
-    if (g.bc_x == FS_BC_FAUXSHOCK && (i == 0 || i == g.nx)) {
-      nt = nt * (T)2; jxt = jxt * (T)2; jyt = jyt * (T)2; jzt = jzt * (T)2;
-    }
-    d.J[q] = jxt;
-    d.J[(size_t)nn + q] = jyt;
-    d.J[(size_t)2 * nn + q] = jzt;
-    const T nf = (T)ph.n_floor;
-    if (nt < nf) nt = nf;
-    d.n[q] = nt;
-    d.u[q] = jxt / nt;
-    d.u[(size_t)nn + q] = jyt / nt;
-    d.u[(size_t)2 * nn + q] = jzt / nt;
-    A* farw = (A*)d.far;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) farw[(size_t)c * nn + q] = (A)0;
+    moments_finish<T, DIM>(d, g, ph, q, i, s);
   }
 }
 
 template <typename T, int DIM>
 __global__ void k_moments(DevPtrs<T> d, Geo g, Phys ph) {
   moments_body<T, DIM>(d, g, ph, blockIdx.x, gridDim.x);
+}
+
+// The same sums for a 2D box with x walls whose tile shape TXC x TYC is
+// compiled in (and whose rows hold more than one tile's accumulator rows and
+// more tile rows than cover a node): the candidate tiles of a node are a
+// fixed, small set (MX columns by MY rows), so every load is issued without a
+// data-dependent loop; rows are taken in increasing wrapped order, columns
+// in increasing order, as in moments_body.
+template <typename T, int TXC, int TYC>
+__global__ void k_moments_ct(DevPtrs<T> d, Geo g, Phys ph) {
+  using A = typename Num<T>::acc;
+  constexpr int AX = TXC + 3, AY = TYC + 3, NA = AX * AY;
+  constexpr int MX = (AX + TXC - 1) / TXC, MY = (AY + TYC - 1) / TYC;
+  const int nn = g.nxn * g.ny;
+  const A* far = (const A*)d.far;
+  const A* partial = (const A*)d.partial;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += gridDim.x * blockDim.x) {
+    const int i = q % g.nxn, j = q / g.nxn;
+    // candidate rows: ty with 0 <= j - (ty TYC - 1) < AY, wrapped, ascending
+    int tyw[MY], ayv[MY];
+    const int tyh = (j + 1) / TYC;
+#pragma unroll
+    for (int u = 0; u < MY; ++u) {
+      const int ty = tyh - (MY - 1) + u;
+      const int ay = j - (ty * TYC - 1);
+      const bool ok = ay >= 0 && ay < AY;
+      tyw[u] = ok ? (ty < 0 ? ty + g.nty : (ty >= g.nty ? ty - g.nty : ty)) : 0x7fffffff;
+      ayv[u] = ay;
+    }
+#pragma unroll
+    for (int a = 0; a < MY; ++a)
+#pragma unroll
+      for (int b = a + 1; b < MY; ++b)
+        if (tyw[b] < tyw[a]) {
+          const int t0 = tyw[a], t1 = ayv[a];
+          tyw[a] = tyw[b]; ayv[a] = ayv[b];
+          tyw[b] = t0; ayv[b] = t1;
+        }
+    A s[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c] = far[(size_t)c * nn + q];
+    const int txh = (i + 1) / TXC;
+#pragma unroll
+    for (int u = 0; u < MY; ++u) {
+      if (tyw[u] == 0x7fffffff) continue;
+#pragma unroll
+      for (int x = 0; x < MX; ++x) {
+        const int tx = txh - (MX - 1) + x;
+        const int ax = i - (tx * TXC - 1);
+        if (tx < 0 || tx >= g.ntx || ax < 0 || ax >= AX) continue;
+        const A* part = partial + (size_t)(tyw[u] * g.ntx + tx) * 4 * NA + ax + ayv[u] * AX;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s[c] += part[c * NA];
+      }
+    }
+    moments_finish<T, 2>(d, g, ph, q, i, s);
+  }
 }
 
 // ------------------------------------------------------------------------

@@ -131,10 +131,19 @@ struct OpsImpl {
 
   static cudaError_t moments(Sim* s) {
     const long long nn = (long long)s->g.nxn * s->g.ny;
-    if (s->g.dim == 1)
-      k_moments<T, 1><<<grid_for(nn), kBlock, 0, s->stream>>>(P(s), s->g, s->ph);
+    const Geo& g = s->g;
+    // the tile shapes the library picks for the 2D workloads (FP32 4 x 2 at
+    // 64 ppc, FP64 8 x 4 at 16 ppc), compiled in, for boxes with x walls that
+    // are more than a tile's accumulator high and more than three tile rows
+    const bool ct = g.dim == 2 && g.bc_x != FS_BC_PERIODIC && g.ny >= 2 * (g.TY + 3) && g.nty > 3;
+    if (g.dim == 1)
+      k_moments<T, 1><<<grid_for(nn), kBlock, 0, s->stream>>>(P(s), g, s->ph);
+    else if (ct && g.TX == 4 && g.TY == 2)
+      k_moments_ct<T, 4, 2><<<grid_for(nn), kBlock, 0, s->stream>>>(P(s), g, s->ph);
+    else if (ct && g.TX == 8 && g.TY == 4)
+      k_moments_ct<T, 8, 4><<<grid_for(nn), kBlock, 0, s->stream>>>(P(s), g, s->ph);
     else
-      k_moments<T, 2><<<grid_for(nn), kBlock, 0, s->stream>>>(P(s), s->g, s->ph);
+      k_moments<T, 2><<<grid_for(nn), kBlock, 0, s->stream>>>(P(s), g, s->ph);
     return cudaGetLastError();
   }
 

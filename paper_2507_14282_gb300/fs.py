@@ -404,10 +404,14 @@ def batch_plan(n_particles, ntiles, ncta_max: int) -> list:
 
 class FsBatch:
     """Independent FauxShock runs stepped together (fs_batch_*): one push
-    launch over every run's CTA group per step, the rest of each run's step in
+    launch per class of runs over every run's CTA group per step (1D FP32 runs
+    of a tile width in COMPILED_WIDTHS form a class with that width compiled
+    in), the rest of the step batched too (1D runs with x walls) or in
     parallel branches of one CUDA graph. The runs must share precision,
     dimension and stream; they are not stepped on their own while the batch
     lives."""
+
+    COMPILED_WIDTHS = (4, 8, 16)
 
     def __init__(self, sims):
         import torch

@@ -39,6 +39,16 @@ def tile_for(nx: int, ppc: int, target: int) -> int:
     return min(ds, key=lambda c: (abs(c * ppc - target), c))
 
 
+def targets_1d(nx: int, ppc: int, widths=None) -> list:
+    """1D targets (mean particles per tile) tried on an nx-cell box: all of
+    TARGETS, or, with widths, those whose tile width is one of them (all if
+    none is)."""
+    if not widths:
+        return list(TARGETS)
+    within = [t for t in TARGETS if tile_for(nx, ppc, t) in widths]
+    return within or list(TARGETS)
+
+
 def tile_candidates_2d(nx: int, ny: int, ppc: int, lo: int = 128, hi: int = 1024) -> list:
     """2D tile shapes (tx, ty) with tx >= 2 dividing nx (at most 64), ty
     dividing ny (at most 32) and a mean particle count in [lo, hi], ordered by
@@ -61,21 +71,27 @@ def launch_shapes(precision: int) -> list:
 
 
 class Autotuner:
+    """widths: 1D tile widths the choice is limited to where a candidate gives
+    one (e.g. FsBatch.COMPILED_WIDTHS for runs that are stepped in a batch,
+    whose push has those widths compiled in; the standalone probe timing does
+    not see that)."""
+
     def __init__(self, cache_path: str | None = None, probe_particles: int = 1 << 22,
-                 warm: int = 3, steps: int = 8, shapes: bool = True):
+                 warm: int = 3, steps: int = 16, shapes: bool = True, widths=None):
         self.cache_path = cache_path
         self.probe_particles = probe_particles
         self.warm, self.steps = warm, steps
         self.shapes = shapes  # also tune the launch shape
+        self.widths = tuple(widths) if widths else None
         self.cache = {}
         if cache_path and os.path.exists(cache_path):
             with open(cache_path) as f:
                 self.cache = json.load(f)
         self.log = []
 
-    @staticmethod
-    def key(dim: int, ppc: int, precision: int) -> str:
-        return f"dim{dim}-ppc{ppc}-{'fp64' if precision == fs.FS_FP64 else 'fp32'}"
+    def key(self, dim: int, ppc: int, precision: int) -> str:
+        k = f"dim{dim}-ppc{ppc}-{'fp64' if precision == fs.FS_FP64 else 'fp32'}"
+        return k + (f"-w{'.'.join(map(str, self.widths))}" if self.widths and dim == 1 else "")
 
     def _time(self, params: dict) -> float:
         """ms per step of the phases the tile and launch shapes set (push and
@@ -132,8 +148,9 @@ class Autotuner:
             return hit
         probe = self._probe(base)
         if dim == 1:
+            targets = targets_1d(probe["nx"], probe["ppc"], self.widths)
             cands = [({"target": t}, dict(probe, tile_x=tile_for(probe["nx"], probe["ppc"], t),
-                                          tile_y=1)) for t in TARGETS]
+                                          tile_y=1)) for t in targets]
         else:
             shapes = tile_candidates_2d(probe["nx"], probe["ny"], probe["ppc"]) or [(0, 0)]
             cands = [({"tile": [tx, ty]}, dict(probe, tile_x=tx, tile_y=ty))

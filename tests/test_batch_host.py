@@ -105,3 +105,21 @@ def test_tuner_2d_candidates_and_launch_shapes():
     assert tune.tile_candidates_2d(7, 1, 1000) == []
     assert (0, 0) in tune.launch_shapes(fs.FS_FP32) and (576, 0) in tune.launch_shapes(fs.FS_FP32)
     assert all(c in (0, 512) for c, _ in tune.launch_shapes(fs.FS_FP64))
+
+
+def test_tuner_limits_batch_runs_to_compiled_widths():
+    from paper_2507_14282_gb300 import tune, fs
+    w = fs.FsBatch.COMPILED_WIDTHS
+    # 32 ppc on 4096 cells: targets 128 / 256 / 512 give widths 4 / 8 / 16,
+    # 1024 gives 32, which no batched push has compiled in
+    assert tune.targets_1d(4096, 32, None) == list(tune.TARGETS)
+    assert tune.targets_1d(4096, 32, w) == [128, 256, 512]
+    assert tune.targets_1d(4096, 256, w) == [1024]
+    for t in tune.targets_1d(4096, 64, w):
+        assert tune.tile_for(4096, 64, t) in w
+    # no candidate within the widths: all of them
+    assert tune.targets_1d(4099, 64, w) == list(tune.TARGETS)
+    a, b = tune.Autotuner(), tune.Autotuner(widths=w)
+    assert a.key(1, 32, fs.FS_FP32) == "dim1-ppc32-fp32"
+    assert b.key(1, 32, fs.FS_FP32) == "dim1-ppc32-fp32-w4.8.16"
+    assert b.key(2, 64, fs.FS_FP32) == a.key(2, 64, fs.FS_FP32)
