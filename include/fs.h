@@ -352,9 +352,9 @@ int fs_field_advance_noalloc(const fs_params* p, const double* B_in,
    precision and dimension, created on one CUDA stream -- with one push
    launch per step for each class of runs (1D FP32 runs of tile width 4, 8
    or 16 cells each form a class with that width compiled in; all other runs
-   one class): each run gets a group of CTAs about proportional to its
-   particles (a (run, tile) work list, each run's pointers, geometry and
-   physics read from a device table). When every run
+   one class; the classes' launches run side by side): each run gets a group
+   of CTAs about proportional to its particles (a (run, tile) work list, each
+   run's pointers, geometry and physics read from a device table). When every run
    is 1D with x walls (the one-launch field advance), the rest of the step --
    movers, injection, moments, field advance, step counter -- is one launch
    per kernel over all runs too (each block works for one run, found from

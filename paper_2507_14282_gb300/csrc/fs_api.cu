@@ -1213,10 +1213,29 @@ namespace {
 cudaError_t batch_enqueue(fs_batch* b, int p, cudaStream_t st) {
   const int nr = (int)b->runs.size();
   cudaError_t e = cudaSuccess;
-  for (const auto& c : b->classes) {
-    e = b->ops->push_batch(b->dim, b->rel, b->chunk, c.txc, b->table + (size_t)p * nr * b->rec,
-                           b->map + c.map0, c.ncta, c.smem, st);
-    if (e != cudaSuccess) return e;
+  const int nc = (int)b->classes.size();
+  if (nc > 1 && (int)b->branch.size() >= nc) {
+    // the classes' push launches side by side (one branch each), so that one
+    // launch's last CTAs overlap the others'
+    if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
+    for (int k = 0; k < nc; ++k) {
+      const auto& c = b->classes[k];
+      cudaStream_t bs = b->branch[k];
+      if ((e = cudaStreamWaitEvent(bs, b->fork, 0)) != cudaSuccess) return e;
+      e = b->ops->push_batch(b->dim, b->rel, b->chunk, c.txc,
+                             b->table + (size_t)p * nr * b->rec, b->map + c.map0, c.ncta, c.smem,
+                             bs);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaEventRecord(b->join[k], bs)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(st, b->join[k], 0)) != cudaSuccess) return e;
+    }
+  } else {
+    for (const auto& c : b->classes) {
+      e = b->ops->push_batch(b->dim, b->rel, b->chunk, c.txc,
+                             b->table + (size_t)p * nr * b->rec, b->map + c.map0, c.ncta, c.smem,
+                             st);
+      if (e != cudaSuccess) return e;
+    }
   }
   if (b->tail_batched)
     return b->ops->batch_rest(b->table + (size_t)p * nr * b->rec, b->pre, nr, b->nblk,
