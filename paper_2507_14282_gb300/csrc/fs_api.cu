@@ -331,6 +331,11 @@ int build_graphs(Sim* s) {
   if (!s->cap_stream &&
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return FS_ECUDA;
+  if (!s->side && cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess)
+    return FS_ECUDA;
+  if ((!s->ev_fork && cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess) ||
+      (!s->ev_join && cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    return FS_ECUDA;
   // the captured work must follow everything already queued on the caller's stream
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return FS_ECUDA;
   cudaStream_t user = s->stream;
@@ -367,6 +372,18 @@ void release_graphs(Sim* s) {
   if (s->cap_stream) {
     cudaStreamDestroy(s->cap_stream);
     s->cap_stream = nullptr;
+  }
+  if (s->side) {
+    cudaStreamDestroy(s->side);
+    s->side = nullptr;
+  }
+  if (s->ev_fork) {
+    cudaEventDestroy(s->ev_fork);
+    s->ev_fork = nullptr;
+  }
+  if (s->ev_join) {
+    cudaEventDestroy(s->ev_join);
+    s->ev_join = nullptr;
   }
   s->graphs_ready = false;
 }
@@ -1239,7 +1256,7 @@ cudaError_t batch_enqueue(fs_batch* b, int p, cudaStream_t st) {
   }
   if (b->tail_batched)
     return b->ops->batch_rest(b->table + (size_t)p * nr * b->rec, b->pre, nr, b->nblk,
-                              b->n_sub_max, st);
+                              b->n_sub_max, st, b->branch[0], b->fork, b->join[0]);
   if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
   const int K = (int)b->branch.size();
   for (int k = 0; k < K; ++k)

@@ -176,8 +176,11 @@ struct Ops {
   // the rest of a batched step in one launch per kernel over every run (1D
   // runs with x walls): pre holds three block prefixes over the runs (movers,
   // moments, field tiles; nruns + 1 entries each), nblk their totals
+  // (the movers on stream side, between events fork and join, beside the
+  // injection, moments and field advance on st)
   cudaError_t (*batch_rest)(const void* runs, const int* pre, int nruns, const int* nblk,
-                            int n_sub_max, cudaStream_t st);
+                            int n_sub_max, cudaStream_t st, cudaStream_t side,
+                            cudaEvent_t fork, cudaEvent_t join);
   cudaError_t (*fields)(Sim*);
   cudaError_t (*insert_staged)(Sim*, int buf, int n, bool from_movers);
   cudaError_t (*diag)(Sim*, int buf);
@@ -215,6 +218,10 @@ struct Sim {
   // one captured step per ping-pong parity (replayed by fs_step)
   cudaGraphExec_t graph[2];
   cudaStream_t cap_stream;
+  // a second stream for the captured step: the movers run on it beside the
+  // injection, moments and field advance (fork / join events)
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
   bool graphs_ready;
   int steps_direct;    // steps launched directly (graphs are captured after one)
   template <typename T>

@@ -290,10 +290,24 @@ struct OpsImpl {
       if (ev) cudaEventRecord(ev[k], s->stream);
     };
     const int mg = std::min((s->g.ntiles + 7) / 8, 152 * 16);
+    // without phase events, the movers (buckets) run on the side stream
+    // beside the injection, moments and field advance, which read no bucket
+    const bool split = !ev && s->side && s->ev_fork && s->ev_join;
+    cudaStream_t mst = s->stream;
+    if (split) {
+      cudaError_t e0 = cudaEventRecord(s->ev_fork, s->stream);
+      if (e0 == cudaSuccess) e0 = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+      if (e0 != cudaSuccess) return e0;
+      mst = s->side;
+    }
     if (s->g.dim == 1)
-      k_movers<T, 1><<<mg, kBlock, 0, s->stream>>>(d, s->g, out);
+      k_movers<T, 1><<<mg, kBlock, 0, mst>>>(d, s->g, out);
     else
-      k_movers<T, 2><<<mg, kBlock, 0, s->stream>>>(d, s->g, out);
+      k_movers<T, 2><<<mg, kBlock, 0, mst>>>(d, s->g, out);
+    if (split) {
+      const cudaError_t e0 = cudaEventRecord(s->ev_join, s->side);
+      if (e0 != cudaSuccess) return e0;
+    }
     mark(2);
     if (s->g.bc_x == FS_BC_FAUXSHOCK && (s->ph.inject_thermal || s->ph.cr_enable)) {
       int* rowcnt = d.inj;
@@ -314,6 +328,10 @@ struct OpsImpl {
     if (e != cudaSuccess) return e;
     mark(4);
     e = fields(s);
+    if (split) {
+      const cudaError_t e0 = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+      if (e0 != cudaSuccess) return e0;
+    }
     k_step_end<<<1, 32, 0, s->stream>>>(d.ctr);
     mark(5);
     return e;
@@ -423,7 +441,8 @@ struct OpsImpl {
 
   // the rest of a batched step over every run (all 1D with x walls)
   static cudaError_t batch_rest(const void* runs, const int* pre, int nruns, const int* nblk,
-                                int n_sub_max, cudaStream_t st) {
+                                int n_sub_max, cudaStream_t st, cudaStream_t side,
+                                cudaEvent_t fork, cudaEvent_t join) {
     const BatchRun<T>* r = (const BatchRun<T>*)runs;
     const size_t fsm = field1_smem<T>(n_sub_max);
     static std::atomic<size_t> attr(0);  // the largest size enabled so far
@@ -436,11 +455,19 @@ struct OpsImpl {
       }
     }
     const int n1 = nruns + 1;
-    k_movers_batch<T, 1><<<nblk[0], kBlock, 0, st>>>(r, pre, nruns);
+    // the movers (buckets) beside the injection, moments and field advance,
+    // which read no bucket: the injection appends to the buckets with its own
+    // slot atomics, the moments read the deposit partials and far sums
+    cudaError_t e;
+    if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
+    k_movers_batch<T, 1><<<nblk[0], kBlock, 0, side>>>(r, pre, nruns);
+    if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
     k_inject_batch<T, 1><<<nruns, kBlock, 0, st>>>(r, nruns);
     k_moments_batch<T, 1><<<nblk[1], kBlock, 0, st>>>(r, pre + n1, nruns);
     k_field1_batch<T><<<nblk[2], kF1Threads, fsm, st>>>(r, pre + 2 * n1, nruns);
     k_copyB_batch<T><<<nblk[2], kF1Threads, 0, st>>>(r, pre + 2 * n1, nruns);
+    if ((e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return e;
     k_step_end_batch<T><<<(nruns + 63) / 64, 64, 0, st>>>(r, nruns);
     return cudaGetLastError();
   }
