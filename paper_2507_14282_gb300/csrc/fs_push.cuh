@@ -592,13 +592,17 @@ __device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T
                                          const T* V, const T* Fo, const uint32_t* ID,
                                          T wth, T wcr, int i, int c) {
   T cw;
+  T v[4];
+  ld4(V + 4 * i, v);
   if constexpr (sizeof(T) == 4) {  // corner weight wp * (gx * gy) from the offsets
     T f[2];
     ld2(Fo + 2 * i, f);
-    const T wp = (ID[i] & kIdCR) ? wcr : wth;
-    const T gx = (c & 1) ? f[0] : (T)1 - f[0];
+    // the particle weight: in V's fourth slot without relativistic terms
+    const T wp = REL ? ((ID[i] & kIdCR) ? wcr : wth) : v[3];
+    // gx = fx or 1 - fx by one fused multiply-add (the same rounded value)
+    const T gx = fmaT((c & 1) ? (T)1 : (T)-1, f[0], (c & 1) ? (T)0 : (T)1);
     if (DIM == 2) {
-      const T gy = (c >> 1) ? f[1] : (T)1 - f[1];
+      const T gy = fmaT((c >> 1) ? (T)1 : (T)-1, f[1], (c >> 1) ? (T)0 : (T)1);
       cw = wp * (gx * gy);
     } else {
       cw = wp * gx;
@@ -606,8 +610,6 @@ __device__ __forceinline__ void team_add(typename Num<T>::acc (&acc)[4], const T
   } else {
     cw = W[4 * i + c];
   }
-  T v[4];
-  ld4(V + 4 * i, v);
   if (REL) {  // relativistic ions: V holds u and 1/gamma
     v[0] = v[0] * v[3];
     v[1] = v[1] * v[3];
@@ -942,8 +944,11 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       oid[pos] = id;
       st2(oF + 2 * pos, fx, fy);
       // {u} of the state, and 1/gamma (the current uses v = u / gamma)
+      // (FP32 without relativistic terms: the particle weight, which the
+      // deposit lanes use to form their corner weights)
       st4(oV + 4 * pos, svx[p], svy[p], svz[p],
-          rel ? inv_gamma_u(svx[p], svy[p], svz[p], c2inv) : (T)1);
+          (sizeof(T) == 4 && !REL) ? wp
+                                   : (rel ? inv_gamma_u(svx[p], svy[p], svz[p], c2inv) : (T)1));
       // corner weights: wp * (gx * gy), corners (0,0) (1,0) (0,1) (1,1)
       // (FP32: formed in the deposit)
       if constexpr (sizeof(T) == 8) {
