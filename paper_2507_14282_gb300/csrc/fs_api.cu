@@ -336,6 +336,11 @@ int build_graphs(Sim* s) {
   if ((!s->ev_fork && cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess) ||
       (!s->ev_join && cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess))
     return FS_ECUDA;
+  if (!s->side2 && cudaStreamCreateWithFlags(&s->side2, cudaStreamNonBlocking) != cudaSuccess)
+    return FS_ECUDA;
+  if ((!s->ev_fork2 && cudaEventCreateWithFlags(&s->ev_fork2, cudaEventDisableTiming) != cudaSuccess) ||
+      (!s->ev_join2 && cudaEventCreateWithFlags(&s->ev_join2, cudaEventDisableTiming) != cudaSuccess))
+    return FS_ECUDA;
   // the captured work must follow everything already queued on the caller's stream
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return FS_ECUDA;
   cudaStream_t user = s->stream;
@@ -384,6 +389,18 @@ void release_graphs(Sim* s) {
   if (s->ev_join) {
     cudaEventDestroy(s->ev_join);
     s->ev_join = nullptr;
+  }
+  if (s->side2) {
+    cudaStreamDestroy(s->side2);
+    s->side2 = nullptr;
+  }
+  if (s->ev_fork2) {
+    cudaEventDestroy(s->ev_fork2);
+    s->ev_fork2 = nullptr;
+  }
+  if (s->ev_join2) {
+    cudaEventDestroy(s->ev_join2);
+    s->ev_join2 = nullptr;
   }
   s->graphs_ready = false;
 }

@@ -222,6 +222,10 @@ struct Sim {
   // injection, moments and field advance (fork / join events)
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
+  // a third stream: the FP32 2D field substep's wall tile columns beside its
+  // interior launch
+  cudaStream_t side2;
+  cudaEvent_t ev_fork2, ev_join2;
   bool graphs_ready;
   int steps_direct;    // steps launched directly (graphs are captured after one)
   template <typename T>

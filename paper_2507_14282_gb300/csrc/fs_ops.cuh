@@ -203,15 +203,32 @@ struct OpsImpl {
       const int fin = (sub + 1 == s->p.n_sub) ? 1 : 0;
       if (split) {
         const dim3 gi(gx - 2, gy), ge(2, gy);
+        // the two wall columns (few CTAs) on the third stream beside the
+        // interior launch, joined before the next substep
+        const bool side = s->side2 && s->ev_fork2 && s->ev_join2;
+        cudaStream_t es = s->stream;
+        if (side) {
+          cudaError_t e0 = cudaEventRecord(s->ev_fork2, s->stream);
+          if (e0 == cudaSuccess) e0 = cudaStreamWaitEvent(s->side2, s->ev_fork2, 0);
+          if (e0 != cudaSuccess) return e0;
+          es = s->side2;
+        }
+        k_field_substep2<T, -1><<<ge, kBlock, smem, es>>>(src, dst, d.n, d.u, d.E, d.Bb, d.G,
+                                                          s->g, s->ph, fc, fin, 0, gx - 1);
+        if (side) {
+          const cudaError_t e0 = cudaEventRecord(s->ev_join2, s->side2);
+          if (e0 != cudaSuccess) return e0;
+        }
         if (fin)
           k_field_substep2<T, 1><<<gi, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
                                                                 d.G, s->g, s->ph, fc, fin, 1, 0);
         else
           k_field_substep2<T, 0><<<gi, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
                                                                 d.G, s->g, s->ph, fc, fin, 1, 0);
-        k_field_substep2<T, -1><<<ge, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
-                                                               d.G, s->g, s->ph, fc, fin, 0,
-                                                               gx - 1);
+        if (side) {
+          const cudaError_t e0 = cudaStreamWaitEvent(s->stream, s->ev_join2, 0);
+          if (e0 != cudaSuccess) return e0;
+        }
       } else {
         const dim3 grid(gx, gy);
         // every column: the general form

@@ -843,8 +843,13 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
     int* kc = kc0 + (ci & 1) * NK;
     A* ACC = ACC0 + tpar * 4 * NA;
 
-    // ---- push in place, key, rank within the key
+    // ---- push, key, rank within the key. FP32: the pushed state written back
+    //      in place; FP64 (128 registers at two CTAs per SM): kept in
+    //      registers until the key-order copy
     int ky[PPT], rk[PPT];
+    int rc_[PPT];
+    uint32_t rid_[PPT];
+    T rfx_[PPT], rfy_[PPT], rvx_[PPT], rvy_[PPT], rvz_[PPT];
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
       const int p = tid + r * kBlock;
@@ -867,13 +872,23 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
           deposit_far<T, DIM>(d, g, cell & 0xFFFF, cell >> 16, fx, fy,
                               (id & kIdCR) ? wcr : wth, dvx, dvy, dvz);
         }
-        sc[p] = cell;
-        sx[p] = fx;
-        if (DIM == 2) sy[p] = fy;
-        svx[p] = vx;
-        svy[p] = vy;
-        svz[p] = vz;
-        sid[p] = id;
+        if constexpr (sizeof(T) == 8) {
+          rc_[r] = cell;
+          rfx_[r] = fx;
+          rfy_[r] = fy;
+          rvx_[r] = vx;
+          rvy_[r] = vy;
+          rvz_[r] = vz;
+          rid_[r] = id;
+        } else {
+          sc[p] = cell;
+          sx[p] = fx;
+          if (DIM == 2) sy[p] = fy;
+          svx[p] = vx;
+          svy[p] = vy;
+          svz[p] = vz;
+          sid[p] = id;
+        }
         ky[r] = key;
       }
       // lanes with equal keys take consecutive ranks after one atomic
@@ -937,18 +952,22 @@ __device__ __forceinline__ void push_run(const DevPtrs<T>& d, const Geo& g, cons
       if (key > NE) continue;
       const int p = tid + r * kBlock;
       const int pos = wk[key] + rk[r];
-      const uint32_t id = sid[p];
-      const T fx = sx[p], fy = (DIM == 2) ? sy[p] : (T)0;
+      constexpr bool inreg = sizeof(T) == 8;
+      const uint32_t id = inreg ? rid_[r] : sid[p];
+      const T fx = inreg ? rfx_[r] : sx[p];
+      const T fy = (DIM == 2) ? (inreg ? rfy_[r] : sy[p]) : (T)0;
+      const T ux = inreg ? rvx_[r] : svx[p];
+      const T uy = inreg ? rvy_[r] : svy[p];
+      const T uz = inreg ? rvz_[r] : svz[p];
       const T wp = (id & kIdCR) ? wcr : wth;
-      oc[pos] = sc[p];
+      oc[pos] = inreg ? rc_[r] : sc[p];
       oid[pos] = id;
       st2(oF + 2 * pos, fx, fy);
       // {u} of the state, and 1/gamma (the current uses v = u / gamma)
       // (FP32 without relativistic terms: the particle weight, which the
       // deposit lanes use to form their corner weights)
-      st4(oV + 4 * pos, svx[p], svy[p], svz[p],
-          (sizeof(T) == 4 && !REL) ? wp
-                                   : (rel ? inv_gamma_u(svx[p], svy[p], svz[p], c2inv) : (T)1));
+      st4(oV + 4 * pos, ux, uy, uz,
+          (sizeof(T) == 4 && !REL) ? wp : (rel ? inv_gamma_u(ux, uy, uz, c2inv) : (T)1));
       // corner weights: wp * (gx * gy), corners (0,0) (1,0) (0,1) (1,1)
       // (FP32: formed in the deposit)
       if constexpr (sizeof(T) == 8) {
