@@ -134,6 +134,24 @@ def test_fp64_2d_bit_exact_several_tiles(fs, tile):
     assert_state_equal(gpu, ref, fs)
 
 
+# The moment finish has the library's tile shapes compiled in for boxes more
+# than a tile's accumulator high with more than three tile rows; these boxes
+# sit on both sides of that rule (4x2: ny 10 compiled, 8 general; 8x4: ny 16
+# compiled, 12 general), with the rows' periodic wrap in every case.
+@pytest.mark.parametrize("nx,ny,tile", [(32, 10, (4, 2)), (32, 8, (4, 2)),
+                                        (64, 16, (8, 4)), (64, 12, (8, 4))])
+def test_fp64_2d_moment_finish_bit_exact_at_the_compiled_shape_rule(fs, nx, ny, tile):
+    cfg = W.scaled(W.CONFIG_2D, nx=nx, ny=ny, ppc=8, mach_a=10.0, theta_bn_deg=20.0,
+                   tile_x=tile[0], tile_y=tile[1])
+    gpu = fs.FauxShock(precision=fs.FS_FP64, **cfg)
+    ocfg = {k: v for k, v in cfg.items() if k not in ("tile_x", "tile_y")}
+    ref = O.Oracle(**ocfg)
+    for n in (1, 6):
+        gpu.step(n)
+        ref.step(n)
+        assert_state_equal(gpu, ref, fs)
+
+
 def test_fp64_2d_many_tiles_per_cta_bit_exact(fs):
     # 2x2-cell tiles on 256 x 128 cells: 8192 tiles, several per persistent CTA
     cfg = W.scaled(W.CONFIG_2D, nx=256, ny=128, ppc=8, mach_a=15.0, theta_bn_deg=10.0,
