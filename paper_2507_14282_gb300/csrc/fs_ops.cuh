@@ -219,12 +219,17 @@ struct OpsImpl {
           const cudaError_t e0 = cudaEventRecord(s->ev_join2, s->side2);
           if (e0 != cudaSuccess) return e0;
         }
+        // the substeps before the last need a halo of kFH - 1 cells only: their
+        // smaller shared memory lets four CTAs share an SM
+        constexpr size_t smem0 =
+            sizeof(T) * (9 * (size_t)(kFTX + 2 * (kFH - 1)) * (kFTY + 2 * (kFH - 1)) +
+                         4 * (size_t)(kFTX + 2 * (kFH - 1) + 1) * (kFTY + 2 * (kFH - 1) + 1));
         if (fin)
           k_field_substep2<T, 1><<<gi, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
                                                                 d.G, s->g, s->ph, fc, fin, 1, 0);
         else
-          k_field_substep2<T, 0><<<gi, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
-                                                                d.G, s->g, s->ph, fc, fin, 1, 0);
+          k_field_substep2<T, 0><<<gi, kBlock, smem0, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
+                                                                 d.G, s->g, s->ph, fc, fin, 1, 0);
         if (side) {
           const cudaError_t e0 = cudaStreamWaitEvent(s->stream, s->ev_join2, 0);
           if (e0 != cudaSuccess) return e0;
