@@ -1202,9 +1202,11 @@ __global__ void __launch_bounds__(kF1Threads)
 constexpr int kFTX = 32, kFTY = 16, kFH = 5;  // owned cells; halo of the last substep
 constexpr int kFLX = kFTX + 2 * kFH, kFLY = kFTY + 2 * kFH;
 constexpr int kFNPT = ((kFLX + 1) * (kFLY + 1) + kBlock - 1) / kBlock;  // nodes per thread
+// (the density, needed only for the density terms at the start, shares the
+// first E plane)
 template <typename T>
 constexpr size_t field_tile_smem() {
-  return sizeof(T) * (9 * (size_t)kFLX * kFLY + 4 * (size_t)(kFLX + 1) * (kFLY + 1));
+  return sizeof(T) * (9 * (size_t)kFLX * kFLY + 3 * (size_t)(kFLX + 1) * (kFLY + 1));
 }
 
 // Walks the elements k = t0, t0 + kBlock, ... of an nx-by-ny local array,
@@ -1232,7 +1234,7 @@ struct TileWalk {
 // tile launch (a full tile whose halo lies inside the box: its local sizes
 // are constants); bx0: the first tile column of the launch (blockIdx.x + bx0)
 template <typename T, int FINC>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, (FINC >= 0 ? 4 : 1))
     k_field_substep2(const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ nN,
                      const T* __restrict__ uN, T* __restrict__ Eo, T* __restrict__ Bbo,
                      T* __restrict__ G, Geo g, Phys ph, FieldConst<T> fc, int fin_arg, int bx0,
@@ -1256,7 +1258,7 @@ __global__ void __launch_bounds__(kBlock)
   T* sBs = sB + 3 * NC;
   T* sK = sBs + 3 * NC;
   T* sE = sK + 3 * NC;  // [3][NN]
-  T* sn = sE + 3 * NN;  // [NN]
+  T* sn = sE;           // [NN], read only before the first stage writes sE
   const int t0 = threadIdx.x;
   auto row = [&](int b) { return wrap(ly0 + b, ny); };
   for (TileWalk w(t0, LX, 3 * LY); w.k < 3 * NC; w.next()) {
@@ -1301,6 +1303,7 @@ __global__ void __launch_bounds__(kBlock)
       }
     }
   }
+  __syncthreads();  // the density terms are read before sE (which holds sn) is written
   // Ohm at local node (a, b), the r-th of this thread, from the centre field Bc
   auto ohm = [&](const T* Bc, int a, int b, int r, T E[3], T Bb[3]) {
     const int im = min(max(a - 1, 0), LX - 1), ip = min(a, LX - 1);

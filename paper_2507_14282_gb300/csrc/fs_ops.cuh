@@ -223,7 +223,7 @@ struct OpsImpl {
         // smaller shared memory lets four CTAs share an SM
         constexpr size_t smem0 =
             sizeof(T) * (9 * (size_t)(kFTX + 2 * (kFH - 1)) * (kFTY + 2 * (kFH - 1)) +
-                         4 * (size_t)(kFTX + 2 * (kFH - 1) + 1) * (kFTY + 2 * (kFH - 1) + 1));
+                         3 * (size_t)(kFTX + 2 * (kFH - 1) + 1) * (kFTY + 2 * (kFH - 1) + 1));
         if (fin)
           k_field_substep2<T, 1><<<gi, kBlock, smem, s->stream>>>(src, dst, d.n, d.u, d.E, d.Bb,
                                                                 d.G, s->g, s->ph, fc, fin, 1, 0);
