@@ -2,18 +2,21 @@
 // arithmetic type T (float or double) and the dimension DIM (1 or 2).
 //
 // Step n -> n+1 (Sec. 2 boundary inside a textbook hybrid PIC step):
-//   k_push     one CTA per tile of cells: CIC gather of E^n and Bbar^n from a
+//   k_push     persistent CTAs, each over a group of tiles of cells
+//              (fs_push.cuh): CIC gather of E^n and Bbar^n from a
 //              shared-memory field tile, Boris push, move, open far wall,
 //              faux-shock pass/return (Eq. 1), in-tile counting sort by new
 //              cell, CIC deposit of n and J by runs of sorted particles with a
-//              warp segmented reduction into a shared-memory node tile, then
+//              warp team reduction into a shared-memory node tile, then
 //              stayers written back to the tile's bucket and leavers to the
 //              mover list. Deposit partials per tile, no global atomics
 //              (except rare far movers).
-//   k_movers   leavers appended to their destination tile's bucket.
+//   k_movers   leavers appended to their destination tile's bucket (in the
+//              captured step, beside the next three, which read no bucket).
 //   k_inject_* thermal inflow at x = L and the cosmic-ray source at x = 0.
 //   k_moments  sum of the per-tile partials in a fixed order, wall
-//              half-volume correction, density floor, u = J / n.
+//              half-volume correction, density floor, u = J / n
+//              (k_moments_ct: the same with the 2D tile shape compiled in).
 //   k_ohm / k_faraday  RK4 substeps of dB/dt = -curl E(B), E from Ohm's law.
 //   k_ohm (final) also packs E and Bbar per node for the next gather.
 //

@@ -6,19 +6,24 @@
 // Per chunk (at most CH particles of one tile):
 //   1. wait for the chunk's bulk copies (its particle columns and the tile's
 //      packed E / Bbar nodes) on an mbarrier;
-//   2. push every particle in place and give it a sort key: its new cell in
-//      the tile (interior cells first), a halo cell, FAR (moved more than
-//      one cell out of the tile) or REMOVED; lanes with the same key take
-//      consecutive ranks after one shared atomic per key;
+//   2. push every particle (the state written back in place in FP32, kept in
+//      registers in FP64) and give it a sort key: its new cell in the tile
+//      (interior cells first), a halo cell, FAR (moved more than one cell out
+//      of the tile) or REMOVED; lanes with the same key take consecutive
+//      ranks after one shared atomic per key; then deposit the PREVIOUS
+//      chunk, in pieces (a key's particles, at most kPiece) that the warps
+//      claim from a shared counter, each piece a corner x split team
+//      reduction, so that warps which finished their push early take more;
 //   3. (barrier) each warp scans the key counts; every thread copies its
 //      particles into the key-sorted buffer;
 //   4. (barrier) the stage is refilled with a later chunk; coalesced writes
 //      from the sorted buffer: stayers to the tile's bucket of the output
-//      buffer, leavers to the tile's range of the mover list; the CIC deposit
-//      walks each key's contiguous range with a corner x split team per warp.
-// A tile's node accumulator is written out as its deposit partial during the
-// next chunk (two accumulators alternate between tiles), so each chunk costs
-// two block-wide barriers.
+//      buffer, leavers to the tile's range of the mover list.
+// A tile's node accumulator is written out as its deposit partial after the
+// first barrier of the chunk that follows the tile's last chunk (whose
+// deposit is done by then); two accumulators alternate between tiles. Each
+// chunk costs two block-wide barriers; the CTA's last chunk is deposited
+// after the loop.
 #pragma once
 #include "fs_engine.cuh"
 
@@ -667,9 +672,11 @@ __device__ __forceinline__ void team_deposit(typename Num<T>::acc* ACC, int NA, 
 // form ceil(n / kPiece) pieces of at most kPiece, numbered from pst[k]. Warp
 // w > 0 takes piece w - 1, then (and warp 0 from the start) the next
 // unclaimed piece from the counter *q until none is left, so that warps which
-// reach the deposit early take more of it. A
-// piece is one team reduction: whole keys (cells) where they are not large,
-// since the reduction, not the particle count, sets most of a piece's cost.
+// reach the deposit early take more of it. A piece is one team reduction:
+// whole keys (cells) where they are not large, since the reduction, not the
+// particle count, sets most of a piece's cost. Each particle's contributions
+// are formed as in the per-particle scheme, so in fixed point (FP64) the sums
+// do not depend on which warp takes which piece.
 constexpr int kPiece = 160;
 template <typename T, int DIM, bool REL>
 __device__ __forceinline__ void deposit_pieces(typename Num<T>::acc* ACC, int NA, int AX, int NE,
