@@ -12,10 +12,12 @@
 
 namespace fsx {
 
+// one thread per element up to 64 blocks per SM (every kernel launched with
+// it strides over the rest)
 inline int grid_for(long long n, int block = kBlock) {
   long long g = (n + block - 1) / block;
   if (g < 1) g = 1;
-  if (g > 152LL * 16) g = 152LL * 16;
+  if (g > 152LL * 64) g = 152LL * 64;
   return (int)g;
 }
 
