@@ -1264,6 +1264,8 @@ __global__ void __launch_bounds__(kBlock, (FINC >= 0 ? 4 : 1))
   T* sn = sE;           // [NN], read only before the first stage writes sE
   const int t0 = threadIdx.x;
   auto row = [&](int b) { return wrap(ly0 + b, ny); };
+  // (unrolled so that a thread's loads are in flight together)
+#pragma unroll 8
   for (TileWalk w(t0, LX, 3 * LY); w.k < 3 * NC; w.next()) {
     const int c = w.b / LY, b = w.b - c * LY;
     sB[w.k] = Bin[(size_t)c * nc + (size_t)row(b) * nx + lx0 + w.a];
